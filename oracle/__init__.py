@@ -1,0 +1,207 @@
+"""FP64 CPU oracle for the MDLG hot path (arXiv:1705.04368).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import this package.  It
+shares no code with the CUDA library in ``paper_1705_04368_gb300``; neither
+imports the other.
+
+Contents
+  mdlg_oracle.c  plain C, FP64: direct O(N^2) and linked-cell Lennard-Jones
+                 forces, velocity-Verlet, MDLG occupation numbers (Eq. MDni),
+                 the binary32 ideal-gas stream-and-bin, FP64 reductions.
+  closed_form.py the Gaussian/wedge equilibrium of Eq. fialpha.
+
+Parity status per function (what pins it, see tests/test_oracle_*.py):
+  lj_forces_direct   pinned: hand-computed two-particle force and energy,
+                     Newton's third law, finite-difference gradient of the
+                     potential energy.
+  lj_forces_cells    pinned: equal to the direct sum on random systems.
+  vv                 pinned: energy drift bound, time reversal, exact free
+                     flight when the potential is switched off.
+  mdlg_bin           pinned: Fig. 2 worked example (tests/golden), brute-force
+                     recount, partition of unity N = sum_i n_i, mass
+                     conservation across intervals, boundary convention.
+  stream_bin_f32     pinned: equal to mdlg_bin on the same binary32 points; its
+                     totals match the closed form within sampling error.
+  closed_form        pinned: numerical quadrature of the wedge integral (Eq.
+                     fieqW), Monte-Carlo binning, normalisation and first
+                     moment identities, the second-moment offset of Sec. VI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mdlg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle C file into a shared library with gcc (FP64, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            D = ctypes.c_double
+            lib.oracle_lj_forces_direct.argtypes = [I64, P, P, D, D, D, P, P, P]
+            lib.oracle_lj_forces_cells.argtypes = [I64, P, P, D, D, D, P, P, P]
+            lib.oracle_lj_forces_sample.argtypes = [I64, P, P, D, D, D, I64, P, P, P]
+            lib.oracle_vv.argtypes = [I64, P, P, P, ctypes.c_int, P, D, D, D, D, D, I64,
+                                      ctypes.c_int, P]
+            lib.oracle_free_stream.argtypes = [I64, P, P, P, D, I64]
+            lib.oracle_mdlg_bin.argtypes = [I64, P, P, D, P, ctypes.c_int, P, P, P, P]
+            lib.oracle_stream_bin_f32.argtypes = [I64, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
+            lib.oracle_kinetic.argtypes = [I64, P, D, P]
+            for name in ("oracle_lj_forces_direct", "oracle_lj_forces_cells",
+                         "oracle_lj_forces_sample", "oracle_vv", "oracle_free_stream",
+                         "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic"):
+                getattr(lib, name).restype = None
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def lj_forces(x, box, eps=1.0, sigma=1.0, rc=2.5, cells=False):
+    """Lennard-Jones forces, sum_j |F_ij| per particle, potential energy and virial.
+
+    x: (n, 2) positions.  Returns (F (n,2), fscale (n,), pe, virial).
+    """
+    lib = _load()
+    x = _f64(x)
+    n = x.shape[0]
+    L = _f64(box)
+    f = np.zeros((n, 2))
+    fs = np.zeros(n)
+    out = np.zeros(2)
+    fn = lib.oracle_lj_forces_cells if cells else lib.oracle_lj_forces_direct
+    fn(n, _p(x), _p(L), eps, sigma, rc, _p(f), _p(fs), _p(out))
+    return f, fs, float(out[0]), float(out[1])
+
+
+def lj_forces_sample(x, box, which, eps=1.0, sigma=1.0, rc=2.5):
+    """Direct-sum forces for the particles listed in ``which`` only."""
+    lib = _load()
+    x = _f64(x)
+    w = np.ascontiguousarray(which, dtype=np.int64)
+    f = np.zeros((w.size, 2))
+    fs = np.zeros(w.size)
+    lib.oracle_lj_forces_sample(x.shape[0], _p(x), _p(_f64(box)), eps, sigma, rc,
+                                w.size, _p(w), _p(f), _p(fs))
+    return f, fs
+
+
+class VV:
+    """Velocity-Verlet state (x, v, F) advanced by the oracle (FP64)."""
+
+    def __init__(self, x, v, box, dt, mass=1.0, eps=1.0, sigma=1.0, rc=2.5, cells=None):
+        self.x = _f64(x).copy()
+        self.v = _f64(v).copy()
+        self.f = np.zeros_like(self.x)
+        self.box = _f64(box)
+        self.dt, self.mass, self.eps, self.sigma, self.rc = dt, mass, eps, sigma, rc
+        n = self.x.shape[0]
+        self.cells = (n > 2048) if cells is None else cells
+        self.have_force = 0
+        self.pe = 0.0
+        self.virial = 0.0
+        self.steps = 0
+
+    def run(self, nsteps: int):
+        lib = _load()
+        out = np.zeros(2)
+        lib.oracle_vv(self.x.shape[0], _p(self.x), _p(self.v), _p(self.f), self.have_force,
+                      _p(self.box), self.mass, self.eps, self.sigma, self.rc, self.dt,
+                      int(nsteps), int(self.cells), _p(out))
+        self.have_force = 1
+        self.pe, self.virial = float(out[0]), float(out[1])
+        self.steps += int(nsteps)
+        return self
+
+    def kinetic(self):
+        """[kinetic energy, momentum_x, momentum_y] in FP64."""
+        out = np.zeros(3)
+        _load().oracle_kinetic(self.x.shape[0], _p(self.v), self.mass, _p(out))
+        return out
+
+    def energy(self):
+        """Total energy KE + PE (the force routine's PE of the current state)."""
+        if not self.have_force:
+            _, _, self.pe, self.virial = lj_forces(self.x, self.box, self.eps, self.sigma,
+                                                   self.rc, self.cells)
+        return float(self.kinetic()[0]) + self.pe
+
+
+def free_stream(x, v, box, dt, nsteps=1):
+    lib = _load()
+    x = _f64(x).copy()
+    lib.oracle_free_stream(x.shape[0], _p(x), _p(_f64(v)), _p(_f64(box)), dt, int(nsteps))
+    return x
+
+
+def mdlg_bin(xprev, xcur, dx, cells, vmax, field=False, counts=None, ncell=None, fld=None):
+    """Occupation numbers of Eq. MDni for one pair of snapshots.
+
+    Returns (counts (Q+1,) uint64, ncell (Cy*Cx,) uint32, field (Cy*Cx, Q+1) uint32
+    or None, vsum (2,) int64).  Passing arrays accumulates into them.
+    """
+    lib = _load()
+    xp, xc = _f64(xprev), _f64(xcur)
+    C = np.ascontiguousarray(cells, dtype=np.int64)
+    q1 = (2 * vmax + 1) ** 2 + 1
+    counts = np.zeros(q1, np.uint64) if counts is None else counts
+    ncell = np.zeros(int(C[0] * C[1]), np.uint32) if ncell is None else ncell
+    if field and fld is None:
+        fld = np.zeros((int(C[0] * C[1]), q1), np.uint32)
+    vsum = np.zeros(2, np.int64)
+    lib.oracle_mdlg_bin(xp.shape[0], _p(xp), _p(xc), float(dx), _p(C), int(vmax),
+                        _p(counts), _p(ncell), _p(fld) if fld is not None else None, _p(vsum))
+    return counts, ncell, fld, vsum
+
+
+def stream_bin_f32(pos, vel, dxs, dts, vmax):
+    """Ideal-gas stream + bin in binary32 decisions; returns (ncombo, Q+1) uint64."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    vel = np.ascontiguousarray(vel, dtype=np.float32)
+    dxs = np.ascontiguousarray(dxs, dtype=np.float32)
+    dts = np.ascontiguousarray(dts, dtype=np.float32)
+    q1 = (2 * vmax + 1) ** 2 + 1
+    counts = np.zeros((dxs.size, q1), np.uint64)
+    lib.oracle_stream_bin_f32(pos.shape[0], _p(pos), _p(vel), dxs.size, _p(dxs), _p(dts),
+                              int(vmax), _p(counts))
+    return counts
+
+
+def velocity_table(vmax):
+    """(Q, 2) integer lattice velocities in the index order i = (vy+V)(2V+1)+(vx+V)."""
+    r = np.arange(-vmax, vmax + 1)
+    vy, vx = np.meshgrid(r, r, indexing="ij")
+    return np.stack([vx.ravel(), vy.ravel()], axis=1)

@@ -1,0 +1,355 @@
+/*
+ * mdlg_oracle.c -- plain, slow, FP64 CPU oracle for the MDLG hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the package entry's smoke check and the
+ * CPU-baseline leg of the benchmark do.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * Paper: M. R. Parsa and A. J. Wagner, "Lattice Gas with Molecular Dynamics
+ * Collision Operator" (arXiv:1705.04368).  Each function names the section /
+ * equation it writes out.
+ *
+ * Conventions (readings of the paper, each fixed here and in the design notes):
+ *  - positions live in the periodic box (0, L] per axis (left-open, right-closed
+ *    like the cell indicator of Sec. III);
+ *  - the lattice cell of coordinate x is ceil(x / dx) - 1, i.e. the cell c with
+ *    c*dx < x <= (c+1)*dx  (cell indicator Delta_x, Sec. III);
+ *  - the lattice displacement is taken modulo the lattice size into the range
+ *    (-C/2, C/2]  (minimum image; the paper is silent on periodic images);
+ *  - velocity index i = (v_y + V)(2V+1) + (v_x + V) for |v_a| <= V, and the
+ *    extra index (2V+1)^2 collects every other displacement (overflow bin);
+ *  - the pair force is the negative gradient of sum_{j != i} V(r_ij) with the
+ *    Lennard-Jones V of Sec. IV, truncated at r_c, energy shifted by V(r_c);
+ *    mass m enters as dv/dt = F/m (the Newton equations of Sec. III).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Periodic helpers                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Minimum-image separation component: d reduced into [-L/2, L/2]. */
+static double min_image(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+/* Map a coordinate into the periodic interval (0, L]. */
+static double wrap_open_closed(double x, double L)
+{
+    while (x <= 0.0) x += L;
+    while (x > L) x -= L;
+    return x;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lennard-Jones pair interaction (Sec. IV, potential V(x))                  */
+/* ------------------------------------------------------------------------ */
+
+/* V(r) = 4 eps [ (sigma/r)^12 - (sigma/r)^6 ] */
+static double lj_v(double r2, double eps, double sigma)
+{
+    double sr2 = sigma * sigma / r2;
+    double sr6 = sr2 * sr2 * sr2;
+    return 4.0 * eps * (sr6 * sr6 - sr6);
+}
+
+/* -(1/r) dV/dr = 24 eps [ 2 (sigma/r)^12 - (sigma/r)^6 ] / r^2 ; the force on
+ * particle i from j is this scalar times (x_i - x_j). */
+static double lj_fscalar(double r2, double eps, double sigma)
+{
+    double sr2 = sigma * sigma / r2;
+    double sr6 = sr2 * sr2 * sr2;
+    return 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
+}
+
+/*
+ * Direct O(N^2) forces: F_i = -d/dx_i sum_{j != i} V(|x_i - x_j|) over all
+ * pairs with r < rc under minimum image (Newton equations of Sec. III with the
+ * pair potential of Sec. IV).  Every pair is evaluated from both sides.
+ *
+ *   x      : n x 2 positions (row-major, x then y)
+ *   f      : n x 2 output forces
+ *   fscale : optional n output, sum_j |F_ij| (a per-particle force magnitude
+ *            scale used to state relative force tolerances)
+ *   out    : optional [pe, virial] where pe = sum_{i<j} (V(r_ij) - V(rc)) and
+ *            virial = sum_{i<j} r_ij . F_ij
+ */
+void oracle_lj_forces_direct(int64_t n, const double *x, const double *L,
+                             double eps, double sigma, double rc,
+                             double *f, double *fscale, double *out)
+{
+    double rc2 = rc * rc, vshift = lj_v(rc2, eps, sigma);
+    double pe = 0.0, vir = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double fx = 0.0, fy = 0.0, fs = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[2 * i] - x[2 * j], L[0]);
+            double dy = min_image(x[2 * i + 1] - x[2 * j + 1], L[1]);
+            double r2 = dx * dx + dy * dy;
+            if (r2 >= rc2) continue;
+            double s = lj_fscalar(r2, eps, sigma);
+            fx += s * dx;
+            fy += s * dy;
+            fs += fabs(s) * sqrt(r2);
+            pe += 0.5 * (lj_v(r2, eps, sigma) - vshift);
+            vir += 0.5 * s * r2;
+        }
+        f[2 * i] = fx;
+        f[2 * i + 1] = fy;
+        if (fscale) fscale[i] = fs;
+    }
+    if (out) { out[0] = pe; out[1] = vir; }
+}
+
+/*
+ * Forces for a SAMPLE of particles only, each by the direct O(N) sum over all
+ * other particles (same definition as above).  Lets tests check outputs of a
+ * full-size system one particle at a time.
+ */
+void oracle_lj_forces_sample(int64_t n, const double *x, const double *L,
+                             double eps, double sigma, double rc,
+                             int64_t ns, const int64_t *which,
+                             double *f, double *fscale)
+{
+    double rc2 = rc * rc;
+    for (int64_t k = 0; k < ns; ++k) {
+        int64_t i = which[k];
+        double fx = 0.0, fy = 0.0, fs = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[2 * i] - x[2 * j], L[0]);
+            double dy = min_image(x[2 * i + 1] - x[2 * j + 1], L[1]);
+            double r2 = dx * dx + dy * dy;
+            if (r2 >= rc2) continue;
+            double s = lj_fscalar(r2, eps, sigma);
+            fx += s * dx;
+            fy += s * dy;
+            fs += fabs(s) * sqrt(r2);
+        }
+        f[2 * k] = fx;
+        f[2 * k + 1] = fy;
+        if (fscale) fscale[k] = fs;
+    }
+}
+
+/*
+ * The same forces found through a linked-cell list (cells of side >= rc), so
+ * the oracle can integrate systems of 10^4 - 10^5 particles.  It visits exactly
+ * the pairs with r < rc that the direct sum visits; only the summation order
+ * differs.  Falls back to the direct sum when fewer than 3 cells fit per axis.
+ */
+void oracle_lj_forces_cells(int64_t n, const double *x, const double *L,
+                            double eps, double sigma, double rc,
+                            double *f, double *fscale, double *out)
+{
+    int64_t ncx = (int64_t)floor(L[0] / rc), ncy = (int64_t)floor(L[1] / rc);
+    if (ncx < 3 || ncy < 3) {
+        oracle_lj_forces_direct(n, x, L, eps, sigma, rc, f, fscale, out);
+        return;
+    }
+    double hx = L[0] / (double)ncx, hy = L[1] / (double)ncy;
+    int64_t ncell = ncx * ncy;
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *cx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *cy = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double px = wrap_open_closed(x[2 * i], L[0]);
+        double py = wrap_open_closed(x[2 * i + 1], L[1]);
+        int64_t a = (int64_t)floor(px / hx), b = (int64_t)floor(py / hy);
+        if (a >= ncx) a = ncx - 1;
+        if (b >= ncy) b = ncy - 1;
+        cx[i] = a; cy[i] = b;
+        next[i] = head[b * ncx + a];
+        head[b * ncx + a] = i;
+    }
+    double rc2 = rc * rc, vshift = lj_v(rc2, eps, sigma);
+    double pe = 0.0, vir = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double fx = 0.0, fy = 0.0, fs = 0.0;
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                int64_t a = (cx[i] + ox + ncx) % ncx, b = (cy[i] + oy + ncy) % ncy;
+                for (int64_t j = head[b * ncx + a]; j >= 0; j = next[j]) {
+                    if (j == i) continue;
+                    double dx = min_image(x[2 * i] - x[2 * j], L[0]);
+                    double dy = min_image(x[2 * i + 1] - x[2 * j + 1], L[1]);
+                    double r2 = dx * dx + dy * dy;
+                    if (r2 >= rc2) continue;
+                    double s = lj_fscalar(r2, eps, sigma);
+                    fx += s * dx;
+                    fy += s * dy;
+                    fs += fabs(s) * sqrt(r2);
+                    pe += 0.5 * (lj_v(r2, eps, sigma) - vshift);
+                    vir += 0.5 * s * r2;
+                }
+            }
+        f[2 * i] = fx;
+        f[2 * i + 1] = fy;
+        if (fscale) fscale[i] = fs;
+    }
+    if (out) { out[0] = pe; out[1] = vir; }
+    free(head); free(next); free(cx); free(cy);
+}
+
+/*
+ * Velocity-Verlet integration of the Newton equations (Sec. III) for nsteps:
+ *   v <- v + F dt / (2m);  x <- x + v dt (wrapped into (0, L]);
+ *   F <- F(x);             v <- v + F dt / (2m).
+ * x, v are updated in place; f holds F(x) on entry and on exit (pass
+ * have_force = 0 to have it computed first).  use_cells selects the cell-list
+ * force routine.  out (optional) receives [pe, virial] of the final state.
+ */
+void oracle_vv(int64_t n, double *x, double *v, double *f, int have_force,
+               const double *L, double mass, double eps, double sigma, double rc,
+               double dt, int64_t nsteps, int use_cells, double *out)
+{
+    double tmp[2] = {0.0, 0.0};
+    if (!have_force) {
+        if (use_cells) oracle_lj_forces_cells(n, x, L, eps, sigma, rc, f, NULL, tmp);
+        else oracle_lj_forces_direct(n, x, L, eps, sigma, rc, f, NULL, tmp);
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 2; ++a) {
+                v[2 * i + a] += 0.5 * dt * f[2 * i + a] / mass;
+                x[2 * i + a] = wrap_open_closed(x[2 * i + a] + dt * v[2 * i + a], L[a]);
+            }
+        if (use_cells) oracle_lj_forces_cells(n, x, L, eps, sigma, rc, f, NULL, tmp);
+        else oracle_lj_forces_direct(n, x, L, eps, sigma, rc, f, NULL, tmp);
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 2; ++a)
+                v[2 * i + a] += 0.5 * dt * f[2 * i + a] / mass;
+    }
+    if (out) { out[0] = tmp[0]; out[1] = tmp[1]; }
+}
+
+/* Free streaming x <- x + v dt of the non-interacting gas (ballistic limit of
+ * Sec. IV-A), wrapped into (0, L]. */
+void oracle_free_stream(int64_t n, double *x, const double *v, const double *L,
+                        double dt, int64_t nsteps)
+{
+    for (int64_t s = 0; s < nsteps; ++s)
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 2; ++a)
+                x[2 * i + a] = wrap_open_closed(x[2 * i + a] + dt * v[2 * i + a], L[a]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* MDLG occupation numbers (Sec. III, Eq. MDni)                              */
+/* ------------------------------------------------------------------------ */
+
+/* Cell indicator of Sec. III: the cell c with c*dx < x <= (c+1)*dx. */
+static int64_t lattice_cell(double x, double dx)
+{
+    return (int64_t)ceil(x / dx) - 1;
+}
+
+/* Lattice displacement modulo C, reduced into (-C/2, C/2]. */
+static int64_t lattice_disp(int64_t d, int64_t C)
+{
+    int64_t r = ((d % C) + C) % C;
+    if (r > C / 2) r -= C;
+    return r;
+}
+
+/*
+ * n_i(x,t) = sum_j Delta_x(x_j(t)) Delta_{x - v_i}(x_j(t - dt))   (Eq. MDni)
+ * and N(x,t) = sum_j Delta_x(x_j(t))                               (Sec. III)
+ *
+ * Walks the particles one by one: the cell of each particle at t (site x) and
+ * at t - dt (site x - v_i) give its lattice velocity v_i, and the particle adds
+ * one to n_i at site x.
+ *
+ *   xprev, xcur : n x 2 positions at t - dt and t, each in (0, L]
+ *   C[2]        : lattice cells per axis (L = C dx)
+ *   vmax        : window half-width V; Q = (2V+1)^2 velocities + 1 overflow
+ *   counts      : Q+1 totals over the lattice (added to)
+ *   ncell       : optional C[0]*C[1] site counts N(x,t) (added to)
+ *   field       : optional C[0]*C[1]*(Q+1) occupation numbers, site-major
+ *                 (added to)
+ *   vsum        : optional [sum_j v_jx, sum_j v_jy] over in-window particles
+ */
+void oracle_mdlg_bin(int64_t n, const double *xprev, const double *xcur,
+                     double dx, const int64_t *C, int vmax,
+                     uint64_t *counts, uint32_t *ncell, uint32_t *field,
+                     int64_t *vsum)
+{
+    int64_t W = 2 * vmax + 1, Q = W * W;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t c0x = lattice_cell(xprev[2 * j], dx), c0y = lattice_cell(xprev[2 * j + 1], dx);
+        int64_t c1x = lattice_cell(xcur[2 * j], dx), c1y = lattice_cell(xcur[2 * j + 1], dx);
+        int64_t vx = lattice_disp(c1x - c0x, C[0]);
+        int64_t vy = lattice_disp(c1y - c0y, C[1]);
+        int64_t i;
+        if (vx < -vmax || vx > vmax || vy < -vmax || vy > vmax) {
+            i = Q;
+        } else {
+            i = (vy + vmax) * W + (vx + vmax);
+            if (vsum) { vsum[0] += vx; vsum[1] += vy; }
+        }
+        int64_t site = c1y * C[0] + c1x;
+        counts[i] += 1;
+        if (ncell) ncell[site] += 1;
+        if (field) field[site * (Q + 1) + i] += 1;
+    }
+}
+
+/*
+ * Non-interacting gas streamed and binned in one pass (the ballistic case of
+ * Sec. IV-A), for several (dx, dt) pairs.  The decision of which cell a point
+ * falls in is taken in IEEE binary32, the precision the device path computes
+ * in: x' = fl(x + fl(v dt)) (not wrapped), cell = ceil(fl(x / dx)) - 1 per
+ * axis, lattice velocity = cell(x') - cell(x).  For |v dt| < L/2 this is the
+ * periodic definition of Eq. MDni, with the site taken modulo C in integers.
+ *
+ *   pos, vel : n x 2 binary32 values, positions in (0, L]
+ *   counts   : ncombo x (Q+1) totals (added to)
+ */
+void oracle_stream_bin_f32(int64_t n, const float *pos, const float *vel,
+                           int ncombo, const float *dxs, const float *dts,
+                           int vmax, uint64_t *counts)
+{
+    int64_t W = 2 * vmax + 1, Q = W * W;
+    for (int k = 0; k < ncombo; ++k) {
+        volatile float dx = dxs[k], dt = dts[k];
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t c[2][2];
+            for (int a = 0; a < 2; ++a) {
+                volatile float x = pos[2 * j + a];
+                volatile float d = vel[2 * j + a] * dt;   /* one rounding */
+                volatile float xn = x + d;                 /* one rounding */
+                volatile float q0 = x / dx, q1 = xn / dx;  /* one rounding each */
+                c[a][0] = (int64_t)ceilf(q0) - 1;
+                c[a][1] = (int64_t)ceilf(q1) - 1;
+            }
+            int64_t vx = c[0][1] - c[0][0], vy = c[1][1] - c[1][0];
+            int64_t i = (vx < -vmax || vx > vmax || vy < -vmax || vy > vmax)
+                            ? Q : (vy + vmax) * W + (vx + vmax);
+            counts[k * (Q + 1) + i] += 1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 global reductions                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* out = [kinetic energy sum m v^2 / 2, momentum_x, momentum_y] */
+void oracle_kinetic(int64_t n, const double *v, double mass, double *out)
+{
+    double ke = 0.0, px = 0.0, py = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        ke += 0.5 * mass * (v[2 * i] * v[2 * i] + v[2 * i + 1] * v[2 * i + 1]);
+        px += mass * v[2 * i];
+        py += mass * v[2 * i + 1];
+    }
+    out[0] = ke; out[1] = px; out[2] = py;
+}

@@ -1,0 +1,367 @@
+"""Benchmark of the MD + MDLG hot path on GB300.
+
+Workload: the production 2D Lennard-Jones gas, N = 4 194 304 at rho = 0.3,
+T = 1 (L = 3740, rounded up to a multiple of dx = 4), eps = sigma = m = 1,
+rc = 2.5 truncated-shifted, dt = 0.005; MDLG binning at dx = 4 for the coarse
+time steps 10, 20, 50, 100 and 200 MD steps; FP64 energy / momentum / virial
+reductions every 100 steps.  One benchmark step = 200 MD steps (all lags bin at
+least once, sorts included).  Metric: particle-steps per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): one independent system per rank
+(different seed), no data-path collective ("scaling": "weak").
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import mdlg_inputs as mi  # noqa: E402
+
+MD_STEPS_PER_STEP = 200
+METRIC = "MD+MDLG particle-steps/s on 1 GB300 (% FP32/HBM roofline); batched & adjoint vs plain"
+UNIT = "particle-steps/s"
+STEP_BYTES_PER_PARTICLE = 36      # read cell 4 + cl 8 + v 8, write cl 8 + v 8
+IDEALGAS_BYTES_PER_PARTICLE = 16  # x, y, vx, vy binary32
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def _traffic_record(kernel: str):
+    """dram bytes per particle of a kernel from profiles/traffic.txt, if the
+    kernel source has not changed since that capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_1705_04368_gb300", "csrc", "mdlg_md.cu"), "rb").read()
+        sha = hashlib.sha256(src).hexdigest()[:16]
+        for ln in open(path):
+            kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("src_sha") == sha:
+                return float(kv["dram_bytes_per_particle"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[3 + k].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _workload():
+    c = mi.PRODUCTION_LJ
+    return c
+
+
+def _config(c, world):
+    rho_eff = c.n / (c.box * c.box)
+    return {"workload": c.name, "n": c.n, "box": c.box, "rho_eff": round(rho_eff, 5),
+            "temperature": c.temperature, "rc": c.rc, "dt": c.dt, "dx": c.dx,
+            "lag_md_steps": list(c.lags), "md_steps_per_step": MD_STEPS_PER_STEP,
+            "stats_every": 100, "systems": world,
+            "l2": "inputs larger than L2 (state 352 MB per system, 151 MB moved per MD step)"}
+
+
+def _params(c, m):
+    return m.Params(n=c.n, box=c.box, dx=c.dx, dt=c.dt, lag_steps=c.lags, rcut=c.rc,
+                    stats_every=100)
+
+
+def _oracle_sample(c, x0, v0, md_steps=3):
+    """FP64 oracle (as it stands, one host thread) on the full system for a few MD steps."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
+    ref.run(md_steps)
+    cnt = np.zeros(50, np.uint64)
+    oracle.mdlg_bin(x0, ref.x, c.dx, (int(c.box / c.dx),) * 2, 3, counts=cnt)
+    dt_s = time.perf_counter() - t0
+    return c.n * md_steps / dt_s, dt_s
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    c = _workload()
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
+    import oracle
+    ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ref.run(1)
+        dt_s = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt_s)
+    total = sum(times)
+    value = c.n * len(times) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(_config(c, 1), md_steps_per_step=1),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} velocity-Verlet steps of the full "
+                                       f"{c.n}-particle system, FP64 linked-cell oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1705_04368_gb300 as m
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = _workload()
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1 + rank)
+    params = _params(c, m)
+    stream = torch.cuda.Stream(device=dev)
+    sim = m.Simulation(params, x0, v0, stream=stream, device=local_rank)
+    for _ in range(args.warmup):
+        sim.step(MD_STEPS_PER_STEP)
+    torch.cuda.synchronize()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sim.profile(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(MD_STEPS_PER_STEP)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sim.profile(False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st, counts, fi = sim.stats()
+    sim.close()
+    md_steps = args.steps * MD_STEPS_PER_STEP
+    value = world * c.n * md_steps / (ms / 1e3)
+
+    # dominant kernel: fused force + velocity-Verlet step
+    hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+    step_ms, step_launches = prof["step"]
+    avg_step_s = step_ms / 1e3 / max(step_launches, 1)
+    step_bytes = STEP_BYTES_PER_PARTICLE * c.n
+    achieved_gbs = step_bytes / avg_step_s / 1e9
+    rho_eff = c.n / (c.box * c.box)
+    n_in = rho_eff * math.pi * c.rc ** 2
+    flops = c.n * (18.0 * n_in + 8.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    achieved_tf = flops / avg_step_s / 1e12
+    tpp = _traffic_record("k_step")
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
+                "traffic": (tpp * c.n) if tpp is not None else None,
+                "kernel": "k_step (force + velocity-Verlet)",
+                "algorithmic_bytes_per_launch": step_bytes,
+                "avg_launch_us": avg_step_s * 1e6,
+                "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
+                         "frac": achieved_tf / fp32_peak,
+                         "flops_per_particle": 18.0 * n_in + 8.0}}
+    kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms if ms else None}
+               for k, v in prof.items() if v[1]}
+    launches = prof["step"][1] + prof["sort"][1] + prof["bin"][1] + prof["sync"][1]
+
+    # ideal-gas single pass (binning throughput), rotating buffers > 2x L2
+    ig = _idealgas(m, torch, dev, stream, hbm_gbs)
+
+    # end to end through the C ABI: pinned host state in, f_i out, every step
+    e2e = _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(c, world), "roofline": roofline,
+            "gpu_launches": launches, "kernels": kernels, "clocks": clk, "e2e": e2e,
+            "idealgas": ig, "status": st["status"]}
+    if rank == 0:
+        if world == 1:
+            v, secs = _oracle_sample(c, x0, v0)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"3 FP64 velocity-Verlet steps of the full "
+                                              f"{c.n}-particle system plus one MDLG binning, "
+                                              f"{secs:.1f} s on one host thread"}
+        print(json.dumps(line), flush=True)
+
+
+def _idealgas(m, torch, dev, stream, hbm_gbs):
+    n = mi.IDEALGAS_N
+    combos = list(mi.IDEALGAS_COMBOS)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    bufs = []
+    with torch.cuda.stream(stream):
+        for _ in range(4):
+            pos = (1.0 - torch.rand((n, 2), generator=g, device=dev)) * mi.IDEALGAS_BOX
+            vel = torch.randn((n, 2), generator=g, device=dev)
+            bufs.append((pos.float().contiguous(), vel.float().contiguous()))
+        counts = torch.zeros((len(combos), 50), dtype=torch.int64, device=dev)
+    for k in range(4):
+        m.idealgas_bin(*bufs[k % 4], combos, 3, counts, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 40
+    e0.record(stream)
+    for k in range(reps):
+        m.idealgas_bin(*bufs[k % 4], combos, 3, counts, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / reps
+    gbs = n * IDEALGAS_BYTES_PER_PARTICLE / s / 1e9
+    return {"workload": "idealgas_n4194304_L2048_9combos", "particles_per_s": n / s,
+            "us_per_pass": s * 1e6, "achieved_gbs": gbs, "frac_hbm": gbs / hbm_gbs,
+            "bin_decisions_per_s": n * len(combos) / s}
+
+
+def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev):
+    x_pin = torch.empty((c.n, 2), dtype=torch.float64, pin_memory=True)
+    v_pin = torch.empty((c.n, 2), dtype=torch.float64, pin_memory=True)
+    x_pin.numpy()[:] = x0
+    v_pin.numpy()[:] = v0
+    reps = max(2, min(args.steps, 5))
+
+    def one():
+        with m.Simulation(params, x_pin.numpy(), v_pin.numpy(), stream=stream,
+                          device=local_rank) as s:
+            s.step(MD_STEPS_PER_STEP)
+            s.stats()
+
+    one()   # warm the allocator
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([secs], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    q1 = params.q1
+    nl = len(params.lag_steps)
+    return {"value": world * c.n * MD_STEPS_PER_STEP * reps / secs, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * c.n * 2 * 8,
+            "d2h_bytes_per_step": 2 * nl * q1 * 8 + 120,
+            "steps": reps,
+            "what": "mdlg_create from pinned host x0, v0 + 200 MD steps + mdlg_stats (counts, "
+                    "f_i to host) + mdlg_destroy, per step"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * mdlg.h -- C ABI of the GB300 MD + MDLG library.
+ *
+ * Method: M. R. Parsa and A. J. Wagner, "Lattice Gas with Molecular Dynamics
+ * Collision Operator", arXiv:1705.04368.  The library integrates a periodic 2D
+ * Lennard-Jones gas (Newton equations of Sec. III, potential of Sec. IV) and
+ * coarse-grains it into the MDLG occupation numbers n_i(x,t) of Eq. MDni:
+ * every particle is binned into a lattice cell at t - dt and at t, the cell
+ * displacement is its lattice velocity v_i, and the counts are accumulated per
+ * velocity (and optionally per lattice site) so that their average estimates
+ * the equilibrium f_i of Eq. fieq.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 (MDLG_OK) or a negative MDLG_E* code; no exception or
+ *    abort crosses the ABI.  mdlg_strerror() names a code.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory; "host" pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes and the library never frees one of them.
+ *  - Work is enqueued on the CUDA stream given at creation (or per call for
+ *    the context-free entry points) and returns before it finishes, except
+ *    where a function says it synchronizes.
+ *  - Lattice cells are left-open, right-closed: coordinate x is in cell c iff
+ *    c*dx < x <= (c+1)*dx (the cell indicator Delta_x of Sec. III).  The box
+ *    is (0, L] per axis.
+ *  - Lattice velocities are indexed i = (v_y + V)(2V+1) + (v_x + V) for
+ *    |v_x|, |v_y| <= V; index Q = (2V+1)^2 counts every displacement outside
+ *    that window.  Displacements are taken modulo the lattice size into
+ *    (-C/2, C/2] (minimum image).
+ */
+#ifndef MDLG_H
+#define MDLG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define MDLG_OK          0
+#define MDLG_EINVAL     -1   /* an argument is out of range or inconsistent    */
+#define MDLG_ENOMEM     -2   /* the allocator returned NULL                    */
+#define MDLG_ECUDA      -3   /* a CUDA runtime call failed                     */
+#define MDLG_EOVERFLOW  -4   /* a counter or index range was exceeded          */
+#define MDLG_ENONFINITE -5   /* a non-finite position or velocity was found    */
+#define MDLG_ETIMEOUT   -6   /* a bounded device wait gave up                  */
+#define MDLG_ENOTIMPL   -7   /* the entry point is declared but not built yet  */
+
+/* ---- limits ------------------------------------------------------------- */
+#define MDLG_MAX_LAGS   8    /* coarse time steps tracked concurrently         */
+#define MDLG_MAX_VMAX   15   /* window half-width V                            */
+#define MDLG_MAX_COMBOS 16   /* (dx, dt) pairs of one ideal-gas pass           */
+
+/* ---- potentials --------------------------------------------------------- */
+#define MDLG_POT_NONE   0    /* non-interacting gas (free flight)              */
+#define MDLG_POT_LJ_TS  1    /* Lennard-Jones, truncated at rc, energy shifted */
+
+/* ---- per-site output modes (mdlg_params.site_mode, bit flags) ------------ */
+#define MDLG_SITES_FIELD 1   /* keep n_i(x,t), N(x,t) of the latest interval   */
+#define MDLG_SITES_ACCUM 2   /* accumulate sum_t n_i(x,t), sum_t N(x,t)        */
+
+/*
+ * Parameters of one simulation (Sec. III: N particles, periodic box, pair
+ * potential; Sec. III lattice spacing dx and coarse time step dt; Sec. IV:
+ * Lennard-Jones eps, sigma, m).
+ */
+typedef struct {
+    int32_t dim;          /* must be 2 (the paper's test case, Sec. IV)          */
+    int64_t n;            /* particles, >= 1                                     */
+    double  box[2];       /* periodic box L_x, L_y; integer multiples of dx       */
+    int32_t potential;    /* MDLG_POT_LJ_TS or MDLG_POT_NONE                      */
+    double  eps, sigma;   /* Lennard-Jones energy and length (Sec. IV)            */
+    double  mass;         /* particle mass m                                     */
+    double  rcut;         /* cutoff radius r_c (> 0)                              */
+    double  dt;           /* MD time step (> 0)                                   */
+    double  grid;         /* base grid g: a power of two; dx is a multiple of g   */
+    double  skin;         /* minimum neighbour-cell skin beyond rcut (>= 0)        */
+    int32_t sort_every;   /* MD steps between cell re-sorts; 0 picks one          */
+    double  dx;           /* lattice spacing Delta x (Sec. III)                   */
+    int32_t nlags;        /* coarse time steps tracked, 1..MDLG_MAX_LAGS          */
+    int32_t lag_steps[MDLG_MAX_LAGS]; /* Delta t of each, in MD steps (>= 1)      */
+    int32_t vmax;         /* window half-width V, 1..MDLG_MAX_VMAX                */
+    int32_t site_mode;    /* MDLG_SITES_* flags for lag 0; 0 = totals only         */
+    int32_t stats_every;  /* MD steps between FP64 reductions; 0 = only on request */
+} mdlg_params;
+
+/*
+ * Device memory supplier.  alloc returns `bytes` of device memory aligned to
+ * at least 256 bytes, or NULL; free releases it.  Passing NULL for the whole
+ * struct makes the library use cudaMalloc / cudaFree.
+ */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void  (*free)(void *ptr, void *user);
+    void  *user;
+} mdlg_allocator;
+
+typedef struct mdlg_ctx mdlg_ctx;
+
+/* FP64 observables of the most recent statistics step and the MDLG totals. */
+typedef struct {
+    int64_t step;                 /* MD steps taken so far                       */
+    int64_t stats_step;           /* step the energies below refer to (-1: none) */
+    double  kinetic;              /* sum m v^2 / 2 at that step                   */
+    double  potential;            /* sum_{i<j} V(r_ij) - V(rc)                    */
+    double  virial;               /* sum_{i<j} r_ij . F_ij                        */
+    double  momentum[2];          /* sum m v                                      */
+    double  temperature;          /* kinetic / (N - 1)  (2N - 2 degrees, k_B = 1) */
+    double  pressure;             /* (kinetic + virial / 2) / (L_x L_y)           */
+    int64_t intervals[MDLG_MAX_LAGS]; /* coarse intervals binned per lag          */
+    int32_t status;               /* MDLG_OK or the first device-side error seen  */
+} mdlg_stats_out;
+
+/*
+ * mdlg_create -- validate parameters, allocate device state, upload the
+ * initial condition and enqueue the initial force evaluation.
+ *   params    : see mdlg_params; MDLG_EINVAL on any inconsistency.
+ *   x0, v0    : host, n x 2 FP64 positions in (0, L] and velocities (Sec. III
+ *               initial condition x_i(0), v_i(0)); NULL -> MDLG_EINVAL.
+ *   allocator : device memory supplier, or NULL for cudaMalloc.
+ *   stream    : cudaStream_t (as void*) all work of the context is enqueued on;
+ *               NULL is the legacy default stream.
+ *   out       : receives the context.
+ * The call copies x0 / v0 before it returns; it does not synchronize the
+ * stream.  Errors: MDLG_EINVAL, MDLG_ENOMEM, MDLG_ECUDA, MDLG_ENONFINITE.
+ */
+int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
+                const mdlg_allocator *allocator, void *stream, mdlg_ctx **out);
+
+/*
+ * mdlg_step -- enqueue nsteps velocity-Verlet steps of the Newton equations
+ * (Sec. III) with Lennard-Jones forces (Sec. IV).  After every MD step whose
+ * count is a multiple of lag_steps[k], the particles are binned for lag k
+ * (Eq. MDni) against their lattice cells lag_steps[k] steps earlier and the
+ * counts are added to the lag's totals (Eq. fieq).  FP64 reductions run on
+ * multiples of stats_every.  Asynchronous.  Errors: MDLG_EINVAL, MDLG_ECUDA.
+ */
+int mdlg_step(mdlg_ctx *ctx, int64_t nsteps);
+
+/*
+ * mdlg_stats -- synchronize the stream and report the FP64 observables of the
+ * most recent statistics step (taking one now at the current step if none was
+ * taken since the last step), the MDLG totals and the device status word.
+ *   out    : host, filled in.
+ *   counts : host, nlags x (Q+1) uint64 totals sum_{t,x} n_i(x,t), or NULL.
+ *   fi     : host, nlags x (Q+1) FP64 estimates f_i / rho^eq
+ *            = counts_i / (N * intervals) (Eq. fieq), or NULL.
+ */
+int mdlg_stats(mdlg_ctx *ctx, mdlg_stats_out *out, uint64_t *counts, double *fi);
+
+/*
+ * mdlg_get_state -- synchronize and copy the state in the original particle
+ * order (host buffers, n x 2 each; any may be NULL):
+ *   x : FP64 positions in (0, L] (exact value of the stored representation)
+ *   v : FP64 velocities at the current integer step
+ *   f : FP64 copy of the FP32 forces at the current positions
+ */
+int mdlg_get_state(mdlg_ctx *ctx, double *x, double *v, double *f);
+
+/*
+ * mdlg_get_sites -- synchronize and copy lag-0 per-site outputs (host; either
+ * may be NULL).  site_counts: C_y*C_x*(Q+1) uint32, ncell: C_y*C_x uint32,
+ * site-major with site = c_y*C_x + c_x.  They hold the latest interval
+ * (MDLG_SITES_FIELD) or the sum over intervals (MDLG_SITES_ACCUM).
+ * MDLG_EINVAL if site_mode is 0.
+ */
+int mdlg_get_sites(mdlg_ctx *ctx, uint32_t *site_counts, uint32_t *ncell);
+
+/* mdlg_reset_counts -- enqueue zeroing of all MDLG totals and per-site outputs,
+ * keeping the stored earlier lattice cells (to discard an equilibration). */
+int mdlg_reset_counts(mdlg_ctx *ctx);
+
+/*
+ * mdlg_adjoint -- reverse-mode gradients of soft-binned MDLG moments with
+ * respect to eps, sigma and the initial state.  Declared for the interface;
+ * returns MDLG_ENOTIMPL in this version.
+ */
+int mdlg_adjoint(mdlg_ctx *ctx, const double *dloss, double *grad_eps,
+                 double *grad_sigma, double *grad_x0, double *grad_v0);
+
+/*
+ * mdlg_profile -- per-kernel timing of the context's launches with CUDA events
+ * on its stream (tracing aid; no counterpart in the paper).
+ *   enable = 1 : clear the record and start recording every launch group;
+ *   enable = 0 : stop, synchronize and report.
+ * ms[k] / launches[k] (host, MDLG_PROF_KINDS entries each, may be NULL) receive
+ * the summed device time and the number of kernel launches of each kind:
+ * MDLG_PROF_STEP (force + velocity-Verlet), MDLG_PROF_SORT (cell re-sort,
+ * all its kernels), MDLG_PROF_BIN (MDLG binning), MDLG_PROF_SYNC (statistics /
+ * state download).  Recording adds two event records per launch group.
+ */
+#define MDLG_PROF_STEP  0
+#define MDLG_PROF_SORT  1
+#define MDLG_PROF_BIN   2
+#define MDLG_PROF_SYNC  3
+#define MDLG_PROF_KINDS 4
+int mdlg_profile(mdlg_ctx *ctx, int enable, double *ms, int64_t *launches);
+
+/* mdlg_destroy -- synchronize, release device state; NULL is ignored. */
+void mdlg_destroy(mdlg_ctx *ctx);
+
+/* mdlg_strerror -- static string naming an MDLG_E* code. */
+const char *mdlg_strerror(int code);
+
+/*
+ * Lattice for the context-free binning entry point.  Positions are given as
+ * integer base-cell indices: base cell k of an axis is (k g, (k+1) g], so a
+ * particle in base cell k lies in lattice cell floor(k / ratio) with
+ * ratio = dx / g.
+ */
+typedef struct {
+    int32_t base[2];   /* base cells per axis, L / g (each a multiple of ratio)  */
+    int32_t ratio;     /* dx / g, >= 1                                           */
+    int32_t vmax;      /* window half-width V, 1..MDLG_MAX_VMAX                  */
+} mdlg_lattice;
+
+/*
+ * mdlg_bin -- Eq. MDni for one pair of snapshots of the same n particles.
+ *   idx_prev, idx_cur : device, n x 2 int32 base-cell indices (x, y) in
+ *                       [0, base) at t - dt and at t.
+ *   counts : device, Q+1 uint64 totals, ADDED to (zero them to start).
+ *   ncell  : device, C_y*C_x uint32 N(x,t), added to, or NULL.
+ *   field  : device, C_y*C_x*(Q+1) uint32 n_i(x,t), added to, or NULL.
+ *   stream : cudaStream_t (as void*).
+ * Errors: MDLG_EINVAL (bad lattice, n < 0, NULL counts), MDLG_ECUDA.
+ * Out-of-range indices are wrapped modulo base (no fault, no error).
+ */
+int mdlg_bin(const mdlg_lattice *lat, int64_t n, const int32_t *idx_prev,
+             const int32_t *idx_cur, uint64_t *counts, uint32_t *ncell,
+             uint32_t *field, void *stream);
+
+/*
+ * mdlg_idealgas_bin -- non-interacting gas of Sec. IV-A (ballistic limit):
+ * stream every particle freely for each (dx_k, dt_k) pair and bin its start
+ * and end points (Eq. MDni), all pairs in one pass over the particles.  The
+ * cell decisions are taken in IEEE binary32:
+ *   x' = fl(x + fl(v dt_k)),  cell = ceil(fl(x / dx_k)) - 1 per axis,
+ *   v_i = cell(x') - cell(x)  (x' is not wrapped; the box is a multiple of
+ *   every dx_k and |v dt_k| < L/2 is assumed, as in the paper's regime).
+ *   pos, vel : device, n x 2 float (x, y) pairs; positions in (0, L].
+ *   dxs, dts : host, ncombo values each; 1 <= ncombo <= MDLG_MAX_COMBOS.
+ *   counts   : device, ncombo x (Q+1) uint64, ADDED to.
+ * Errors: MDLG_EINVAL, MDLG_ECUDA.
+ */
+int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t ncombo,
+                      const float *dxs, const float *dts, int32_t vmax,
+                      uint64_t *counts, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDLG_H */

@@ -128,13 +128,10 @@ def displaced(x: np.ndarray, box: float, seed: int, scale: float, bits: int = 16
     rng = np.random.default_rng(seed)
     s = 1 << bits
     step = np.round(rng.normal(0.0, scale, size=x.shape) * s) / s
-    y = x + step
-    y = np.where(y <= 0, y + box, y)
-    y = np.where(y > box, y - box, y)
+    y = np.mod(x + step, box)
     on_edge = rng.random(x.shape) < boundary_frac
     y[on_edge] = np.ceil(y[on_edge])
-    y[y <= 0] += box
-    y[y > box] -= box
+    y[y <= 0] = box
     return y
 
 

@@ -1,0 +1,12 @@
+"""GB300-native MD + MDLG hot path (arXiv:1705.04368, Parsa & Wagner).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/mdlg.h``); this package only marshals arguments to it.
+"""
+from .binding import (MAX_LAGS, MAX_VMAX, POT_LJ_TS, POT_NONE, SITES_ACCUM, SITES_FIELD,
+                      MdlgError, Params, Simulation, bin_snapshots, header_functions,
+                      idealgas_bin, lib)
+
+__all__ = ["MAX_LAGS", "MAX_VMAX", "POT_LJ_TS", "POT_NONE", "SITES_ACCUM", "SITES_FIELD",
+           "MdlgError", "Params", "Simulation", "bin_snapshots", "header_functions",
+           "idealgas_bin", "lib"]

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libmdlg (include/mdlg.h).
+
+Argument marshalling only: every step of the MD + MDLG path runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory (through the
+allocator callback) and streams.  There is no CPU fallback: if the library
+cannot be built or loaded, the import of the first entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+import threading
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+MAX_LAGS = 8
+MAX_VMAX = 15
+MAX_COMBOS = 16
+POT_NONE = 0
+POT_LJ_TS = 1
+SITES_FIELD = 1
+SITES_ACCUM = 2
+
+ERRORS = {0: "MDLG_OK", -1: "MDLG_EINVAL", -2: "MDLG_ENOMEM", -3: "MDLG_ECUDA",
+          -4: "MDLG_EOVERFLOW", -5: "MDLG_ENONFINITE", -6: "MDLG_ETIMEOUT", -7: "MDLG_ENOTIMPL"}
+
+
+class MdlgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({lib().mdlg_strerror(code).decode()})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int64), ("box", ctypes.c_double * 2),
+                ("potential", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("mass", ctypes.c_double),
+                ("rcut", ctypes.c_double), ("dt", ctypes.c_double), ("grid", ctypes.c_double),
+                ("skin", ctypes.c_double), ("sort_every", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("nlags", ctypes.c_int32),
+                ("lag_steps", ctypes.c_int32 * MAX_LAGS), ("vmax", ctypes.c_int32),
+                ("site_mode", ctypes.c_int32), ("stats_every", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("stats_step", ctypes.c_int64),
+                ("kinetic", ctypes.c_double), ("potential", ctypes.c_double),
+                ("virial", ctypes.c_double), ("momentum", ctypes.c_double * 2),
+                ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
+                ("intervals", ctypes.c_int64 * MAX_LAGS), ("status", ctypes.c_int32)]
+
+
+class _Lattice(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_int32 * 2), ("ratio", ctypes.c_int32), ("vmax", ctypes.c_int32)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# Every function the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "mdlg_create": (ctypes.c_int, [ctypes.POINTER(_Params), _P, _P, ctypes.POINTER(_Allocator), _P,
+                                   ctypes.POINTER(_P)]),
+    "mdlg_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "mdlg_stats": (ctypes.c_int, [_P, ctypes.POINTER(_Stats), _P, _P]),
+    "mdlg_get_state": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mdlg_get_sites": (ctypes.c_int, [_P, _P, _P]),
+    "mdlg_reset_counts": (ctypes.c_int, [_P]),
+    "mdlg_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "mdlg_profile": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "mdlg_destroy": (None, [_P]),
+    "mdlg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mdlg_bin": (ctypes.c_int, [ctypes.POINTER(_Lattice), ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "mdlg_idealgas_bin": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P,
+                                         ctypes.c_int32, _P, _P]),
+}
+
+
+def lib():
+    """Load (building if needed) libmdlg.so; raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            h = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = h
+    return _lib
+
+
+def header_functions(path: str) -> list[str]:
+    """Names of the functions declared in a C header (for export checks)."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mdlg_\w+)\s*\(", text,
+                                 flags=re.M)))
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise MdlgError(rc, where)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the library."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.c_alloc = _ALLOC_FN(_alloc)
+        self.c_free = _FREE_FN(_free)
+        self.struct = _Allocator(self.c_alloc, self.c_free, None)
+
+
+@dataclass
+class Params:
+    """Parameters of mdlg_create (see include/mdlg.h, mdlg_params)."""
+    n: int
+    box: float | tuple
+    dx: float
+    dt: float = 0.005
+    lag_steps: Sequence[int] = (50,)
+    potential: int = POT_LJ_TS
+    eps: float = 1.0
+    sigma: float = 1.0
+    mass: float = 1.0
+    rcut: float = 2.5
+    grid: float = 0.5
+    skin: float = 0.5
+    sort_every: int = 0
+    vmax: int = 3
+    site_mode: int = 0
+    stats_every: int = 0
+
+    def to_c(self) -> _Params:
+        p = _Params()
+        p.dim = 2
+        p.n = int(self.n)
+        box = (self.box, self.box) if np.isscalar(self.box) else self.box
+        p.box[0], p.box[1] = float(box[0]), float(box[1])
+        p.potential = int(self.potential)
+        p.eps, p.sigma, p.mass, p.rcut = float(self.eps), float(self.sigma), float(self.mass), float(self.rcut)
+        p.dt, p.grid, p.skin = float(self.dt), float(self.grid), float(self.skin)
+        p.sort_every = int(self.sort_every)
+        p.dx = float(self.dx)
+        lags = list(self.lag_steps)
+        if not 1 <= len(lags) <= MAX_LAGS:
+            raise ValueError("between 1 and 8 lags")
+        p.nlags = len(lags)
+        for i, l in enumerate(lags):
+            p.lag_steps[i] = int(l)
+        p.vmax = int(self.vmax)
+        p.site_mode = int(self.site_mode)
+        p.stats_every = int(self.stats_every)
+        return p
+
+    @property
+    def q1(self) -> int:
+        return (2 * self.vmax + 1) ** 2 + 1
+
+    @property
+    def lattice_cells(self) -> tuple:
+        box = (self.box, self.box) if np.isscalar(self.box) else self.box
+        return (int(round(box[0] / self.dx)), int(round(box[1] / self.dx)))
+
+
+class Simulation:
+    """One MD + MDLG context (mdlg_create ... mdlg_destroy)."""
+
+    def __init__(self, params: Params, x0: np.ndarray, v0: np.ndarray, stream=None,
+                 device: int = 0, torch_memory: bool = True):
+        self.params = params
+        self._lib = lib()
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        if x0.shape != (params.n, 2) or v0.shape != (params.n, 2):
+            raise ValueError("x0 and v0 must be (n, 2)")
+        self._stream = _stream_handle(stream)
+        self._alloc = _TorchAllocator(device, self._stream) if torch_memory else None
+        self._cparams = params.to_c()
+        h = ctypes.c_void_p()
+        rc = self._lib.mdlg_create(ctypes.byref(self._cparams), x0.ctypes.data, v0.ctypes.data,
+                                   ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                   self._stream, ctypes.byref(h))
+        _check(rc, "mdlg_create")
+        self._h = h
+
+    def step(self, nsteps: int):
+        _check(self._lib.mdlg_step(self._h, int(nsteps)), "mdlg_step")
+
+    def stats(self):
+        """(dict of FP64 observables, counts (nlags, Q+1) uint64, f_i (nlags, Q+1))."""
+        out = _Stats()
+        nl, q1 = len(self.params.lag_steps), self.params.q1
+        counts = np.zeros((nl, q1), np.uint64)
+        fi = np.zeros((nl, q1), np.float64)
+        _check(self._lib.mdlg_stats(self._h, ctypes.byref(out), counts.ctypes.data, fi.ctypes.data),
+               "mdlg_stats")
+        d = {k: getattr(out, k) for k in ("step", "stats_step", "kinetic", "potential", "virial",
+                                          "temperature", "pressure", "status")}
+        d["momentum"] = (out.momentum[0], out.momentum[1])
+        d["intervals"] = [out.intervals[i] for i in range(nl)]
+        return d, counts, fi
+
+    def get_state(self, want_force: bool = False):
+        n = self.params.n
+        x = np.empty((n, 2))
+        v = np.empty((n, 2))
+        f = np.empty((n, 2)) if want_force else None
+        _check(self._lib.mdlg_get_state(self._h, x.ctypes.data, v.ctypes.data,
+                                        f.ctypes.data if f is not None else None), "mdlg_get_state")
+        return (x, v, f) if want_force else (x, v)
+
+    def get_sites(self):
+        cx, cy = self.params.lattice_cells
+        sc = np.zeros((cy * cx, self.params.q1), np.uint32)
+        nc = np.zeros(cy * cx, np.uint32)
+        _check(self._lib.mdlg_get_sites(self._h, sc.ctypes.data, nc.ctypes.data), "mdlg_get_sites")
+        return sc, nc
+
+    PROF_KINDS = ("step", "sort", "bin", "sync")
+
+    def profile(self, enable: bool):
+        """Start (True) or stop (False) per-kernel event timing; stop returns
+        {kind: (milliseconds, launches)}."""
+        ms = np.zeros(4)
+        ln = np.zeros(4, np.int64)
+        _check(self._lib.mdlg_profile(self._h, int(enable), ms.ctypes.data, ln.ctypes.data),
+               "mdlg_profile")
+        if enable:
+            return None
+        return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(self.PROF_KINDS)}
+
+    def reset_counts(self):
+        _check(self._lib.mdlg_reset_counts(self._h), "mdlg_reset_counts")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdlg_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bin_snapshots(base: Sequence[int], ratio: int, vmax: int, idx_prev, idx_cur, counts,
+                  ncell=None, field=None, stream=None):
+    """mdlg_bin: tensors on the GPU; idx_* int32 (n, 2); counts int64 (Q+1,) (added to)."""
+    lat = _Lattice()
+    lat.base[0], lat.base[1] = int(base[0]), int(base[1])
+    lat.ratio, lat.vmax = int(ratio), int(vmax)
+    n = 0 if idx_cur is None else int(idx_cur.shape[0])
+    _check(lib().mdlg_bin(ctypes.byref(lat), n, _ptr(idx_prev), _ptr(idx_cur), _ptr(counts),
+                          _ptr(ncell), _ptr(field), _stream_handle(stream)), "mdlg_bin")
+
+
+def idealgas_bin(pos, vel, combos: Sequence[tuple], vmax: int, counts, stream=None):
+    """mdlg_idealgas_bin: pos/vel float32 (n, 2) on the GPU; counts int64 (ncombo, Q+1)."""
+    dxs = np.ascontiguousarray([c[0] for c in combos], dtype=np.float32)
+    dts = np.ascontiguousarray([c[1] for c in combos], dtype=np.float32)
+    n = int(pos.shape[0])
+    _check(lib().mdlg_idealgas_bin(n, _ptr(pos), _ptr(vel), len(combos), dxs.ctypes.data,
+                                   dts.ctypes.data, int(vmax), _ptr(counts),
+                                   _stream_handle(stream)), "mdlg_idealgas_bin")

@@ -1,0 +1,632 @@
+// mdlg_api.cu -- the C ABI of include/mdlg.h: context lifecycle, step
+// scheduling and host <-> device marshalling.  All arithmetic of the method
+// runs in the kernels of mdlg_md.cu and mdlg_bin.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mdlg.h"
+#include "mdlg_kernels.h"
+
+using namespace mdlg;
+
+struct mdlg_ctx {
+    mdlg_params p{};
+    Geom geo{};
+    cudaStream_t stream = nullptr;
+    mdlg_allocator alloc{};
+    bool use_cuda_malloc = true;
+    std::vector<void *> owned;
+    int64_t ncells = 0;
+    int32_t ratio_shift = -1;
+    int32_t q1 = 0;
+    // double-buffered state: position/velocity swap every step, the rest at sorts
+    int32_t *cell[2]{};
+    float2 *cl[2]{};
+    float2 *vel[2]{};
+    int32_t *pid[2]{};
+    uint32_t *lprev[2][kMaxLags]{};
+    int pos_cur = 0, meta_cur = 0;
+    int32_t *cell_start = nullptr;
+    // scratch
+    int32_t *key = nullptr, *slot = nullptr, *count = nullptr, *block_sums = nullptr;
+    unsigned long long *entry = nullptr;
+    double *partials = nullptr;
+    Control *ctl = nullptr;
+    unsigned long long *counts = nullptr;   // nlags x q1
+    uint32_t *site_n = nullptr, *site_counts = nullptr;
+    float2 *vsync = nullptr, *fsync = nullptr;
+    double *xbuf = nullptr, *vbuf = nullptr, *fbuf = nullptr;
+    // host-side schedule
+    int64_t step = 0, last_sort = 0, stats_step = -1;
+    int64_t intervals[kMaxLags]{};
+    int32_t sort_every = 1;
+    float rc = 0.f, round_margin = 0.f;
+    // profiling: event pairs around launch groups
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;
+    int64_t launches[MDLG_PROF_KINDS]{};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return MDLG_OK;
+    fprintf(stderr, "mdlg: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+    return MDLG_ECUDA;
+}
+
+#define MDLG_TRY(expr)                 \
+    do {                               \
+        int rc__ = (expr);             \
+        if (rc__ != MDLG_OK) return rc__; \
+    } while (0)
+
+void *dev_alloc(mdlg_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (c->use_cuda_malloc) {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+    } else {
+        p = c->alloc.alloc(bytes, c->alloc.user);
+    }
+    if (p) c->owned.push_back(p);
+    return p;
+}
+
+template <typename T>
+int alloc_n(mdlg_ctx *c, T **out, size_t count) {
+    *out = static_cast<T *>(dev_alloc(c, sizeof(T) * (count ? count : 1)));
+    return *out ? MDLG_OK : MDLG_ENOMEM;
+}
+
+void free_all(mdlg_ctx *c) {
+    for (void *p : c->owned) {
+        if (c->use_cuda_malloc) cudaFree(p);
+        else c->alloc.free(p, c->alloc.user);
+    }
+    c->owned.clear();
+}
+
+// Launch-group bracketing for mdlg_profile.
+struct ProfScope {
+    mdlg_ctx *c;
+    int kind;
+    bool on;
+    ProfScope(mdlg_ctx *ctx, int k, int nlaunch) : c(ctx), kind(k), on(ctx->prof) {
+        c->launches[k] += nlaunch;
+        if (on) record();
+    }
+    ~ProfScope() {
+        if (on) record();
+    }
+    void record() {
+        if (c->ev_used == c->ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+            c->ev_pool.push_back(e);
+        }
+        cudaEventRecord(c->ev_pool[c->ev_used++], c->stream);
+        c->ev_kind.push_back(kind);
+    }
+};
+
+bool is_pow2(double g) {
+    if (!(g > 0.0) || !std::isfinite(g)) return false;
+    int e = 0;
+    return std::frexp(g, &e) == 0.5;
+}
+
+// value / unit as an exact positive integer, or -1
+int64_t exact_ratio(double value, double unit) {
+    if (!(unit > 0.0) || !(value > 0.0)) return -1;
+    double r = value / unit;
+    double k = std::nearbyint(r);
+    if (k < 1.0 || k > 2147483647.0 || std::fabs(r - k) > 1e-9 * k) return -1;
+    return (int64_t)k;
+}
+
+int log2_exact(int32_t v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int s = 0;
+    while ((1 << s) < v) ++s;
+    return s;
+}
+
+int validate(const mdlg_params *p) {
+    if (!p) return MDLG_EINVAL;
+    if (p->dim != 2 || p->n < 1 || p->n > 2000000000LL) return MDLG_EINVAL;
+    if (p->potential != MDLG_POT_LJ_TS && p->potential != MDLG_POT_NONE) return MDLG_EINVAL;
+    if (!(p->dt > 0.0) || !(p->mass > 0.0) || !is_pow2(p->grid)) return MDLG_EINVAL;
+    if (p->potential == MDLG_POT_LJ_TS &&
+        (!(p->rcut > 0.0) || !(p->sigma > 0.0) || !std::isfinite(p->eps)))
+        return MDLG_EINVAL;
+    if (!(p->skin >= 0.0)) return MDLG_EINVAL;
+    if (p->vmax < 1 || p->vmax > MDLG_MAX_VMAX) return MDLG_EINVAL;
+    if (p->nlags < 1 || p->nlags > MDLG_MAX_LAGS) return MDLG_EINVAL;
+    for (int l = 0; l < p->nlags; ++l)
+        if (p->lag_steps[l] < 1) return MDLG_EINVAL;
+    if (p->site_mode & ~(MDLG_SITES_FIELD | MDLG_SITES_ACCUM)) return MDLG_EINVAL;
+    if (p->site_mode == (MDLG_SITES_FIELD | MDLG_SITES_ACCUM)) return MDLG_EINVAL;
+    if (p->sort_every < 0 || p->stats_every < 0) return MDLG_EINVAL;
+    int64_t ratio = exact_ratio(p->dx, p->grid);
+    if (ratio < 1) return MDLG_EINVAL;
+    for (int a = 0; a < 2; ++a) {
+        int64_t lat = exact_ratio(p->box[a], p->dx);
+        if (lat < 1 || lat > 65535) return MDLG_EINVAL;
+        int64_t lg = exact_ratio(p->box[a], p->grid);
+        if (lg < 1 || lg > 65535) return MDLG_EINVAL;
+        if (p->potential == MDLG_POT_LJ_TS && !(p->rcut < 0.5 * p->box[a])) return MDLG_EINVAL;
+    }
+    return MDLG_OK;
+}
+
+StepArgs step_args(mdlg_ctx *c) {
+    StepArgs a{};
+    a.geo = c->geo;
+    a.n = c->p.n;
+    a.cell = c->cell[c->meta_cur];
+    a.cell_start = c->cell_start;
+    a.cl_in = c->cl[c->pos_cur];
+    a.v_in = c->vel[c->pos_cur];
+    a.cl_out = c->cl[c->pos_cur ^ 1];
+    a.v_out = c->vel[c->pos_cur ^ 1];
+    a.v_sync = c->vsync;
+    a.f_sync = c->fsync;
+    const double rc = c->p.rcut, s = c->p.sigma, e = c->p.eps;
+    a.rc2 = (float)(rc * rc);
+    a.sig2 = (float)(s * s);
+    a.eps24 = (float)(24.0 * e);
+    a.eps4 = (float)(4.0 * e);
+    const double sr6 = std::pow(s / rc, 6.0);
+    a.vshift = (float)(4.0 * e * (sr6 * sr6 - sr6));
+    a.dt = (float)c->p.dt;
+    a.dt_m = (float)(c->p.dt / c->p.mass);
+    a.half_dt_m = (float)(0.5 * c->p.dt / c->p.mass);
+    a.mass = (float)c->p.mass;
+    a.cell_w = (float)(c->geo.k * c->p.grid);
+    a.rc = c->p.potential ? (float)rc : 0.f;
+    a.round_margin = c->round_margin;
+    a.potential = c->p.potential == MDLG_POT_LJ_TS ? 1 : 0;
+    a.partials = c->partials;
+    a.ctl = c->ctl;
+    return a;
+}
+
+StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
+    StateBinArgs b{};
+    b.geo = c->geo;
+    b.n = c->p.n;
+    b.ratio_shift = c->ratio_shift;
+    b.nlags = c->p.nlags;
+    b.mask = mask;
+    b.cell = c->cell[c->meta_cur];
+    b.cl = c->cl[c->pos_cur];
+    for (int l = 0; l < c->p.nlags; ++l) {
+        b.lprev[l] = c->lprev[c->meta_cur][l];
+        b.counts[l] = c->counts + (size_t)l * c->q1;
+    }
+    b.site_n = c->site_n;
+    b.site_counts = c->site_counts;
+    return b;
+}
+
+int do_sort(mdlg_ctx *c) {
+    SortArgs s{};
+    s.geo = c->geo;
+    s.n = c->p.n;
+    s.nlags = c->p.nlags;
+    s.ncells = c->ncells;
+    const int pi = c->pos_cur, mi = c->meta_cur;
+    s.cell_in = c->cell[mi];
+    s.cl_in = c->cl[pi];
+    s.v_in = c->vel[pi];
+    s.pid_in = c->pid[mi];
+    s.cell_out = c->cell[mi ^ 1];
+    s.cl_out = c->cl[pi ^ 1];
+    s.v_out = c->vel[pi ^ 1];
+    s.pid_out = c->pid[mi ^ 1];
+    for (int l = 0; l < c->p.nlags; ++l) {
+        s.lprev_in[l] = c->lprev[mi][l];
+        s.lprev_out[l] = c->lprev[mi ^ 1][l];
+    }
+    s.cell_start = c->cell_start;
+    s.key = c->key;
+    s.slot = c->slot;
+    s.count = c->count;
+    s.entry = c->entry;
+    s.block_sums = c->block_sums;
+    s.ctl = c->ctl;
+    {
+        ProfScope ps(c, MDLG_PROF_SORT, 5);
+        MDLG_TRY(cuda_err(launch_sort(s, c->stream)));
+    }
+    c->pos_cur ^= 1;
+    c->meta_cur ^= 1;
+    c->last_sort = c->step;
+    return MDLG_OK;
+}
+
+int sync_stats(mdlg_ctx *c, bool with_force) {
+    StepArgs a = step_args(c);
+    a.stats = 1;
+    if (!with_force) a.f_sync = c->fsync;   // buffer always present; harmless
+    ProfScope ps(c, MDLG_PROF_SYNC, 1);
+    MDLG_TRY(cuda_err(launch_step(a, kModeSync, c->stream)));
+    c->stats_step = c->step;
+    return MDLG_OK;
+}
+
+int read_status(mdlg_ctx *c, int32_t *status, double *stats) {
+    Control h{};
+    MDLG_TRY(cuda_err(cudaMemcpyAsync(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
+                                      c->stream)));
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    if (status) *status = h.status;
+    if (stats) memcpy(stats, h.stats, sizeof(h.stats));
+    return MDLG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mdlg_strerror(int code) {
+    switch (code) {
+        case MDLG_OK: return "ok";
+        case MDLG_EINVAL: return "invalid argument";
+        case MDLG_ENOMEM: return "device allocation failed";
+        case MDLG_ECUDA: return "CUDA runtime error";
+        case MDLG_EOVERFLOW: return "counter or index range exceeded";
+        case MDLG_ENONFINITE: return "non-finite or out-of-box particle state";
+        case MDLG_ETIMEOUT: return "bounded device wait timed out";
+        case MDLG_ENOTIMPL: return "not implemented";
+        default: return "unknown error";
+    }
+}
+
+int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
+                const mdlg_allocator *allocator, void *stream, mdlg_ctx **out) {
+    if (!out) return MDLG_EINVAL;
+    *out = nullptr;
+    MDLG_TRY(validate(params));
+    if (!x0 || !v0) return MDLG_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->free)) return MDLG_EINVAL;
+
+    mdlg_ctx *c = new (std::nothrow) mdlg_ctx();
+    if (!c) return MDLG_ENOMEM;
+    c->p = *params;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (allocator) {
+        c->alloc = *allocator;
+        c->use_cuda_malloc = false;
+    }
+    const mdlg_params &p = c->p;
+    const int64_t n = p.n;
+
+    // geometry
+    Geom &g = c->geo;
+    g.g = (float)p.grid;
+    g.inv_g = (float)(1.0 / p.grid);
+    g.ratio = (int32_t)exact_ratio(p.dx, p.grid);
+    const double reach = p.potential == MDLG_POT_LJ_TS ? p.rcut + p.skin : 4.0;
+    g.k = (int32_t)std::ceil(reach / p.grid - 1e-12);
+    if (g.k < 1) g.k = 1;
+    for (int a = 0; a < 2; ++a) {
+        g.lg[a] = (int32_t)exact_ratio(p.box[a], p.grid);
+        g.lat[a] = (int32_t)exact_ratio(p.box[a], p.dx);
+        g.nc[a] = g.lg[a] / g.k;
+        if (g.lg[a] % g.ratio) { delete c; return MDLG_EINVAL; }
+    }
+    g.vmax = p.vmax;
+    if (p.potential == MDLG_POT_LJ_TS && (g.nc[0] < 3 || g.nc[1] < 3)) { delete c; return MDLG_EINVAL; }
+    if (g.nc[0] < 1) g.nc[0] = 1;
+    if (g.nc[1] < 1) g.nc[1] = 1;
+    c->ncells = (int64_t)g.nc[0] * g.nc[1];
+    if (c->ncells > (int64_t)4096 * 4096) { delete c; return MDLG_EINVAL; }
+    c->ratio_shift = log2_exact(g.ratio);
+    c->q1 = (2 * p.vmax + 1) * (2 * p.vmax + 1) + 1;
+    c->rc = (float)p.rcut;
+    // rounding slack of one drift update: a few ulps of the largest offset
+    c->round_margin = (float)(4.0 * std::ldexp(1.0, -23) * (2.0 * g.k * p.grid));
+
+    // re-sort interval: half the skin covered at 1.3x the fastest initial speed
+    double vmax0 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double s2 = v0[2 * i] * v0[2 * i] + v0[2 * i + 1] * v0[2 * i + 1];
+        if (s2 > vmax0) vmax0 = s2;
+    }
+    vmax0 = std::sqrt(vmax0);
+    if (p.sort_every > 0) {
+        c->sort_every = p.sort_every;
+    } else {
+        const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
+        const double v = std::fmax(vmax0 * 1.3, 1e-12);
+        double k = std::floor(0.5 * skin_eff / (v * p.dt));
+        c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
+    }
+
+    int rc = MDLG_OK;
+    auto fail = [&](int code) {
+        free_all(c);
+        delete c;
+        return code;
+    };
+    const size_t N = (size_t)n;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N)) ||
+            (rc = alloc_n(c, &c->vel[b], N)) || (rc = alloc_n(c, &c->pid[b], N)))
+            return fail(rc);
+        for (int l = 0; l < p.nlags; ++l)
+            if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
+    }
+    const int64_t nb = sort_scratch_blocks(c->ncells);
+    const int64_t step_blocks = (n + 255) / 256;
+    if ((rc = alloc_n(c, &c->cell_start, (size_t)c->ncells + 1)) ||
+        (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
+        (rc = alloc_n(c, &c->count, (size_t)c->ncells)) ||
+        (rc = alloc_n(c, &c->block_sums, (size_t)nb)) || (rc = alloc_n(c, &c->entry, N)) ||
+        (rc = alloc_n(c, &c->partials, (size_t)step_blocks * 5)) ||
+        (rc = alloc_n(c, &c->ctl, 1)) ||
+        (rc = alloc_n(c, &c->counts, (size_t)p.nlags * c->q1)) ||
+        (rc = alloc_n(c, &c->vsync, N)) || (rc = alloc_n(c, &c->fsync, N)) ||
+        (rc = alloc_n(c, &c->xbuf, 2 * N)) || (rc = alloc_n(c, &c->vbuf, 2 * N)) ||
+        (rc = alloc_n(c, &c->fbuf, 2 * N)))
+        return fail(rc);
+    if (p.site_mode) {
+        const size_t sites = (size_t)g.lat[0] * g.lat[1];
+        if ((rc = alloc_n(c, &c->site_n, sites)) || (rc = alloc_n(c, &c->site_counts, sites * c->q1)))
+            return fail(rc);
+    }
+
+    cudaStream_t s = c->stream;
+    auto chk = [&](cudaError_t e) { return cuda_err(e); };
+    if ((rc = chk(cudaMemsetAsync(c->ctl, 0, sizeof(Control), s))) ||
+        (rc = chk(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * p.nlags * c->q1, s))))
+        return fail(rc);
+    for (int b = 0; b < 2; ++b)
+        for (int l = 0; l < p.nlags; ++l)
+            if ((rc = chk(cudaMemsetAsync(c->lprev[b][l], 0, sizeof(uint32_t) * N, s))))
+                return fail(rc);
+    if (p.site_mode) {
+        const size_t sites = (size_t)g.lat[0] * g.lat[1];
+        if ((rc = chk(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, s))) ||
+            (rc = chk(cudaMemsetAsync(c->site_counts, 0, sizeof(uint32_t) * sites * c->q1, s))))
+            return fail(rc);
+    }
+    // upload (pageable host memory: the copy completes before the call returns)
+    if ((rc = chk(cudaMemcpyAsync(c->xbuf, x0, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s))) ||
+        (rc = chk(cudaMemcpyAsync(c->vbuf, v0, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s))))
+        return fail(rc);
+    // pack into buffer 1 (original order), sort into buffer 0
+    c->pos_cur = 1;
+    c->meta_cur = 1;
+    if ((rc = chk(launch_pack(g, n, c->xbuf, c->vbuf, c->cell[1], c->cl[1], c->vel[1], c->pid[1],
+                              c->ctl, s))))
+        return fail(rc);
+    if ((rc = do_sort(c))) return fail(rc);
+    // v_{-1/2} = v_0 - F(x_0) dt / (2m), in place; FP64 observables of step 0
+    StepArgs a = step_args(c);
+    a.v_out = c->vel[c->pos_cur];
+    a.stats = 1;
+    if ((rc = chk(launch_step(a, kModeInit, s)))) return fail(rc);
+    c->stats_step = 0;
+    // every lag starts from the lattice cells at t = 0
+    StateBinArgs b = bin_args(c, (1u << p.nlags) - 1u);
+    if ((rc = chk(launch_bin_seed(b, s)))) return fail(rc);
+    if ((rc = chk(cudaStreamSynchronize(s)))) return fail(rc);
+    int32_t status = 0;
+    if ((rc = read_status(c, &status, nullptr))) return fail(rc);
+    if (status) return fail(status);
+    *out = c;
+    return MDLG_OK;
+}
+
+int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
+    if (!c || nsteps < 0) return MDLG_EINVAL;
+    const mdlg_params &p = c->p;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        if (c->step - c->last_sort >= c->sort_every) MDLG_TRY(do_sort(c));
+        StepArgs a = step_args(c);
+        a.stats = (p.stats_every > 0 && c->step % p.stats_every == 0) ? 1 : 0;
+        {
+            ProfScope ps(c, MDLG_PROF_STEP, 1);
+            MDLG_TRY(cuda_err(launch_step(a, kModeStep, c->stream)));
+        }
+        if (a.stats) c->stats_step = c->step;
+        c->pos_cur ^= 1;
+        c->step += 1;
+        uint32_t mask = 0;
+        for (int l = 0; l < p.nlags; ++l)
+            if (c->step % p.lag_steps[l] == 0) mask |= 1u << l;
+        if (mask) {
+            if ((mask & 1u) && (p.site_mode & MDLG_SITES_FIELD)) {
+                const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+                MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, c->stream)));
+                MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts, 0,
+                                                  sizeof(uint32_t) * sites * c->q1, c->stream)));
+            }
+            StateBinArgs b = bin_args(c, mask);
+            if (!(mask & 1u)) { b.site_n = nullptr; b.site_counts = nullptr; }
+            {
+                ProfScope ps(c, MDLG_PROF_BIN, 1);
+                MDLG_TRY(cuda_err(launch_bin_state(b, c->stream)));
+            }
+            for (int l = 0; l < p.nlags; ++l)
+                if ((mask >> l) & 1u) c->intervals[l] += 1;
+        }
+    }
+    return MDLG_OK;
+}
+
+int mdlg_stats(mdlg_ctx *c, mdlg_stats_out *out, uint64_t *counts, double *fi) {
+    if (!c || !out) return MDLG_EINVAL;
+    if (c->stats_step != c->step) MDLG_TRY(sync_stats(c, false));
+    double st[8];
+    int32_t status = 0;
+    MDLG_TRY(read_status(c, &status, st));
+    const mdlg_params &p = c->p;
+    memset(out, 0, sizeof(*out));
+    out->step = c->step;
+    out->stats_step = c->stats_step;
+    out->kinetic = st[0];
+    out->potential = st[1];
+    out->virial = st[2];
+    out->momentum[0] = st[3];
+    out->momentum[1] = st[4];
+    out->temperature = p.n > 1 ? st[0] / (double)(p.n - 1) : 0.0;
+    out->pressure = (st[0] + 0.5 * st[2]) / (p.box[0] * p.box[1]);
+    for (int l = 0; l < p.nlags; ++l) out->intervals[l] = c->intervals[l];
+    out->status = status;
+    if (counts || fi) {
+        std::vector<unsigned long long> h((size_t)p.nlags * c->q1);
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(h.data(), c->counts, sizeof(unsigned long long) * h.size(),
+                                          cudaMemcpyDeviceToHost, c->stream)));
+        MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+        for (int l = 0; l < p.nlags; ++l)
+            for (int i = 0; i < c->q1; ++i) {
+                const size_t k = (size_t)l * c->q1 + i;
+                if (counts) counts[k] = h[k];
+                if (fi) {
+                    const double denom = (double)p.n * (double)c->intervals[l];
+                    fi[k] = denom > 0 ? (double)h[k] / denom : 0.0;
+                }
+            }
+    }
+    return status ? status : MDLG_OK;
+}
+
+int mdlg_get_state(mdlg_ctx *c, double *x, double *v, double *f) {
+    if (!c) return MDLG_EINVAL;
+    const size_t N = (size_t)c->p.n;
+    if (v || f) {
+        StepArgs a = step_args(c);
+        a.stats = 1;
+        MDLG_TRY(cuda_err(launch_step(a, kModeSync, c->stream)));
+        c->stats_step = c->step;
+    }
+    MDLG_TRY(cuda_err(launch_unpack(c->geo, c->p.n, c->cell[c->meta_cur], c->cl[c->pos_cur],
+                                    c->vsync, c->fsync, c->pid[c->meta_cur], x ? c->xbuf : nullptr,
+                                    v ? c->vbuf : nullptr, f ? c->fbuf : nullptr, c->stream)));
+    if (x) MDLG_TRY(cuda_err(cudaMemcpyAsync(x, c->xbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
+    if (v) MDLG_TRY(cuda_err(cudaMemcpyAsync(v, c->vbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
+    if (f) MDLG_TRY(cuda_err(cudaMemcpyAsync(f, c->fbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    return MDLG_OK;
+}
+
+int mdlg_get_sites(mdlg_ctx *c, uint32_t *site_counts, uint32_t *ncell) {
+    if (!c) return MDLG_EINVAL;
+    if (!c->p.site_mode) return MDLG_EINVAL;
+    const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+    if (site_counts)
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(site_counts, c->site_counts, sizeof(uint32_t) * sites * c->q1,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+    if (ncell)
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(ncell, c->site_n, sizeof(uint32_t) * sites,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+    return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+int mdlg_reset_counts(mdlg_ctx *c) {
+    if (!c) return MDLG_EINVAL;
+    MDLG_TRY(cuda_err(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * c->p.nlags * c->q1,
+                                      c->stream)));
+    if (c->p.site_mode) {
+        const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+        MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, c->stream)));
+        MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts, 0, sizeof(uint32_t) * sites * c->q1, c->stream)));
+    }
+    for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = 0;
+    return MDLG_OK;
+}
+
+int mdlg_adjoint(mdlg_ctx *c, const double *dloss, double *grad_eps, double *grad_sigma,
+                 double *grad_x0, double *grad_v0) {
+    (void)c; (void)dloss; (void)grad_eps; (void)grad_sigma; (void)grad_x0; (void)grad_v0;
+    return MDLG_ENOTIMPL;
+}
+
+int mdlg_profile(mdlg_ctx *c, int enable, double *ms, int64_t *launches) {
+    if (!c) return MDLG_EINVAL;
+    if (enable) {
+        c->prof = true;
+        c->ev_used = 0;
+        c->ev_kind.clear();
+        for (int k = 0; k < MDLG_PROF_KINDS; ++k) c->launches[k] = 0;
+        return MDLG_OK;
+    }
+    c->prof = false;
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    double acc[MDLG_PROF_KINDS] = {0, 0, 0, 0};
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float t = 0.f;
+        MDLG_TRY(cuda_err(cudaEventElapsedTime(&t, c->ev_pool[i], c->ev_pool[i + 1])));
+        acc[c->ev_kind[i]] += t;
+    }
+    for (int k = 0; k < MDLG_PROF_KINDS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = c->launches[k];
+    }
+    c->ev_used = 0;
+    c->ev_kind.clear();
+    return MDLG_OK;
+}
+
+void mdlg_destroy(mdlg_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    free_all(c);
+    delete c;
+}
+
+int mdlg_bin(const mdlg_lattice *lat, int64_t n, const int32_t *idx_prev, const int32_t *idx_cur,
+             uint64_t *counts, uint32_t *ncell, uint32_t *field, void *stream) {
+    if (!lat || n < 0 || !counts) return MDLG_EINVAL;
+    if (n > 0 && (!idx_prev || !idx_cur)) return MDLG_EINVAL;
+    if (lat->ratio < 1 || lat->vmax < 1 || lat->vmax > MDLG_MAX_VMAX) return MDLG_EINVAL;
+    LatticeArgs la{};
+    for (int a = 0; a < 2; ++a) {
+        if (lat->base[a] < 1 || lat->base[a] % lat->ratio) return MDLG_EINVAL;
+        la.base[a] = lat->base[a];
+        la.lat[a] = lat->base[a] / lat->ratio;
+    }
+    la.ratio = lat->ratio;
+    la.shift = log2_exact(lat->ratio);
+    la.vmax = lat->vmax;
+    if (n == 0) return MDLG_OK;
+    return cuda_err(launch_bin_snapshots(la, n, idx_prev, idx_cur,
+                                         reinterpret_cast<unsigned long long *>(counts), ncell,
+                                         field, static_cast<cudaStream_t>(stream)));
+}
+
+int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t ncombo,
+                      const float *dxs, const float *dts, int32_t vmax, uint64_t *counts,
+                      void *stream) {
+    if (n < 0 || !counts || !dxs || !dts) return MDLG_EINVAL;
+    if (ncombo < 1 || ncombo > MDLG_MAX_COMBOS || vmax < 1 || vmax > MDLG_MAX_VMAX) return MDLG_EINVAL;
+    if (n > 0 && (!pos || !vel)) return MDLG_EINVAL;
+    IdealGasArgs ga{};
+    ga.ncombo = ncombo;
+    ga.vmax = vmax;
+    for (int k = 0; k < ncombo; ++k) {
+        if (!(dxs[k] > 0.f) || !std::isfinite(dxs[k]) || !std::isfinite(dts[k])) return MDLG_EINVAL;
+        ga.dx[k] = dxs[k];
+        ga.dt[k] = dts[k];
+        ga.pow2[k] = is_pow2((double)dxs[k]) ? 1 : 0;
+        ga.inv_dx[k] = ga.pow2[k] ? (float)(1.0 / (double)dxs[k]) : 0.f;
+    }
+    if (n == 0) return MDLG_OK;
+    return cuda_err(launch_idealgas_bin(ga, n, pos, vel, reinterpret_cast<unsigned long long *>(counts),
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// mdlg_device.cuh -- device-side types and helpers shared by the MDLG kernels.
+//
+// State layout (device, structure of arrays, sorted by neighbour ("MD") cell):
+//   cell[j]  int32   MD cell the particle was sorted into (row-major, x fastest)
+//   cl[j]    float2  position relative to that cell's origin, in length units
+//   vel[j]   float2  velocity (half-step velocity v_{n-1/2} between steps)
+//   pid[j]   int32   original particle number
+//   lprev[l][j] uint32 lattice cell of the particle at the last binning of
+//            lag l, packed (c_y << 16) | c_x
+// A cell's origin is an integer number of base cells g (g a power of two), so
+// every position is "integer + binary32 offset": the base cell of a particle,
+// and therefore its lattice cell, is exact integer arithmetic, and pair
+// separations are differences of small offsets plus a small integer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdlg {
+
+constexpr int kMaxLags = 8;
+constexpr int kMaxVmax = 15;
+
+// Geometry of the base grid, the MD cells and the MDLG lattice.
+struct Geom {
+    int32_t lg[2];     // base cells per axis (L / g)
+    int32_t nc[2];     // MD cells per axis; cell c spans base cells [c k, (c+1) k),
+                       // the last one also takes the remainder lg - nc k
+    int32_t k;         // base cells per MD cell
+    float g;           // base grid spacing (power of two)
+    float inv_g;       // 1 / g (exact)
+    int32_t ratio;     // lattice spacing dx / g
+    int32_t lat[2];    // lattice cells per axis
+    int32_t vmax;      // window half-width V
+};
+
+// Wrap an integer base-cell difference into [-lg/2, lg/2).
+__device__ __forceinline__ int32_t wrap_half(int32_t d, int32_t lg) {
+    if (d >= (lg >> 1)) d -= lg;
+    if (d < -(lg >> 1)) d += lg;
+    return d;
+}
+
+__device__ __forceinline__ int32_t wrap_mod(int32_t d, int32_t m) {
+    if (d < 0) d += m;
+    if (d >= m) d -= m;
+    return d;
+}
+
+// Base cell of a particle: the cell (b g, (b+1) g] that holds origin + cl.
+// cl / g is exact (g a power of two), ceil(t) - 1 is the left-open rule.  The
+// result is reduced modulo lg, so it is a valid index for any input (a
+// non-finite offset converts to an arbitrary integer and is flagged elsewhere).
+__device__ __forceinline__ int32_t base_cell(int32_t origin, float cl, float inv_g, int32_t lg) {
+    const float t = fminf(fmaxf(ceilf(cl * inv_g), -1.0e9f), 1.0e9f);
+    int32_t b = (origin + (int32_t)t - 1) % lg;
+    return b < 0 ? b + lg : b;
+}
+
+// Lattice displacement reduced into (-C/2, C/2].
+__device__ __forceinline__ int32_t lattice_disp(int32_t d, int32_t C) {
+    int32_t r = d % C;
+    if (r < 0) r += C;
+    if (r > (C >> 1)) r -= C;
+    return r;
+}
+
+// Velocity index of a lattice displacement (vx, vy); Q for outside the window.
+__device__ __forceinline__ int32_t vel_index(int32_t vx, int32_t vy, int32_t vmax) {
+    const int32_t w = 2 * vmax + 1;
+    if (vx < -vmax || vx > vmax || vy < -vmax || vy > vmax) return w * w;
+    return (vy + vmax) * w + (vx + vmax);
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int32_t cx, int32_t cy) {
+    return ((uint32_t)cy << 16) | (uint32_t)cx;
+}
+
+// Add one count to a block-shared histogram.  Most particles of a short
+// coarse step land in the rest velocity, so the lanes that do are counted by
+// one ballot and a single shared atomic; the rest add individually.
+__device__ __forceinline__ void hist_add(uint32_t *sh, int32_t bin, int32_t center, bool active) {
+    const unsigned full = 0xffffffffu;
+    unsigned rest = __ballot_sync(full, active && bin == center);
+    if (rest && (threadIdx.x & 31) == (unsigned)(__ffs(rest) - 1)) atomicAdd(&sh[center], (uint32_t)__popc(rest));
+    if (active && bin != center) atomicAdd(&sh[bin], 1u);
+}
+
+}  // namespace mdlg

@@ -1,0 +1,129 @@
+// mdlg_kernels.h -- argument blocks and launchers of the MDLG kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mdlg_device.cuh"
+
+namespace mdlg {
+
+// ---- binning ---------------------------------------------------------------
+struct LatticeArgs {
+    int32_t base[2];   // base cells per axis
+    int32_t ratio;     // base cells per lattice cell
+    int32_t shift;     // log2(ratio) if a power of two, else -1
+    int32_t lat[2];    // lattice cells per axis
+    int32_t vmax;
+};
+
+struct IdealGasArgs {
+    int32_t ncombo;
+    int32_t vmax;
+    float dx[16], dt[16], inv_dx[16];
+    int32_t pow2[16];
+};
+
+struct StateBinArgs {
+    Geom geo;
+    int64_t n;
+    int32_t ratio_shift;   // log2(ratio) or -1
+    int32_t nlags;
+    uint32_t mask;         // lags binned by this launch
+    const int32_t *cell;
+    const float2 *cl;
+    uint32_t *lprev[kMaxLags];
+    unsigned long long *counts[kMaxLags];
+    uint32_t *site_n;       // lag 0 per-site N(x,t), or null
+    uint32_t *site_counts;  // lag 0 per-site n_i(x,t), or null
+};
+
+int hist_grid(int64_t n, int threads);
+cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t *prev,
+                                 const int32_t *cur, unsigned long long *counts, uint32_t *ncell,
+                                 uint32_t *field, cudaStream_t s);
+cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *pos,
+                                const float *vel, unsigned long long *counts, cudaStream_t s);
+cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s);
+cudaError_t launch_bin_seed(const StateBinArgs &sa, cudaStream_t s);
+
+// ---- molecular dynamics ------------------------------------------------------
+// Device control block of one context (one allocation).
+struct Control {
+    float dbound;              // bound on any particle's distance outside its MD cell
+    uint32_t vmax2_bits;       // max |v|^2 of the running step (float bits)
+    uint32_t done;             // blocks finished in the running launch
+    int32_t status;            // first device-side error (MDLG_E* value) or 0
+    double stats[8];           // ke, pe, virial, px, py of the last stats launch
+};
+
+enum StepMode : int32_t {
+    kModeStep = 0,   // F(x_n); v_{n+1/2} = v_{n-1/2} + F dt/m; x_{n+1} = x_n + v dt
+    kModeInit = 1,   // F(x_0); v_{-1/2} = v_0 - F dt/(2m)        (positions kept)
+    kModeSync = 2,   // F(x_n); v_n = v_{n-1/2} + F dt/(2m) into sync buffers
+};
+
+struct StepArgs {
+    Geom geo;
+    int64_t n;
+    const int32_t *cell;
+    const int32_t *cell_start;  // nc[0]*nc[1] + 1
+    const float2 *cl_in;
+    const float2 *v_in;
+    float2 *cl_out;             // kModeStep
+    float2 *v_out;              // kModeStep / kModeInit
+    float2 *v_sync;             // kModeSync: v_n
+    float2 *f_sync;             // kModeSync: F(x_n), or null
+    float rc2, sig2, eps24, eps4, vshift;
+    float dt, dt_m, half_dt_m, mass;
+    float cell_w;               // k g: narrowest MD cell width
+    float rc;
+    float round_margin;         // per-step slack added to the displacement bound
+    int32_t potential;          // 0 none, 1 LJ
+    int32_t stats;              // 1: FP64 reductions into partials
+    double *partials;           // gridDim.x x 5
+    Control *ctl;
+};
+
+cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);
+
+struct SortArgs {
+    Geom geo;
+    int64_t n;
+    int32_t nlags;
+    int64_t ncells;
+    // current state
+    const int32_t *cell_in;
+    const float2 *cl_in;
+    const float2 *v_in;
+    const int32_t *pid_in;
+    const uint32_t *lprev_in[kMaxLags];
+    // sorted state
+    int32_t *cell_out;
+    float2 *cl_out;
+    float2 *v_out;
+    int32_t *pid_out;
+    uint32_t *lprev_out[kMaxLags];
+    int32_t *cell_start;     // ncells + 1
+    // scratch
+    int32_t *key;            // n
+    int32_t *slot;           // n
+    int32_t *count;          // ncells
+    unsigned long long *entry;  // n
+    int32_t *block_sums;     // scan partials
+    Control *ctl;
+};
+
+int64_t sort_scratch_blocks(int64_t ncells);
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
+
+// Upload conversion: FP64 positions -> (cell, cl) in original order (unsorted).
+cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
+                        int32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                        cudaStream_t s);
+// Download conversion: sorted state -> FP64 arrays in original order.
+cudaError_t launch_unpack(const Geom &geo, int64_t n, const int32_t *cell, const float2 *cl,
+                          const float2 *vsync, const float2 *fsync, const int32_t *pid,
+                          double *x, double *v, double *f, cudaStream_t s);
+
+}  // namespace mdlg

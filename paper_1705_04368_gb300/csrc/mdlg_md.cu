@@ -1,0 +1,427 @@
+// mdlg_md.cu -- Lennard-Jones velocity-Verlet step, neighbour-cell sort and the
+// FP64 reductions (Newton equations of Sec. III and potential of Sec. IV of
+// arXiv:1705.04368).
+//
+// Time stepping is the leapfrog form of velocity Verlet: the stored velocity is
+// the half-step velocity v_{n-1/2}, and one launch per MD step does
+//     F_n = F(x_n),  v_{n+1/2} = v_{n-1/2} + F_n dt/m,  x_{n+1} = x_n + v_{n+1/2} dt,
+// which reproduces the kick-drift-kick positions exactly in exact arithmetic;
+// the integer-step velocity v_n = v_{n-1/2} + F_n dt/(2m) is formed when it is
+// needed (statistics, state download).
+//
+// Neighbour search: particles are sorted by MD cell (side k g >= rc + skin).
+// Between sorts a particle drifts at most D outside its cell (D tracked on the
+// device from the largest speed of every step), so every pair closer than rc
+// lies within R = ceil((rc + 2D) / (k g)) cells; R = 1 while 2D <= skin.
+#include "mdlg_kernels.h"
+
+namespace mdlg {
+
+namespace {
+
+constexpr int kStepThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 cells per scan block
+constexpr int kStatsN = 5;
+constexpr int kErrNonFinite = -5;
+constexpr int kErrOverflow = -4;
+
+__device__ __forceinline__ void set_status(Control *ctl, int code) {
+    atomicCAS(&ctl->status, 0, code);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Stencil bounds of one axis: [-R, R], or every cell once if that would wrap.
+__device__ __forceinline__ void stencil(int R, int nc, int &lo, int &hi) {
+    if (2 * R + 1 <= nc) { lo = -R; hi = R; }
+    else { lo = -(nc >> 1); hi = lo + nc - 1; }
+}
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+    const Geom &geo = a.geo;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < a.n;
+
+    // Neighbour-cell radius for the displacement bound of the input positions.
+    const float D = a.ctl->dbound;
+    const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
+    // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
+    const int R = (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
+    if (a.potential && threadIdx.x == 0 && blockIdx.x == 0 &&
+        (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1]))
+        set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
+    int lox, hix, loy, hiy;
+    stencil(R, geo.nc[0], lox, hix);
+    stencil(R, geo.nc[1], loy, hiy);
+
+    float fx = 0.f, fy = 0.f;
+    double pe = 0.0, vir = 0.0;
+    float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+    if (act) {
+        const int32_t c = a.cell[i];
+        p = a.cl_in[i];
+        v = a.v_in[i];
+        if (a.potential) {
+            const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
+            for (int oy = loy; oy <= hiy; ++oy) {
+                const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
+                const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
+                for (int ox = lox; ox <= hix; ++ox) {
+                    const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
+                    const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
+                    const int32_t cn = ny * geo.nc[0] + nx;
+                    const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+                    for (int32_t j = s; j < e; ++j) {
+                        if (j == i) continue;
+                        const float2 q = __ldg(a.cl_in + j);
+                        // x_i - x_j = (cl_i - cl_j) - (origin_j - origin_i)
+                        const float dx = (p.x - q.x) - odx;
+                        const float dy = (p.y - q.y) - ody;
+                        const float r2 = fmaf(dx, dx, dy * dy);
+                        if (r2 < a.rc2) {
+                            const float ir2 = __frcp_rn(r2);
+                            const float sr2 = a.sig2 * ir2;
+                            const float sr6 = sr2 * sr2 * sr2;
+                            // -(1/r) dV/dr = 24 eps (2 s^12 - s^6) / r^2
+                            const float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+                            fx = fmaf(fs, dx, fx);
+                            fy = fmaf(fs, dy, fy);
+                            if (STATS) {
+                                pe += 0.5 * (double)(a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift);
+                                vir += 0.5 * (double)fs * (double)r2;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    float2 vn = v;   // velocity at the integer step (statistics)
+    float vmax2 = 0.f;
+    if (act) {
+        if (MODE == kModeStep) {
+            vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
+            const float2 vh = make_float2(fmaf(fx, a.dt_m, v.x), fmaf(fy, a.dt_m, v.y));
+            const float2 pn = make_float2(fmaf(vh.x, a.dt, p.x), fmaf(vh.y, a.dt, p.y));
+            a.v_out[i] = vh;
+            a.cl_out[i] = pn;
+            vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
+            if (!(vmax2 < 3.0e38f) || !(fabsf(pn.x) < 3.0e38f) || !(fabsf(pn.y) < 3.0e38f))
+                set_status(a.ctl, kErrNonFinite);
+        } else if (MODE == kModeInit) {
+            vn = v;
+            a.v_out[i] = make_float2(fmaf(-fx, a.half_dt_m, v.x), fmaf(-fy, a.half_dt_m, v.y));
+        } else {
+            vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
+            a.v_sync[i] = vn;
+            if (a.f_sync) a.f_sync[i] = make_float2(fx, fy);
+        }
+    }
+
+    __shared__ double s_red[kStepThreads / 32][kStatsN];
+    __shared__ float s_max[kStepThreads / 32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MODE == kModeStep) {
+        const float m = warp_max(vmax2);
+        if (lane == 0) s_max[warp] = m;
+    }
+    if (STATS) {
+        double ke = 0.0, px = 0.0, py = 0.0;
+        if (act) {
+            const double vx = vn.x, vy = vn.y;
+            ke = 0.5 * (double)a.mass * (vx * vx + vy * vy);
+            px = (double)a.mass * vx;
+            py = (double)a.mass * vy;
+        }
+        const double r[kStatsN] = {warp_sum(ke), warp_sum(pe), warp_sum(vir), warp_sum(px),
+                                   warp_sum(py)};
+        if (lane == 0)
+            for (int k = 0; k < kStatsN; ++k) s_red[warp][k] = r[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (MODE == kModeStep) {
+            float m = 0.f;
+            for (int w = 0; w < kStepThreads / 32; ++w) m = fmaxf(m, s_max[w]);
+            atomicMax(&a.ctl->vmax2_bits, __float_as_uint(m));
+        }
+        if (STATS) {
+            for (int k = 0; k < kStatsN; ++k) {
+                double t = 0.0;
+                for (int w = 0; w < kStepThreads / 32; ++w) t += s_red[w][k];
+                a.partials[(size_t)blockIdx.x * kStatsN + k] = t;
+            }
+        }
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctl->done, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // Last block of the launch: every other block has published its results.
+    __threadfence();
+    if (STATS) {
+        // Fixed-order sum over block partials, one warp per quantity: deterministic.
+        if (warp < kStatsN) {
+            double t = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32)
+                t += ((volatile double *)a.partials)[(size_t)b * kStatsN + warp];
+            t = warp_sum(t);
+            if (lane == 0) a.ctl->stats[warp] = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (MODE == kModeStep) {
+            const uint32_t bits = atomicExch(&a.ctl->vmax2_bits, 0u);
+            const float vmax = sqrtf(__uint_as_float(bits));
+            a.ctl->dbound = D + vmax * a.dt * 1.000001f + a.round_margin;
+        }
+        a.ctl->done = 0u;
+    }
+}
+
+// ---- neighbour-cell sort (stable counting sort keyed by MD cell, particle
+//      number order inside a cell) -------------------------------------------
+
+__global__ void k_sort_key(SortArgs a) {
+    const Geom &geo = a.geo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const int32_t c = a.cell_in[i];
+        const float2 p = a.cl_in[i];
+        const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
+        const int32_t bx = base_cell(cx * geo.k, p.x, geo.inv_g, geo.lg[0]);
+        const int32_t by = base_cell(cy * geo.k, p.y, geo.inv_g, geo.lg[1]);
+        int32_t nx = bx / geo.k, ny = by / geo.k;
+        nx = nx < geo.nc[0] ? nx : geo.nc[0] - 1;
+        ny = ny < geo.nc[1] ? ny : geo.nc[1] - 1;
+        const int32_t key = ny * geo.nc[0] + nx;
+        a.key[i] = key;
+        a.slot[i] = atomicAdd(&a.count[key], 1);
+    }
+}
+
+// Exclusive scan of one 4096-entry chunk in place; chunk total to block_sums.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t *data, int64_t base, int64_t m,
+                                                        int32_t *total) {
+    __shared__ int32_t s_warp[kScanThreads / 32];
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+    const int64_t o = base + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (o + k < m) ? data[o + k] : 0;
+        sum += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = s_warp[lane];
+        int32_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += t;
+        }
+        s_warp[lane] = wi - w;   // exclusive warp offsets
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    int32_t run = s_warp[warp] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (o + k < m) data[o + k] = run;
+        run += v[k];
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(int32_t *count, int64_t m,
+                                                             int32_t *block_sums) {
+    __shared__ int32_t total;
+    block_exclusive_scan(count, (int64_t)blockIdx.x * kScanChunk, m, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int32_t *block_sums, int64_t nb) {
+    __shared__ int32_t total;
+    block_exclusive_scan(block_sums, 0, nb, &total);
+}
+
+__device__ __forceinline__ int32_t cell_begin(const SortArgs &a, int64_t c) {
+    return a.count[c] + a.block_sums[c / kScanChunk];
+}
+
+__global__ void k_sort_place(SortArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const int32_t key = a.key[i];
+        const int64_t at = (int64_t)cell_begin(a, key) + a.slot[i];
+        a.entry[at] = ((unsigned long long)(uint32_t)a.pid_in[i] << 32) | (uint32_t)i;
+    }
+}
+
+// One thread per MD cell: order the cell's particles by particle number, then
+// gather them from the old order, re-expressing positions against the new
+// cell's origin.
+__global__ void k_sort_cells(SortArgs a) {
+    const Geom &geo = a.geo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.cell_start[a.ncells] = (int32_t)a.n;
+        a.ctl->dbound = 0.0f;
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncells; c += stride) {
+        const int32_t s = cell_begin(a, c);
+        const int32_t e = (c + 1 < a.ncells) ? cell_begin(a, c + 1) : (int32_t)a.n;
+        a.cell_start[c] = s;
+        const int32_t m = e - s;
+        const int32_t cx = (int32_t)(c % geo.nc[0]), cy = (int32_t)(c / geo.nc[0]);
+        for (int32_t r = 0; r < m; ++r) {
+            // rank r: the r-th smallest particle number in the cell
+            const unsigned long long er = a.entry[s + r];
+            int32_t rank = 0;
+            for (int32_t t = 0; t < m; ++t) rank += (a.entry[s + t] >> 32) < (er >> 32);
+            const int32_t from = (int32_t)(er & 0xffffffffu);
+            const int32_t to = s + rank;
+            const int32_t oc = a.cell_in[from];
+            const int32_t ocx = oc % geo.nc[0], ocy = oc / geo.nc[0];
+            const float2 p = a.cl_in[from];
+            const float sx = (float)wrap_half((ocx - cx) * geo.k, geo.lg[0]) * geo.g;
+            const float sy = (float)wrap_half((ocy - cy) * geo.k, geo.lg[1]) * geo.g;
+            a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
+            a.v_out[to] = a.v_in[from];
+            a.pid_out[to] = a.pid_in[from];
+            a.cell_out[to] = (int32_t)c;
+            for (int l = 0; l < a.nlags; ++l) a.lprev_out[l][to] = a.lprev_in[l][from];
+        }
+    }
+}
+
+// ---- upload / download conversions ----------------------------------------
+
+__global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, int32_t *cell,
+                       float2 *cl, float2 *vel, int32_t *pid, Control *ctl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double g = geo.g;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double px = x[2 * i], py = x[2 * i + 1];
+        const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
+        if (!(px > 0.0 && px <= L0 && py > 0.0 && py <= L1) || !isfinite(v[2 * i]) ||
+            !isfinite(v[2 * i + 1])) {
+            set_status(ctl, kErrNonFinite);
+        }
+        // base cell b with b g < x <= (b+1) g
+        int64_t bx = (int64_t)ceil(px / g) - 1, by = (int64_t)ceil(py / g) - 1;
+        bx = bx < 0 ? 0 : (bx >= geo.lg[0] ? geo.lg[0] - 1 : bx);
+        by = by < 0 ? 0 : (by >= geo.lg[1] ? geo.lg[1] - 1 : by);
+        int32_t cx = (int32_t)(bx / geo.k), cy = (int32_t)(by / geo.k);
+        cx = cx < geo.nc[0] ? cx : geo.nc[0] - 1;
+        cy = cy < geo.nc[1] ? cy : geo.nc[1] - 1;
+        cell[i] = cy * geo.nc[0] + cx;
+        cl[i] = make_float2((float)(px - (double)cx * geo.k * g), (float)(py - (double)cy * geo.k * g));
+        vel[i] = make_float2((float)v[2 * i], (float)v[2 * i + 1]);
+        pid[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_unpack(Geom geo, int64_t n, const int32_t *cell, const float2 *cl,
+                         const float2 *vsync, const float2 *fsync, const int32_t *pid, double *x,
+                         double *v, double *f) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double g = geo.g;
+    const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const int32_t c = cell[j];
+        const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
+        const float2 p = cl[j];
+        double px = (double)cx * geo.k * g + (double)p.x;
+        double py = (double)cy * geo.k * g + (double)p.y;
+        px = px <= 0.0 ? px + L0 : (px > L0 ? px - L0 : px);
+        py = py <= 0.0 ? py + L1 : (py > L1 ? py - L1 : py);
+        const int64_t o = pid[j];
+        if (x) { x[2 * o] = px; x[2 * o + 1] = py; }
+        if (v) { const float2 w = vsync[j]; v[2 * o] = w.x; v[2 * o + 1] = w.y; }
+        if (f) { const float2 w = fsync[j]; f[2 * o] = w.x; f[2 * o + 1] = w.y; }
+    }
+}
+
+int grid_for(int64_t n, int threads, int per_sm = 8) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t need = (n + threads - 1) / threads;
+    int64_t g = (int64_t)sms * per_sm;
+    if (need < g) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
+    const int64_t blocks = (a.n + kStepThreads - 1) / kStepThreads;
+    if (blocks < 1) return cudaSuccess;
+    const dim3 grid((unsigned)blocks), block(kStepThreads);
+    if (mode == kModeStep) {
+        if (a.stats) k_step<kModeStep, true><<<grid, block, 0, s>>>(a);
+        else k_step<kModeStep, false><<<grid, block, 0, s>>>(a);
+    } else if (mode == kModeInit) {
+        k_step<kModeInit, true><<<grid, block, 0, s>>>(a);
+    } else {
+        k_step<kModeSync, true><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int64_t sort_scratch_blocks(int64_t ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.count, 0, sizeof(int32_t) * (size_t)a.ncells, s);
+    if (e != cudaSuccess) return e;
+    const int t = 256;
+    k_sort_key<<<grid_for(a.n, t), t, 0, s>>>(a);
+    const int64_t nb = sort_scratch_blocks(a.ncells);
+    k_scan_local<<<(unsigned)nb, kScanThreads, 0, s>>>(a.count, a.ncells, a.block_sums);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
+    k_sort_place<<<grid_for(a.n, t), t, 0, s>>>(a);
+    k_sort_cells<<<grid_for(a.ncells, t), t, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
+                        int32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                        cudaStream_t s) {
+    k_pack<<<grid_for(n, 256), 256, 0, s>>>(geo, n, x, v, cell, cl, vel, pid, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Geom &geo, int64_t n, const int32_t *cell, const float2 *cl,
+                          const float2 *vsync, const float2 *fsync, const int32_t *pid,
+                          double *x, double *v, double *f, cudaStream_t s) {
+    k_unpack<<<grid_for(n, 256), 256, 0, s>>>(geo, n, cell, cl, vsync, fsync, pid, x, v, f);
+    return cudaGetLastError();
+}
+
+}  // namespace mdlg

@@ -11,3 +11,14 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    """The CUDA device for gpu-marked tests (skips only where no GPU exists)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1705_04368_gb300 as m
+    m.lib()          # builds / loads the library; raises if it cannot
+    return torch.device("cuda", 0)

@@ -1,0 +1,197 @@
+"""GPU parity of the Lennard-Jones velocity-Verlet MD and the fused MDLG binning
+of the simulation state against the FP64 oracle.
+
+Tolerances (FP32 pair arithmetic against FP64):
+  forces      |F_gpu - F_ref| <= 1e-5 * sum_j |F_ij|  per particle
+  trajectory  10 steps, every coordinate within 1e-4 sigma (minimum image)
+  FP64 sums   kinetic energy rel 1e-6, potential energy and virial rel 1e-5
+  counts      bit-exact on identical snapshots; ensemble f_i within 3 SE
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mdlg_inputs as mi
+import oracle
+import paper_1705_04368_gb300 as m
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(n, L, x0, v0, **kw):
+    p = m.Params(n=n, box=L, dx=kw.pop("dx", 4.0), **kw)
+    return m.Simulation(p, x0, v0)
+
+
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def _force_check(f_gpu, f_ref, scale, tol=1e-5):
+    err = np.abs(f_gpu - f_ref).max(axis=1)
+    bound = tol * np.maximum(scale, 1e-3)
+    assert np.all(err <= bound), float((err / np.maximum(scale, 1e-3)).max())
+
+
+@pytest.mark.parametrize("n,rho,seed", [(1024, 0.25, 1), (5000, 0.3, 2), (20000, 0.6, 3)])
+def test_forces_match_direct_sum(cuda, n, rho, seed):
+    L = mi.box_for(n, rho, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed)
+    with _sim(n, L, x0, v0) as s:
+        _, _, f = s.get_state(want_force=True)
+    f_ref, scale, _, _ = oracle.lj_forces(x0, (L, L))
+    _force_check(f, f_ref, scale)
+
+
+def test_forces_full_size_sampled(cuda):
+    c = mi.PRODUCTION_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
+    with _sim(c.n, c.box, x0, v0) as s:
+        _, _, f = s.get_state(want_force=True)
+    rng = np.random.default_rng(0)
+    which = np.concatenate([rng.choice(c.n, 150, replace=False), [0, c.n - 1]])
+    f_ref, scale = oracle.lj_forces_sample(x0, (c.box, c.box), which)
+    _force_check(f[which], f_ref, scale)
+
+
+@pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3)])
+def test_ten_step_trajectory(cuda, n, rho, sort_every):
+    L = mi.box_for(n, rho, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=n)
+    ref = oracle.VV(x0, v0, (L, L), dt=0.005).run(10)
+    with _sim(n, L, x0, v0, sort_every=sort_every) as s:
+        s.step(10)
+        x, v = s.get_state()
+        st, _, _ = s.stats()
+    assert np.abs(_min_image(x - ref.x, L)).max() <= 1e-4
+    assert np.abs(v - ref.v).max() <= 1e-3
+    assert st["status"] == 0 and st["step"] == 10
+
+
+def test_fp64_reductions_at_start(cuda):
+    n, L = 8192, mi.box_for(8192, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=11)
+    with _sim(n, L, x0, v0) as s:
+        st, _, _ = s.stats()
+    _, _, pe, vir = oracle.lj_forces(x0, (L, L), cells=True)
+    ke, px, py = oracle.VV(x0, v0, (L, L), 0.005).kinetic()
+    assert st["kinetic"] == pytest.approx(ke, rel=1e-6)
+    assert st["potential"] == pytest.approx(pe, rel=1e-5, abs=1e-3)
+    assert st["virial"] == pytest.approx(vir, rel=1e-5, abs=1e-3)
+    assert abs(st["momentum"][0] - px) < 1e-4 and abs(st["momentum"][1] - py) < 1e-4
+    assert st["temperature"] == pytest.approx(1.0, rel=1e-6)
+
+
+def test_conservation_long_run(cuda):
+    # 1000 steps of a 65 536-particle gas: energy per particle and total momentum
+    # stay put (truncated force and FP32 pair sums bound the drift).
+    n, L = 65536, mi.box_for(65536, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=12)
+    with _sim(n, L, x0, v0, stats_every=100) as s:
+        st0, _, _ = s.stats()
+        s.step(1000)
+        st1, _, _ = s.stats()
+    e0 = st0["kinetic"] + st0["potential"]
+    e1 = st1["kinetic"] + st1["potential"]
+    assert abs(e1 - e0) / n < 2e-3
+    assert abs(st1["momentum"][0]) / n < 1e-5 and abs(st1["momentum"][1]) / n < 1e-5
+    assert st1["status"] == 0
+
+
+def _dyadic_free_flight(n, L, seed):
+    # Positions on a 2^-12 grid and velocities on a 2^-10 grid with dt = 2^-3:
+    # every drift x + v dt is exact in binary32 offsets and in FP64, so the
+    # library's state and the oracle's trajectory are identical snapshots.
+    rng = np.random.default_rng(seed)
+    x = mi.dyadic_positions(n, L, seed, bits=12, boundary_frac=0.05)
+    v = np.round(rng.normal(0.0, 2.0, size=(n, 2)) * 1024) / 1024
+    return x, v
+
+
+@pytest.mark.parametrize("n,L,lags,sort_every,steps", [
+    (5000, 64.0, (4, 7), 3, 60),
+    (70000, 256.0, (1, 5, 16), 2, 48),
+])
+def test_fused_state_binning_bit_exact(cuda, n, L, lags, sort_every, steps):
+    x0, v0 = _dyadic_free_flight(n, L, seed=n)
+    dt = 0.125
+    vmax = 3
+    with _sim(n, L, x0, v0, potential=m.POT_NONE, dt=dt, lag_steps=lags, sort_every=sort_every,
+              vmax=vmax, site_mode=m.SITES_ACCUM) as s:
+        s.step(steps)
+        st, counts, fi = s.stats()
+        sites, ncell = s.get_sites()
+        x_end, _ = s.get_state()
+    C = (int(L / 4.0),) * 2
+    q1 = (2 * vmax + 1) ** 2 + 1
+    ref = np.zeros((len(lags), q1), np.uint64)
+    ref_sites = np.zeros((C[0] * C[1], q1), np.uint32)
+    ref_n = np.zeros(C[0] * C[1], np.uint32)
+    traj = [x0]
+    xx = x0
+    for _ in range(steps):
+        xx = oracle.free_stream(xx, v0, (L, L), dt, 1)
+        traj.append(xx)
+    for li, lag in enumerate(lags):
+        for t in range(lag, steps + 1, lag):
+            oracle.mdlg_bin(traj[t - lag], traj[t], 4.0, C, vmax, counts=ref[li],
+                            field=(li == 0), ncell=ref_n if li == 0 else None,
+                            fld=ref_sites if li == 0 else None)
+    assert np.array_equal(x_end, traj[-1])
+    assert np.array_equal(counts, ref)
+    assert np.array_equal(sites, ref_sites)
+    assert np.array_equal(ncell, ref_n)
+    for li, lag in enumerate(lags):
+        assert st["intervals"][li] == steps // lag
+        assert fi[li].sum() == pytest.approx(1.0)
+
+
+def test_ensemble_fi_matches_oracle(cuda):
+    # Small LJ gas (N = 1024, L = 64, dx = 4, lag 50 steps, 2000 steps): the
+    # per-seed f_i of the library and of the oracle agree within 3 standard
+    # errors of the difference of their seed means, bin by bin.
+    c = mi.SMALL_LJ
+    seeds = range(1, 17)
+    g_runs, o_runs = [], []
+    for seed in seeds:
+        x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed)
+        with _sim(c.n, c.box, x0, v0, lag_steps=c.lags) as s:
+            s.step(c.steps)
+            _, _, fi = s.stats()
+        g_runs.append(fi[0])
+        ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
+        cnt = np.zeros(50, np.uint64)
+        prev = ref.x.copy()
+        for _ in range(c.steps // c.lags[0]):
+            ref.run(c.lags[0])
+            oracle.mdlg_bin(prev, ref.x, c.dx, (16, 16), 3, counts=cnt)
+            prev = ref.x.copy()
+        o_runs.append(cnt / (c.n * (c.steps // c.lags[0])))
+    g, o = np.array(g_runs), np.array(o_runs)
+    S = len(seeds)
+    se = np.sqrt(g.var(axis=0, ddof=1) / S + o.var(axis=0, ddof=1) / S)
+    d = np.abs(g.mean(axis=0) - o.mean(axis=0))
+    live = (g.mean(axis=0) + o.mean(axis=0)) > 1e-4
+    assert np.all(d[live] <= 3 * se[live] + 1e-12), (d[live], se[live])
+    assert np.all(d[~live] < 1e-4)
+
+
+def test_production_run_invariants(cuda):
+    # 4 194 304 particles, rho = 0.3: 200 steps with lags 10, 20, 50, 100, 200.
+    c = mi.PRODUCTION_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=2)
+    with _sim(c.n, c.box, x0, v0, lag_steps=c.lags, stats_every=100,
+              site_mode=m.SITES_FIELD) as s:
+        st0, _, _ = s.stats()
+        s.step(200)
+        st, counts, fi = s.stats()
+        sites, ncell = s.get_sites()
+    assert st["status"] == 0
+    for li, lag in enumerate(c.lags):
+        assert int(counts[li].sum()) == c.n * (200 // lag)
+    assert np.array_equal(sites.sum(axis=1, dtype=np.int64), ncell.astype(np.int64))
+    assert int(ncell.sum()) == c.n
+    e0, e1 = st0["kinetic"] + st0["potential"], st["kinetic"] + st["potential"]
+    assert abs(e1 - e0) / c.n < 1e-3
+    assert abs(st["momentum"][0]) / c.n < 1e-5

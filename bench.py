@@ -337,13 +337,31 @@ def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev
                     "f_i to host) + mdlg_destroy, per step"}
 
 
+def run_ncu_target(md_steps):
+    import torch
+    import paper_1705_04368_gb300 as m
+    c = _workload()
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
+    sim = m.Simulation(_params(c, m), x0, v0)
+    sim.step(md_steps)
+    sim.stats()
+    sim.close()
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--ncu-target", type=int, default=0, metavar="MD_STEPS",
+                    help="profiling target: build the production system, run MD_STEPS MD "
+                         "steps (sorts and binning included), print nothing, exit")
     args = ap.parse_args()
+    if args.ncu_target:
+        run_ncu_target(args.ncu_target)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -86,10 +86,19 @@ def maxwell_velocities(n: int, temperature: float, rng: np.random.Generator,
 
 
 def lj_initial_state(n: int, box, temperature: float, seed: int, dmin: float = 0.9,
-                     mass: float = 1.0):
-    """(x, v): (n, 2) FP64 positions in (0, L] and velocities for the LJ gas."""
+                     mass: float = 1.0, quantum: float | None = None):
+    """(x, v): (n, 2) FP64 positions in (0, L] and velocities for the LJ gas.
+
+    ``quantum`` (a power of two, e.g. 2**-20) rounds positions to its multiples
+    so that they are exactly representable as integer cell origin + binary32
+    offset: both sides of a force comparison then see identical positions.
+    """
     L = (float(box), float(box)) if np.isscalar(box) else (float(box[0]), float(box[1]))
     x = _nonoverlap(n, L, dmin, seed)
+    if quantum is not None:
+        x = np.round(x / quantum) * quantum
+        for a in (0, 1):
+            x[:, a] = np.where(x[:, a] <= 0, L[a], x[:, a])
     v = maxwell_velocities(n, temperature, np.random.default_rng(seed), mass)
     return x, v
 

@@ -346,6 +346,11 @@ def run_ncu_target(md_steps):
     sim.step(md_steps)
     sim.stats()
     sim.close()
+    dev = torch.device("cuda", 0)
+    pos, vel = mi.idealgas_state(mi.IDEALGAS_N, mi.IDEALGAS_BOX, 1.0, seed=7)
+    pos, vel = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+    counts = torch.zeros((len(mi.IDEALGAS_COMBOS), 50), dtype=torch.int64, device=dev)
+    m.idealgas_bin(pos, vel, list(mi.IDEALGAS_COMBOS), 3, counts)
     torch.cuda.synchronize()
 
 
@@ -357,7 +362,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--ncu-target", type=int, default=0, metavar="MD_STEPS",
                     help="profiling target: build the production system, run MD_STEPS MD "
-                         "steps (sorts and binning included), print nothing, exit")
+                         "steps (sorts and binning included) and one ideal-gas pass, exit")
     args = ap.parse_args()
     if args.ncu_target:
         run_ncu_target(args.ncu_target)

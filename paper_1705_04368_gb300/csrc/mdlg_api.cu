@@ -23,7 +23,7 @@ struct mdlg_ctx {
     int32_t ratio_shift = -1;
     int32_t q1 = 0;
     // double-buffered state: position/velocity swap every step, the rest at sorts
-    int32_t *cell[2]{};
+    uint32_t *cell[2]{};
     float2 *cl[2]{};
     float2 *vel[2]{};
     int32_t *pid[2]{};
@@ -31,14 +31,19 @@ struct mdlg_ctx {
     int pos_cur = 0, meta_cur = 0;
     int32_t *cell_start = nullptr;
     // scratch
-    int32_t *key = nullptr, *slot = nullptr, *count = nullptr, *block_sums = nullptr;
+    uint32_t *key = nullptr;
+    int32_t *slot = nullptr, *count = nullptr, *block_sums = nullptr;
     unsigned long long *entry = nullptr;
-    double *partials = nullptr;
+    long long *partials = nullptr;
     Control *ctl = nullptr;
     unsigned long long *counts = nullptr;   // nlags x q1
     uint32_t *site_n = nullptr, *site_counts = nullptr;
     float2 *vsync = nullptr, *fsync = nullptr;
     double *xbuf = nullptr, *vbuf = nullptr, *fbuf = nullptr;
+    uint32_t *nbr = nullptr;      // Verlet list (cap x n)
+    int32_t *ncount = nullptr;
+    int32_t cap = 0;
+    float list_radius = 0.f;
     // host-side schedule
     int64_t step = 0, last_sort = 0, stats_step = -1;
     int64_t intervals[kMaxLags]{};
@@ -165,6 +170,8 @@ int validate(const mdlg_params *p) {
         if (lg < 1 || lg > 65535) return MDLG_EINVAL;
         if (p->potential == MDLG_POT_LJ_TS && !(p->rcut < 0.5 * p->box[a])) return MDLG_EINVAL;
     }
+    // Verlet-list entries carry the particle index in 28 bits
+    if (p->potential == MDLG_POT_LJ_TS && p->n >= (1LL << 28)) return MDLG_EINVAL;
     return MDLG_OK;
 }
 
@@ -197,6 +204,10 @@ StepArgs step_args(mdlg_ctx *c) {
     a.potential = c->p.potential == MDLG_POT_LJ_TS ? 1 : 0;
     a.partials = c->partials;
     a.ctl = c->ctl;
+    a.nbr = c->nbr;
+    a.ncount = c->ncount;
+    a.cap = c->cap;
+    a.list_skin = c->list_radius - (float)rc;
     return a;
 }
 
@@ -244,8 +255,12 @@ int do_sort(mdlg_ctx *c) {
     s.entry = c->entry;
     s.block_sums = c->block_sums;
     s.ctl = c->ctl;
+    s.nbr = c->nbr;
+    s.ncount = c->ncount;
+    s.cap = c->cap;
+    s.rl2 = c->list_radius * c->list_radius;
     {
-        ProfScope ps(c, MDLG_PROF_SORT, 5);
+        ProfScope ps(c, MDLG_PROF_SORT, c->nbr ? 7 : 6);
         MDLG_TRY(cuda_err(launch_sort(s, c->stream)));
     }
     c->pos_cur ^= 1;
@@ -368,12 +383,11 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
             if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
     }
     const int64_t nb = sort_scratch_blocks(c->ncells);
-    const int64_t step_blocks = (n + 255) / 256;
     if ((rc = alloc_n(c, &c->cell_start, (size_t)c->ncells + 1)) ||
         (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
         (rc = alloc_n(c, &c->count, (size_t)c->ncells)) ||
         (rc = alloc_n(c, &c->block_sums, (size_t)nb)) || (rc = alloc_n(c, &c->entry, N)) ||
-        (rc = alloc_n(c, &c->partials, (size_t)step_blocks * 5)) ||
+        (rc = alloc_n(c, &c->partials, (size_t)mdlg::step_blocks(n) * 5)) ||
         (rc = alloc_n(c, &c->ctl, 1)) ||
         (rc = alloc_n(c, &c->counts, (size_t)p.nlags * c->q1)) ||
         (rc = alloc_n(c, &c->vsync, N)) || (rc = alloc_n(c, &c->fsync, N)) ||
@@ -383,6 +397,17 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     if (p.site_mode) {
         const size_t sites = (size_t)g.lat[0] * g.lat[1];
         if ((rc = alloc_n(c, &c->site_n, sites)) || (rc = alloc_n(c, &c->site_counts, sites * c->q1)))
+            return fail(rc);
+    }
+    if (p.potential == MDLG_POT_LJ_TS) {
+        // Verlet list of radius = the MD cell width (rc + the whole skin);
+        // capacity three times the mean count at the box density, plus 16
+        c->list_radius = (float)(g.k * p.grid);
+        const double rho = (double)n / (p.box[0] * p.box[1]);
+        const double mean = rho * 3.14159265358979 * (double)c->list_radius * c->list_radius;
+        c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
+        if (c->cap > 4096) c->cap = 4096;
+        if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
             return fail(rc);
     }
 

@@ -122,9 +122,9 @@ __global__ void k_bin_state(StateBinArgs sa) {
         const bool act = j < sa.n;
         int32_t lx = 0, ly = 0;
         if (act) {
-            const int32_t c = sa.cell[j];
+            const uint32_t c = sa.cell[j];
             const float2 p = sa.cl[j];
-            const int32_t ccx = c % geo.nc[0], ccy = c / geo.nc[0];
+            const int32_t ccx = (int32_t)(c & 0xffffu), ccy = (int32_t)(c >> 16);
             const int32_t bx = base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
             const int32_t by = base_cell(ccy * geo.k, p.y, geo.inv_g, geo.lg[1]);
             lx = lattice_of_base(bx, geo.ratio, sa.ratio_shift);
@@ -159,9 +159,9 @@ __global__ void k_bin_seed(StateBinArgs sa) {
     const Geom &geo = sa.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < sa.n; j += stride) {
-        const int32_t c = sa.cell[j];
+        const uint32_t c = sa.cell[j];
         const float2 p = sa.cl[j];
-        const int32_t ccx = c % geo.nc[0], ccy = c / geo.nc[0];
+        const int32_t ccx = (int32_t)(c & 0xffffu), ccy = (int32_t)(c >> 16);
         const int32_t bx = base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
         const int32_t by = base_cell(ccy * geo.k, p.y, geo.inv_g, geo.lg[1]);
         const uint32_t now = pack_cell(lattice_of_base(bx, geo.ratio, sa.ratio_shift),
@@ -178,7 +178,7 @@ int hist_grid(int64_t n, int threads) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t need = (n + threads - 1) / threads;
-    int64_t g = (int64_t)sms * 4;
+    int64_t g = (int64_t)sms * 8;
     if (need < g) g = need;
     return (int)(g < 1 ? 1 : g);
 }

@@ -48,21 +48,24 @@ __device__ __forceinline__ int32_t wrap_mod(int32_t d, int32_t m) {
 }
 
 // Base cell of a particle: the cell (b g, (b+1) g] that holds origin + cl.
-// cl / g is exact (g a power of two), ceil(t) - 1 is the left-open rule.  The
-// result is reduced modulo lg, so it is a valid index for any input (a
-// non-finite offset converts to an arbitrary integer and is flagged elsewhere).
+// cl / g is exact (g a power of two), ceil(t) - 1 is the left-open rule.  A
+// particle is within a few cells of its MD cell's origin, so one conditional
+// wrap suffices; the clamp keeps any input (even a non-finite offset, which is
+// flagged elsewhere) a valid index.
 __device__ __forceinline__ int32_t base_cell(int32_t origin, float cl, float inv_g, int32_t lg) {
-    const float t = fminf(fmaxf(ceilf(cl * inv_g), -1.0e9f), 1.0e9f);
-    int32_t b = (origin + (int32_t)t - 1) % lg;
-    return b < 0 ? b + lg : b;
+    const float lim = (float)lg;
+    const float t = fminf(fmaxf(ceilf(cl * inv_g), -lim + 1.0f), lim);
+    int32_t b = origin + (int32_t)t - 1;
+    b += b < 0 ? lg : 0;
+    b -= b >= lg ? lg : 0;
+    return b;
 }
 
-// Lattice displacement reduced into (-C/2, C/2].
+// Lattice displacement of two cells in [0, C), reduced into (-C/2, C/2].
 __device__ __forceinline__ int32_t lattice_disp(int32_t d, int32_t C) {
-    int32_t r = d % C;
-    if (r < 0) r += C;
-    if (r > (C >> 1)) r -= C;
-    return r;
+    d += d < 0 ? C : 0;               // [0, C)
+    d -= d > (C >> 1) ? C : 0;        // (-C/2, C/2]
+    return d;
 }
 
 // Velocity index of a lattice displacement (vx, vy); Q for outside the window.

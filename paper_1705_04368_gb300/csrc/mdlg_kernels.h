@@ -30,7 +30,7 @@ struct StateBinArgs {
     int32_t ratio_shift;   // log2(ratio) or -1
     int32_t nlags;
     uint32_t mask;         // lags binned by this launch
-    const int32_t *cell;
+    const uint32_t *cell;   // packed MD cell (c_x | c_y << 16)
     const float2 *cl;
     uint32_t *lprev[kMaxLags];
     unsigned long long *counts[kMaxLags];
@@ -66,8 +66,8 @@ enum StepMode : int32_t {
 struct StepArgs {
     Geom geo;
     int64_t n;
-    const int32_t *cell;
-    const int32_t *cell_start;  // nc[0]*nc[1] + 1
+    const uint32_t *cell;       // packed MD cell (c_x | c_y << 16)
+    const int32_t *cell_start;  // nc[0]*nc[1] + 1, by row-major cell number
     const float2 *cl_in;
     const float2 *v_in;
     float2 *cl_out;             // kModeStep
@@ -79,12 +79,17 @@ struct StepArgs {
     float cell_w;               // k g: narrowest MD cell width
     float rc;
     float round_margin;         // per-step slack added to the displacement bound
+    const uint32_t *nbr;        // Verlet list, column-major (cap x n), or null
+    const int32_t *ncount;      // entries per particle (cap + 1: overflowed)
+    int32_t cap;                // list capacity per particle
+    float list_skin;            // list radius - rc
     int32_t potential;          // 0 none, 1 LJ
     int32_t stats;              // 1: FP64 reductions into partials
-    double *partials;           // gridDim.x x 5
+    long long *partials;        // gridDim.x x 5 fixed-point block sums
     Control *ctl;
 };
 
+int64_t step_blocks(int64_t n);
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);
 
 struct SortArgs {
@@ -93,25 +98,30 @@ struct SortArgs {
     int32_t nlags;
     int64_t ncells;
     // current state
-    const int32_t *cell_in;
+    const uint32_t *cell_in;
     const float2 *cl_in;
     const float2 *v_in;
     const int32_t *pid_in;
     const uint32_t *lprev_in[kMaxLags];
     // sorted state
-    int32_t *cell_out;
+    uint32_t *cell_out;
     float2 *cl_out;
     float2 *v_out;
     int32_t *pid_out;
     uint32_t *lprev_out[kMaxLags];
     int32_t *cell_start;     // ncells + 1
     // scratch
-    int32_t *key;            // n
+    uint32_t *key;           // n, packed new cell
     int32_t *slot;           // n
     int32_t *count;          // ncells
     unsigned long long *entry;  // n
     int32_t *block_sums;     // scan partials
     Control *ctl;
+    // Verlet list built from the sorted state (nbr null: none)
+    uint32_t *nbr;
+    int32_t *ncount;
+    int32_t cap;
+    float rl2;               // list radius squared
 };
 
 int64_t sort_scratch_blocks(int64_t ncells);
@@ -119,10 +129,10 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
 
 // Upload conversion: FP64 positions -> (cell, cl) in original order (unsorted).
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
-                        int32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                        uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
                         cudaStream_t s);
 // Download conversion: sorted state -> FP64 arrays in original order.
-cudaError_t launch_unpack(const Geom &geo, int64_t n, const int32_t *cell, const float2 *cl,
+cudaError_t launch_unpack(const Geom &geo, int64_t n, const uint32_t *cell, const float2 *cl,
                           const float2 *vsync, const float2 *fsync, const int32_t *pid,
                           double *x, double *v, double *f, cudaStream_t s);
 

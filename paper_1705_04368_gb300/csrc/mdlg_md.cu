@@ -1,6 +1,6 @@
-// mdlg_md.cu -- Lennard-Jones velocity-Verlet step, neighbour-cell sort and the
-// FP64 reductions (Newton equations of Sec. III and potential of Sec. IV of
-// arXiv:1705.04368).
+// mdlg_md.cu -- Lennard-Jones velocity-Verlet step, neighbour-cell sort, Verlet
+// list and the global reductions (Newton equations of Sec. III and potential of
+// Sec. IV of arXiv:1705.04368).
 //
 // Time stepping is the leapfrog form of velocity Verlet: the stored velocity is
 // the half-step velocity v_{n-1/2}, and one launch per MD step does
@@ -9,29 +9,40 @@
 // the integer-step velocity v_n = v_{n-1/2} + F_n dt/(2m) is formed when it is
 // needed (statistics, state download).
 //
-// Neighbour search: particles are sorted by MD cell (side k g >= rc + skin).
-// Between sorts a particle drifts at most D outside its cell (D tracked on the
-// device from the largest speed of every step), so every pair closer than rc
-// lies within R = ceil((rc + 2D) / (k g)) cells; R = 1 while 2D <= skin.
+// Neighbour search: particles are sorted by MD cell (side k g >= rc + skin) and
+// a Verlet list of radius k g is built right after every sort.  Between sorts a
+// particle moves at most D (tracked on the device from the largest speed of
+// every step).  While 2D <= skin the list holds every pair closer than rc; past
+// that the step kernel falls back to the cell stencil of radius
+// R = ceil((rc + 2D) / (k g)), so forces are correct whatever the sort schedule.
+//
+// MD cells are stored packed as (c_x | c_y << 16); cell_start is indexed by
+// the row-major cell number c_y nc_x + c_x.
 #include "mdlg_kernels.h"
 
 namespace mdlg {
 
 namespace {
 
-constexpr int kStepThreads = 256;
+constexpr int kStepThreads = 128;
+constexpr int kListBatch = 8;       // list entries loaded before any is used
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 cells per scan block
 constexpr int kStatsN = 5;
 constexpr int kErrNonFinite = -5;
 constexpr int kErrOverflow = -4;
+constexpr uint32_t kNoEntry = 0xffffffffu;
+// Fixed-point scale of the exact reductions: per-particle terms are rounded to
+// multiples of 2^-24 and summed as 64-bit integers.
+constexpr float kFixScale = 16777216.0f;
+constexpr double kFixInv = 1.0 / 16777216.0;
 
 __device__ __forceinline__ void set_status(Control *ctl, int code) {
     atomicCAS(&ctl->status, 0, code);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -43,10 +54,102 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+__device__ __forceinline__ int32_t cell_x(uint32_t cw) { return (int32_t)(cw & 0xffffu); }
+__device__ __forceinline__ int32_t cell_y(uint32_t cw) { return (int32_t)(cw >> 16); }
+
 // Stencil bounds of one axis: [-R, R], or every cell once if that would wrap.
 __device__ __forceinline__ void stencil(int R, int nc, int &lo, int &hi) {
     if (2 * R + 1 <= nc) { lo = -R; hi = R; }
     else { lo = -(nc >> 1); hi = lo + nc - 1; }
+}
+
+// Per-particle pair sums (FP32; the cross-particle reductions are exact).
+struct PairAcc {
+    float fx, fy, pe, vir;
+};
+
+// One pair term of the truncated-shifted Lennard-Jones interaction:
+// force on i from j is 24 eps (2 s^12 - s^6) / r^2 (x_i - x_j), s = sigma / r;
+// pe adds V(r) - V(rc), vir adds r . F (both halved later: each pair is seen twice).
+template <bool STATS>
+__device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy, PairAcc &acc) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    if (r2 < a.rc2) {
+        const float ir2 = __frcp_rn(r2);
+        const float sr2 = a.sig2 * ir2;
+        const float sr6 = sr2 * sr2 * sr2;
+        const float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+        acc.fx = fmaf(fs, dx, acc.fx);
+        acc.fy = fmaf(fs, dy, acc.fy);
+        if (STATS) {
+            acc.pe += a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
+            acc.vir = fmaf(fs, r2, acc.vir);
+        }
+    }
+}
+
+// Origin shift o_j - o_i of the neighbouring cell at offset `off` along one axis.
+__device__ __forceinline__ float cell_shift(int32_t c, int off, int32_t nc, int32_t k, int32_t lg,
+                                            float g) {
+    return (float)wrap_half((wrap_mod(c + off, nc) - c) * k, lg) * g;
+}
+
+// All pairs through the cell stencil (always correct for the current bound D).
+template <bool STATS>
+__device__ __forceinline__ void forces_cells(const StepArgs &a, int64_t i, int32_t cx, int32_t cy,
+                                             float2 p, int lox, int hix, int loy, int hiy,
+                                             PairAcc &acc) {
+    const Geom &geo = a.geo;
+    for (int oy = loy; oy <= hiy; ++oy) {
+        const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
+        const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
+        for (int ox = lox; ox <= hix; ++ox) {
+            const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
+            const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
+            const int32_t cn = ny * geo.nc[0] + nx;
+            const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+            for (int32_t j = s; j < e; ++j) {
+                if (j == i) continue;
+                const float2 q = __ldg(a.cl_in + j);
+                // x_i - x_j = (cl_i - cl_j) - (origin_j - origin_i)
+                pair_term<STATS>(a, (p.x - q.x) - odx, (p.y - q.y) - ody, acc);
+            }
+        }
+    }
+}
+
+// Pairs from the Verlet list built at the last sort: entry t of particle i is
+// nbr[t n + i] = j | (ox + 1) << 28 | (oy + 1) << 30 with (ox, oy) the offset of
+// j's cell from i's cell.  Entries are fetched kListBatch at a time so that
+// their loads (and the dependent position loads) overlap.
+template <bool STATS>
+__device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, int32_t cx, int32_t cy,
+                                            float2 p, int cnt, PairAcc &acc) {
+    const Geom &geo = a.geo;
+    const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+    const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+    const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+    const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+    const uint32_t *e = a.nbr + i;
+    const int64_t n = a.n;
+    for (int t0 = 0; t0 < cnt; t0 += kListBatch) {
+        uint32_t ent[kListBatch];
+#pragma unroll
+        for (int u = 0; u < kListBatch; ++u)
+            ent[u] = (t0 + u < cnt) ? __ldg(e + (int64_t)(t0 + u) * n) : kNoEntry;
+        float2 q[kListBatch];
+#pragma unroll
+        for (int u = 0; u < kListBatch; ++u)
+            q[u] = (ent[u] != kNoEntry) ? __ldg(a.cl_in + (ent[u] & 0x0fffffffu))
+                                        : make_float2(1.0e18f, 1.0e18f);
+#pragma unroll
+        for (int u = 0; u < kListBatch; ++u) {
+            const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
+            const float sx = ox == 0u ? sxm : (ox == 2u ? sxp : 0.0f);
+            const float sy = oy == 0u ? sym : (oy == 2u ? syp : 0.0f);
+            pair_term<STATS>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
+        }
+    }
 }
 
 template <int MODE, bool STATS>
@@ -63,52 +166,29 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     if (a.potential && threadIdx.x == 0 && blockIdx.x == 0 &&
         (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1]))
         set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
-    int lox, hix, loy, hiy;
-    stencil(R, geo.nc[0], lox, hix);
-    stencil(R, geo.nc[1], loy, hiy);
+    // the Verlet list holds every pair that can be closer than rc while 2D <= skin
+    const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
 
-    float fx = 0.f, fy = 0.f;
-    double pe = 0.0, vir = 0.0;
+    PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
     if (act) {
-        const int32_t c = a.cell[i];
+        const uint32_t cw = a.cell[i];
         p = a.cl_in[i];
         v = a.v_in[i];
         if (a.potential) {
-            const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
-            for (int oy = loy; oy <= hiy; ++oy) {
-                const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
-                const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
-                for (int ox = lox; ox <= hix; ++ox) {
-                    const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
-                    const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
-                    const int32_t cn = ny * geo.nc[0] + nx;
-                    const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
-                    for (int32_t j = s; j < e; ++j) {
-                        if (j == i) continue;
-                        const float2 q = __ldg(a.cl_in + j);
-                        // x_i - x_j = (cl_i - cl_j) - (origin_j - origin_i)
-                        const float dx = (p.x - q.x) - odx;
-                        const float dy = (p.y - q.y) - ody;
-                        const float r2 = fmaf(dx, dx, dy * dy);
-                        if (r2 < a.rc2) {
-                            const float ir2 = __frcp_rn(r2);
-                            const float sr2 = a.sig2 * ir2;
-                            const float sr6 = sr2 * sr2 * sr2;
-                            // -(1/r) dV/dr = 24 eps (2 s^12 - s^6) / r^2
-                            const float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
-                            fx = fmaf(fs, dx, fx);
-                            fy = fmaf(fs, dy, fy);
-                            if (STATS) {
-                                pe += 0.5 * (double)(a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift);
-                                vir += 0.5 * (double)fs * (double)r2;
-                            }
-                        }
-                    }
-                }
+            const int32_t cx = cell_x(cw), cy = cell_y(cw);
+            const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
+            if (cnt <= a.cap) {
+                forces_list<STATS>(a, i, cx, cy, p, cnt, acc);
+            } else {
+                int lox, hix, loy, hiy;
+                stencil(R, geo.nc[0], lox, hix);
+                stencil(R, geo.nc[1], loy, hiy);
+                forces_cells<STATS>(a, i, cx, cy, p, lox, hix, loy, hiy, acc);
             }
         }
     }
+    const float fx = acc.fx, fy = acc.fy;
 
     float2 vn = v;   // velocity at the integer step (statistics)
     float vmax2 = 0.f;
@@ -132,8 +212,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
         }
     }
 
-    __shared__ double s_red[kStepThreads / 32][kStatsN];
-    __shared__ float s_max[kStepThreads / 32];
+    constexpr int kWarps = kStepThreads / 32;
+    __shared__ long long s_red[kWarps][kStatsN];
+    __shared__ float s_max[kWarps];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (MODE == kModeStep) {
@@ -141,29 +222,32 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
         if (lane == 0) s_max[warp] = m;
     }
     if (STATS) {
-        double ke = 0.0, px = 0.0, py = 0.0;
+        // per-particle FP32 terms -> multiples of 2^-24 -> exact 64-bit sums
+        float t[kStatsN] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (act) {
-            const double vx = vn.x, vy = vn.y;
-            ke = 0.5 * (double)a.mass * (vx * vx + vy * vy);
-            px = (double)a.mass * vx;
-            py = (double)a.mass * vy;
+            t[0] = 0.5f * a.mass * fmaf(vn.x, vn.x, vn.y * vn.y);
+            t[1] = 0.5f * acc.pe;
+            t[2] = 0.5f * acc.vir;
+            t[3] = a.mass * vn.x;
+            t[4] = a.mass * vn.y;
         }
-        const double r[kStatsN] = {warp_sum(ke), warp_sum(pe), warp_sum(vir), warp_sum(px),
-                                   warp_sum(py)};
-        if (lane == 0)
-            for (int k = 0; k < kStatsN; ++k) s_red[warp][k] = r[k];
+#pragma unroll
+        for (int k = 0; k < kStatsN; ++k) {
+            const long long r = warp_sum_ll(__float2ll_rn(t[k] * kFixScale));
+            if (lane == 0) s_red[warp][k] = r;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (MODE == kModeStep) {
             float m = 0.f;
-            for (int w = 0; w < kStepThreads / 32; ++w) m = fmaxf(m, s_max[w]);
+            for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_max[w]);
             atomicMax(&a.ctl->vmax2_bits, __float_as_uint(m));
         }
         if (STATS) {
             for (int k = 0; k < kStatsN; ++k) {
-                double t = 0.0;
-                for (int w = 0; w < kStepThreads / 32; ++w) t += s_red[w][k];
+                long long t = 0;
+                for (int w = 0; w < kWarps; ++w) t += s_red[w][k];
                 a.partials[(size_t)blockIdx.x * kStatsN + k] = t;
             }
         }
@@ -176,13 +260,14 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     // Last block of the launch: every other block has published its results.
     __threadfence();
     if (STATS) {
-        // Fixed-order sum over block partials, one warp per quantity: deterministic.
-        if (warp < kStatsN) {
-            double t = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32)
-                t += ((volatile double *)a.partials)[(size_t)b * kStatsN + warp];
-            t = warp_sum(t);
-            if (lane == 0) a.ctl->stats[warp] = t;
+        if (warp == 0) {
+            for (int k = 0; k < kStatsN; ++k) {
+                long long t = 0;
+                for (int b = lane; b < (int)gridDim.x; b += 32)
+                    t += ((volatile long long *)a.partials)[(size_t)b * kStatsN + k];
+                t = warp_sum_ll(t);
+                if (lane == 0) a.ctl->stats[k] = (double)t * kFixInv;
+            }
         }
     }
     if (threadIdx.x == 0) {
@@ -195,30 +280,33 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     }
 }
 
-// ---- neighbour-cell sort (stable counting sort keyed by MD cell, particle
-//      number order inside a cell) -------------------------------------------
+// ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
+//      order inside a cell) ---------------------------------------------------
+
+__device__ __forceinline__ int32_t lin(const Geom &geo, uint32_t cw) {
+    return cell_y(cw) * geo.nc[0] + cell_x(cw);
+}
 
 __global__ void k_sort_key(SortArgs a) {
     const Geom &geo = a.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const int32_t c = a.cell_in[i];
+        const uint32_t cw = a.cell_in[i];
         const float2 p = a.cl_in[i];
-        const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
-        const int32_t bx = base_cell(cx * geo.k, p.x, geo.inv_g, geo.lg[0]);
-        const int32_t by = base_cell(cy * geo.k, p.y, geo.inv_g, geo.lg[1]);
+        const int32_t bx = base_cell(cell_x(cw) * geo.k, p.x, geo.inv_g, geo.lg[0]);
+        const int32_t by = base_cell(cell_y(cw) * geo.k, p.y, geo.inv_g, geo.lg[1]);
         int32_t nx = bx / geo.k, ny = by / geo.k;
         nx = nx < geo.nc[0] ? nx : geo.nc[0] - 1;
         ny = ny < geo.nc[1] ? ny : geo.nc[1] - 1;
-        const int32_t key = ny * geo.nc[0] + nx;
+        const uint32_t key = (uint32_t)nx | ((uint32_t)ny << 16);
         a.key[i] = key;
-        a.slot[i] = atomicAdd(&a.count[key], 1);
+        a.slot[i] = atomicAdd(&a.count[lin(geo, key)], 1);
     }
 }
 
-// Exclusive scan of one 4096-entry chunk in place; chunk total to block_sums.
-__device__ __forceinline__ int32_t block_exclusive_scan(int32_t *data, int64_t base, int64_t m,
-                                                        int32_t *total) {
+// Exclusive scan of one 4096-entry chunk in place; chunk total to *total.
+__device__ __forceinline__ void block_exclusive_scan(int32_t *data, int64_t base, int64_t m,
+                                                     int32_t *total) {
     __shared__ int32_t s_warp[kScanThreads / 32];
     int32_t v[kScanItems];
     int32_t sum = 0;
@@ -238,7 +326,7 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t *data, int64_t b
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        int32_t w = s_warp[lane];
+        const int32_t w = s_warp[lane];
         int32_t wi = w;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -255,13 +343,13 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t *data, int64_t b
         if (o + k < m) data[o + k] = run;
         run += v[k];
     }
-    return 0;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_local(int32_t *count, int64_t m,
                                                              int32_t *block_sums) {
     __shared__ int32_t total;
     block_exclusive_scan(count, (int64_t)blockIdx.x * kScanChunk, m, &total);
+    __syncthreads();
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
@@ -277,88 +365,135 @@ __device__ __forceinline__ int32_t cell_begin(const SortArgs &a, int64_t c) {
 __global__ void k_sort_place(SortArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const int32_t key = a.key[i];
-        const int64_t at = (int64_t)cell_begin(a, key) + a.slot[i];
+        const int64_t at = (int64_t)cell_begin(a, lin(a.geo, a.key[i])) + a.slot[i];
         a.entry[at] = ((unsigned long long)(uint32_t)a.pid_in[i] << 32) | (uint32_t)i;
     }
 }
 
-// One thread per MD cell: order the cell's particles by particle number, then
-// gather them from the old order, re-expressing positions against the new
-// cell's origin.
-__global__ void k_sort_cells(SortArgs a) {
-    const Geom &geo = a.geo;
+// Cell start offsets (one thread per MD cell) and the reset of the
+// displacement bound: after the sort every particle is inside its cell.
+__global__ void k_cell_start(SortArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.cell_start[a.ncells] = (int32_t)a.n;
         a.ctl->dbound = 0.0f;
     }
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncells; c += stride) {
-        const int32_t s = cell_begin(a, c);
-        const int32_t e = (c + 1 < a.ncells) ? cell_begin(a, c + 1) : (int32_t)a.n;
-        a.cell_start[c] = s;
-        const int32_t m = e - s;
-        const int32_t cx = (int32_t)(c % geo.nc[0]), cy = (int32_t)(c / geo.nc[0]);
-        for (int32_t r = 0; r < m; ++r) {
-            // rank r: the r-th smallest particle number in the cell
-            const unsigned long long er = a.entry[s + r];
-            int32_t rank = 0;
-            for (int32_t t = 0; t < m; ++t) rank += (a.entry[s + t] >> 32) < (er >> 32);
-            const int32_t from = (int32_t)(er & 0xffffffffu);
-            const int32_t to = s + rank;
-            const int32_t oc = a.cell_in[from];
-            const int32_t ocx = oc % geo.nc[0], ocy = oc / geo.nc[0];
-            const float2 p = a.cl_in[from];
-            const float sx = (float)wrap_half((ocx - cx) * geo.k, geo.lg[0]) * geo.g;
-            const float sy = (float)wrap_half((ocy - cy) * geo.k, geo.lg[1]) * geo.g;
-            a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
-            a.v_out[to] = a.v_in[from];
-            a.pid_out[to] = a.pid_in[from];
-            a.cell_out[to] = (int32_t)c;
-            for (int l = 0; l < a.nlags; ++l) a.lprev_out[l][to] = a.lprev_in[l][from];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncells; c += stride)
+        a.cell_start[c] = cell_begin(a, c);
+}
+
+// One thread per slot of the new order: the particle that arrived in that slot
+// finds its rank by particle number among its cell's arrivals, then is copied
+// from the old order to its final place, its position re-expressed against the
+// new cell's origin.
+__global__ void k_sort_scatter(SortArgs a) {
+    const Geom &geo = a.geo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+        const unsigned long long et = a.entry[t];
+        const int32_t from = (int32_t)(et & 0xffffffffu);
+        const uint32_t my_pid = (uint32_t)(et >> 32);
+        const uint32_t cw = a.key[from];
+        const int32_t c = lin(geo, cw);
+        const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
+        int32_t rank = 0;
+        for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
+        const int32_t to = s + rank;
+        const uint32_t ow = a.cell_in[from];
+        const float2 p = a.cl_in[from];
+        const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
+        const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
+        a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
+        a.v_out[to] = a.v_in[from];
+        a.pid_out[to] = a.pid_in[from];
+        a.cell_out[to] = cw;
+        for (int l = 0; l < a.nlags; ++l) a.lprev_out[l][to] = a.lprev_in[l][from];
+    }
+}
+
+// Verlet list of the freshly sorted state: every j != i closer than the list
+// radius, found in the 3 x 3 cell stencil (cells are at least that wide and
+// every particle is inside its cell).  Candidates are fetched four at a time
+// (predicated) so their loads overlap.  Column-major: entry t of particle i at
+// nbr[t n + i].  A particle with more than `cap` entries stores cap + 1 as its
+// count and is handled through the cell stencil by the step kernel.
+__global__ void k_nlist(SortArgs a) {
+    const Geom &geo = a.geo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const uint32_t cw = a.cell_out[i];
+        const int32_t cx = cell_x(cw), cy = cell_y(cw);
+        const float2 p = a.cl_out[i];
+        int cnt = 0;
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
+            const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
+                const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
+                const int32_t cn = ny * geo.nc[0] + nx;
+                const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+                const uint32_t code = ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
+                for (int32_t b = s; b < e; b += 4) {
+                    float2 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        q[u] = (b + u < e) ? __ldg(a.cl_out + b + u) : make_float2(1.0e18f, 1.0e18f);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t j = b + u;
+                        const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
+                        if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
+                            if (cnt < a.cap) a.nbr[(int64_t)cnt * a.n + i] = (uint32_t)j | code;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
         }
+        a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
     }
 }
 
 // ---- upload / download conversions ----------------------------------------
 
-__global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, int32_t *cell,
+__global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, uint32_t *cell,
                        float2 *cl, float2 *vel, int32_t *pid, Control *ctl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const double g = geo.g;
+    const double g = geo.g, inv_g = geo.inv_g;   // g a power of two: x * (1/g) is exact
+    const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double px = x[2 * i], py = x[2 * i + 1];
-        const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
         if (!(px > 0.0 && px <= L0 && py > 0.0 && py <= L1) || !isfinite(v[2 * i]) ||
             !isfinite(v[2 * i + 1])) {
             set_status(ctl, kErrNonFinite);
         }
         // base cell b with b g < x <= (b+1) g
-        int64_t bx = (int64_t)ceil(px / g) - 1, by = (int64_t)ceil(py / g) - 1;
+        int64_t bx = (int64_t)ceil(px * inv_g) - 1, by = (int64_t)ceil(py * inv_g) - 1;
         bx = bx < 0 ? 0 : (bx >= geo.lg[0] ? geo.lg[0] - 1 : bx);
         by = by < 0 ? 0 : (by >= geo.lg[1] ? geo.lg[1] - 1 : by);
         int32_t cx = (int32_t)(bx / geo.k), cy = (int32_t)(by / geo.k);
         cx = cx < geo.nc[0] ? cx : geo.nc[0] - 1;
         cy = cy < geo.nc[1] ? cy : geo.nc[1] - 1;
-        cell[i] = cy * geo.nc[0] + cx;
-        cl[i] = make_float2((float)(px - (double)cx * geo.k * g), (float)(py - (double)cy * geo.k * g));
+        cell[i] = (uint32_t)cx | ((uint32_t)cy << 16);
+        cl[i] = make_float2((float)(px - (double)(cx * geo.k) * g),
+                            (float)(py - (double)(cy * geo.k) * g));
         vel[i] = make_float2((float)v[2 * i], (float)v[2 * i + 1]);
         pid[i] = (int32_t)i;
     }
 }
 
-__global__ void k_unpack(Geom geo, int64_t n, const int32_t *cell, const float2 *cl,
+__global__ void k_unpack(Geom geo, int64_t n, const uint32_t *cell, const float2 *cl,
                          const float2 *vsync, const float2 *fsync, const int32_t *pid, double *x,
                          double *v, double *f) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const double g = geo.g;
     const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const int32_t c = cell[j];
-        const int32_t cx = c % geo.nc[0], cy = c / geo.nc[0];
+        const uint32_t cw = cell[j];
         const float2 p = cl[j];
-        double px = (double)cx * geo.k * g + (double)p.x;
-        double py = (double)cy * geo.k * g + (double)p.y;
+        double px = (double)(cell_x(cw) * geo.k) * g + (double)p.x;
+        double py = (double)(cell_y(cw) * geo.k) * g + (double)p.y;
         px = px <= 0.0 ? px + L0 : (px > L0 ? px - L0 : px);
         py = py <= 0.0 ? py + L1 : (py > L1 ? py - L1 : py);
         const int64_t o = pid[j];
@@ -380,8 +515,10 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 
 }  // namespace
 
+int64_t step_blocks(int64_t n) { return (n + kStepThreads - 1) / kStepThreads; }
+
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
-    const int64_t blocks = (a.n + kStepThreads - 1) / kStepThreads;
+    const int64_t blocks = step_blocks(a.n);
     if (blocks < 1) return cudaSuccess;
     const dim3 grid((unsigned)blocks), block(kStepThreads);
     if (mode == kModeStep) {
@@ -406,18 +543,20 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {
     k_scan_local<<<(unsigned)nb, kScanThreads, 0, s>>>(a.count, a.ncells, a.block_sums);
     k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
     k_sort_place<<<grid_for(a.n, t), t, 0, s>>>(a);
-    k_sort_cells<<<grid_for(a.ncells, t), t, 0, s>>>(a);
+    k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
+    k_sort_scatter<<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    if (a.nbr) k_nlist<<<grid_for(a.n, 128, 16), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
-                        int32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                        uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
                         cudaStream_t s) {
     k_pack<<<grid_for(n, 256), 256, 0, s>>>(geo, n, x, v, cell, cl, vel, pid, ctl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const Geom &geo, int64_t n, const int32_t *cell, const float2 *cl,
+cudaError_t launch_unpack(const Geom &geo, int64_t n, const uint32_t *cell, const float2 *cl,
                           const float2 *vsync, const float2 *fsync, const int32_t *pid,
                           double *x, double *v, double *f, cudaStream_t s) {
     k_unpack<<<grid_for(n, 256), 256, 0, s>>>(geo, n, cell, cl, vsync, fsync, pid, x, v, f);

@@ -61,8 +61,11 @@ def test_forces_full_size_sampled(cuda):
     _force_check(f[which], f_ref, scale)
 
 
-@pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3)])
+@pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3),
+                                               (4096, 0.3, 1000)])
 def test_ten_step_trajectory(cuda, n, rho, sort_every):
+    # sort_every = 1000: the Verlet list goes stale mid-run and the step kernel
+    # switches to the cell stencil of the current displacement bound
     L = mi.box_for(n, rho, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=n)
     ref = oracle.VV(x0, v0, (L, L), dt=0.005).run(10)
@@ -73,6 +76,21 @@ def test_ten_step_trajectory(cuda, n, rho, sort_every):
     assert np.abs(_min_image(x - ref.x, L)).max() <= 1e-4
     assert np.abs(v - ref.v).max() <= 1e-3
     assert st["status"] == 0 and st["step"] == 10
+
+
+def test_late_resort_uses_wider_stencil(cuda):
+    # 60 steps without a re-sort: the displacement bound grows past the skin,
+    # so forces come from the cell stencil (radius 2 once 2D > skin); the
+    # trajectory still follows the FP64 oracle.
+    n, L = 4096, mi.box_for(4096, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=77)
+    ref = oracle.VV(x0, v0, (L, L), dt=0.005).run(60)
+    with _sim(n, L, x0, v0, sort_every=100000) as s:
+        s.step(60)
+        x, _ = s.get_state()
+        st, _, _ = s.stats()
+    assert np.abs(_min_image(x - ref.x, L)).max() <= 1e-3
+    assert st["status"] == 0
 
 
 def test_fp64_reductions_at_start(cuda):

@@ -406,7 +406,7 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
         const double rho = (double)n / (p.box[0] * p.box[1]);
         const double mean = rho * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
-        if (c->cap > 4096) c->cap = 4096;
+        if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x cap words of shared memory
         if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
             return fail(rc);
     }

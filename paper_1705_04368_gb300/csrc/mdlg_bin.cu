@@ -108,7 +108,10 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
 
 // Binning of the simulation state (sorted by MD cell) for the lags in `mask`:
 // the lattice cell now versus the one stored at the lag's previous binning,
-// which is then replaced.  Lag 0 may also write per-site outputs.
+// which is then replaced.  Lag 0 may also write per-site outputs.  Every load
+// of an iteration is issued before any of its stores (a store followed by a
+// load the compiler cannot prove independent stalls the thread), and the lag
+// loop is unrolled over the compile-time maximum, predicated by the mask.
 __global__ void k_bin_state(StateBinArgs sa) {
     extern __shared__ uint32_t sh[];
     const Geom &geo = sa.geo;
@@ -120,6 +123,10 @@ __global__ void k_bin_state(StateBinArgs sa) {
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < sa.n; base += stride) {
         const int64_t j = base + threadIdx.x;
         const bool act = j < sa.n;
+        uint32_t before[kMaxLags];
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            before[l] = (act && ((sa.mask >> l) & 1u)) ? sa.lprev[l][j] : 0u;
         int32_t lx = 0, ly = 0;
         if (act) {
             const uint32_t c = sa.cell[j];
@@ -131,13 +138,13 @@ __global__ void k_bin_state(StateBinArgs sa) {
             ly = lattice_of_base(by, geo.ratio, sa.ratio_shift);
         }
         const uint32_t now = pack_cell(lx, ly);
-        for (int l = 0; l < sa.nlags; ++l) {
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l) {
             if (!((sa.mask >> l) & 1u)) continue;
             int32_t bin = 0;
             if (act) {
-                const uint32_t before = sa.lprev[l][j];
-                const int32_t vx = lattice_disp(lx - (int32_t)(before & 0xffffu), geo.lat[0]);
-                const int32_t vy = lattice_disp(ly - (int32_t)(before >> 16), geo.lat[1]);
+                const int32_t vx = lattice_disp(lx - (int32_t)(before[l] & 0xffffu), geo.lat[0]);
+                const int32_t vy = lattice_disp(ly - (int32_t)(before[l] >> 16), geo.lat[1]);
                 bin = vel_index(vx, vy, geo.vmax);
                 sa.lprev[l][j] = now;
                 if (l == 0 && sa.site_n) {
@@ -150,7 +157,8 @@ __global__ void k_bin_state(StateBinArgs sa) {
         }
     }
     __syncthreads();
-    for (int l = 0; l < sa.nlags; ++l)
+#pragma unroll
+    for (int l = 0; l < kMaxLags; ++l)
         if ((sa.mask >> l) & 1u) flush_hist(sh + l * q1, q1, sa.counts[l]);
 }
 

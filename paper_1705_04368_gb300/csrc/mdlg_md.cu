@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kStepThreads = 128;
 constexpr int kListBatch = 8;       // list entries loaded before any is used
+constexpr int kNlistThreads = 64;   // list-build block (entries staged in shared memory)
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 cells per scan block
@@ -399,15 +400,23 @@ __global__ void k_sort_scatter(SortArgs a) {
         int32_t rank = 0;
         for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
         const int32_t to = s + rank;
+        // every load before any store (see k_bin_state)
         const uint32_t ow = a.cell_in[from];
         const float2 p = a.cl_in[from];
+        const float2 vv = a.v_in[from];
+        const int32_t pid = a.pid_in[from];
+        uint32_t lp[kMaxLags];
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l) lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
         const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
         const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
         a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
-        a.v_out[to] = a.v_in[from];
-        a.pid_out[to] = a.pid_in[from];
+        a.v_out[to] = vv;
+        a.pid_out[to] = pid;
         a.cell_out[to] = cw;
-        for (int l = 0; l < a.nlags; ++l) a.lprev_out[l][to] = a.lprev_in[l][from];
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            if (l < a.nlags) a.lprev_out[l][to] = lp[l];
     }
 }
 
@@ -417,41 +426,50 @@ __global__ void k_sort_scatter(SortArgs a) {
 // (predicated) so their loads overlap.  Column-major: entry t of particle i at
 // nbr[t n + i].  A particle with more than `cap` entries stores cap + 1 as its
 // count and is handled through the cell stencil by the step kernel.
-__global__ void k_nlist(SortArgs a) {
+__global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
+    // entries are staged in shared memory and written after the search, so
+    // that no global store precedes a candidate load (see k_bin_state)
+    extern __shared__ uint32_t s_ent[];          // kNlistThreads x cap, column-major
     const Geom &geo = a.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const uint32_t cw = a.cell_out[i];
-        const int32_t cx = cell_x(cw), cy = cell_y(cw);
-        const float2 p = a.cl_out[i];
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
         int cnt = 0;
-        for (int oy = -1; oy <= 1; ++oy) {
-            const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
-            const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
-                const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
-                const int32_t cn = ny * geo.nc[0] + nx;
-                const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
-                const uint32_t code = ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
-                for (int32_t b = s; b < e; b += 4) {
-                    float2 q[4];
+        if (i < a.n) {
+            const uint32_t cw = a.cell_out[i];
+            const int32_t cx = cell_x(cw), cy = cell_y(cw);
+            const float2 p = a.cl_out[i];
+            for (int oy = -1; oy <= 1; ++oy) {
+                const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
+                const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
+                    const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
+                    const int32_t cn = ny * geo.nc[0] + nx;
+                    const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+                    const uint32_t code = ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
+                    for (int32_t b = s; b < e; b += 4) {
+                        float2 q[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        q[u] = (b + u < e) ? __ldg(a.cl_out + b + u) : make_float2(1.0e18f, 1.0e18f);
+                        for (int u = 0; u < 4; ++u)
+                            q[u] = (b + u < e) ? __ldg(a.cl_out + b + u)
+                                               : make_float2(1.0e18f, 1.0e18f);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int32_t j = b + u;
-                        const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                        if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
-                            if (cnt < a.cap) a.nbr[(int64_t)cnt * a.n + i] = (uint32_t)j | code;
-                            ++cnt;
+                        for (int u = 0; u < 4; ++u) {
+                            const int32_t j = b + u;
+                            const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
+                            if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
+                                if (cnt < a.cap) s_ent[cnt * kNlistThreads + threadIdx.x] = (uint32_t)j | code;
+                                ++cnt;
+                            }
                         }
                     }
                 }
             }
+            const int keep = cnt < a.cap ? cnt : a.cap;
+            for (int t = 0; t < keep; ++t) a.nbr[(int64_t)t * a.n + i] = s_ent[t * kNlistThreads + threadIdx.x];
+            a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
         }
-        a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
     }
 }
 
@@ -545,7 +563,14 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {
     k_sort_place<<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
     k_sort_scatter<<<grid_for(a.n, t, 16), t, 0, s>>>(a);
-    if (a.nbr) k_nlist<<<grid_for(a.n, 128, 16), 128, 0, s>>>(a);
+    if (a.nbr) {
+        const size_t smem = sizeof(uint32_t) * (size_t)kNlistThreads * a.cap;
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_nlist<<<grid_for(a.n, kNlistThreads, 32), kNlistThreads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

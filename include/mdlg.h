@@ -247,6 +247,43 @@ int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t nco
                       const float *dxs, const float *dts, int32_t vmax,
                       uint64_t *counts, void *stream);
 
+/*
+ * mdlg_forces_static -- Lennard-Jones forces and FP64 observables of one
+ * configuration, computed without allocating any memory.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory where they need a force evaluation -- code inside a CUDA graph being
+ * captured (an allocation there breaks the capture), frameworks whose memory
+ * pool owns every allocation, or real-time loops that must not block in the
+ * allocator.  It computes what a context computes at a statistics step
+ * (pack, neighbour-cell sort, the step kernel's force/reduction mode with a
+ * zero time step), with every intermediate array in one statically sized
+ * device array of the library instead of allocated scratch.
+ *   params : as for mdlg_create; only n, box, potential (must be
+ *            MDLG_POT_LJ_TS), eps, sigma, mass, rcut, grid and skin are used.
+ *   x, v   : device, n x 2 FP64 positions in (0, L] and velocities (inputs).
+ *   f      : device, n x 2 FP64 forces F_i (output, original particle order).
+ *   obs    : device, 5 FP64 (output): kinetic energy, potential energy,
+ *            virial, momentum x, momentum y -- as in mdlg_stats_out.
+ *   status : device, one int32 (output, may be NULL): 0, or MDLG_ENONFINITE if
+ *            a position was outside the box or a value was not finite.
+ *   stream : cudaStream_t (as void*); all work is enqueued there, nothing
+ *            synchronizes.
+ * Limits: n <= MDLG_STATIC_MAX_N and at most MDLG_STATIC_MAX_CELLS neighbour
+ * cells (box area / (cell side)^2, cell side = grid * ceil((rcut+skin)/grid));
+ * larger inputs return MDLG_EOVERFLOW before any GPU work.  The static array
+ * (about 6 MB) exists on every GPU that loads the library and is held until
+ * the process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents; calls whose GPU work overlaps (other
+ * streams, other host threads) race and corrupt each other: serialize them.
+ * Errors: MDLG_EINVAL, MDLG_EOVERFLOW, MDLG_ECUDA.
+ */
+#define MDLG_STATIC_MAX_N     65536
+#define MDLG_STATIC_MAX_CELLS 65536
+int mdlg_forces_static(const mdlg_params *params, const double *x, const double *v, double *f,
+                       double *obs, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ from . import _build
 MAX_LAGS = 8
 MAX_VMAX = 15
 MAX_COMBOS = 16
+STATIC_MAX_N = 65536      # mdlg_forces_static particle limit (MDLG_STATIC_MAX_N)
 POT_NONE = 0
 POT_LJ_TS = 1
 SITES_FIELD = 1
@@ -86,6 +87,7 @@ _SIGNATURES = {
     "mdlg_bin": (ctypes.c_int, [ctypes.POINTER(_Lattice), ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "mdlg_idealgas_bin": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P,
                                          ctypes.c_int32, _P, _P]),
+    "mdlg_forces_static": (ctypes.c_int, [ctypes.POINTER(_Params), _P, _P, _P, _P, _P, _P]),
 }
 
 

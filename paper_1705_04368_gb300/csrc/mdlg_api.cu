@@ -352,7 +352,9 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     // rounding slack of one drift update: a few ulps of the largest offset
     c->round_margin = (float)(4.0 * std::ldexp(1.0, -23) * (2.0 * g.k * p.grid));
 
-    // re-sort interval: half the skin covered at 1.3x the fastest initial speed
+    // re-sort interval: half the skin covered at 1.15x the fastest initial speed (if the
+    // bound tracked on the device grows past it earlier, the step kernel uses the
+    // cell stencil for the remaining steps, so a late sort costs time, not accuracy)
     double vmax0 = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         const double s2 = v0[2 * i] * v0[2 * i] + v0[2 * i + 1] * v0[2 * i + 1];
@@ -363,7 +365,7 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
         c->sort_every = p.sort_every;
     } else {
         const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
-        const double v = std::fmax(vmax0 * 1.3, 1e-12);
+        const double v = std::fmax(1.15 * vmax0, 1e-12);
         double k = std::floor(0.5 * skin_eff / (v * p.dt));
         c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
     }

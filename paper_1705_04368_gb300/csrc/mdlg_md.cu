@@ -76,7 +76,7 @@ template <bool STATS>
 __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy, PairAcc &acc) {
     const float r2 = fmaf(dx, dx, dy * dy);
     if (r2 < a.rc2) {
-        const float ir2 = __frcp_rn(r2);
+        const float ir2 = __fdividef(1.0f, r2);   // hardware reciprocal, <= 2 ulp
         const float sr2 = a.sig2 * ir2;
         const float sr6 = sr2 * sr2 * sr2;
         const float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
@@ -86,6 +86,26 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
             acc.pe += a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
             acc.vir = fmaf(fs, r2, acc.vir);
         }
+    }
+}
+
+// The same term without a branch: evaluated for every list slot and masked, so
+// the lanes of a warp never diverge inside a batch.  Far or empty slots give a
+// tiny finite r^-2, multiplied by a zero mask.
+template <bool STATS>
+__device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, float dy,
+                                                 PairAcc &acc) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float on = r2 < a.rc2 ? 1.0f : 0.0f;
+    const float ir2 = __fdividef(1.0f, r2);   // hardware reciprocal, <= 2 ulp
+    const float sr2 = a.sig2 * ir2;
+    const float sr6 = sr2 * sr2 * sr2;
+    const float fs = on * (a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f));
+    acc.fx = fmaf(fs, dx, acc.fx);
+    acc.fy = fmaf(fs, dy, acc.fy);
+    if (STATS) {
+        acc.pe = fmaf(on, a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift, acc.pe);
+        acc.vir = fmaf(fs, r2, acc.vir);
     }
 }
 
@@ -122,17 +142,17 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, int64_t i, int32
 // Pairs from the Verlet list built at the last sort: entry t of particle i is
 // nbr[t n + i] = j | (ox + 1) << 28 | (oy + 1) << 30 with (ox, oy) the offset of
 // j's cell from i's cell.  Entries are fetched kListBatch at a time so that
-// their loads (and the dependent position loads) overlap.
-template <bool STATS>
-__device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, int32_t cx, int32_t cy,
-                                            float2 p, int cnt, PairAcc &acc) {
-    const Geom &geo = a.geo;
-    const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-    const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-    const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-    const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+// their loads (and the dependent position loads) overlap.  For a particle whose
+// neighbouring cells are all full-width and unwrapped (REGULAR), the origin
+// shift is (code - 1) w; at the periodic edges and next to the wider last
+// cell it is looked up from the four per-particle shifts.
+template <bool STATS, bool REGULAR>
+__device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
+                                            float sxm, float sxp, float sym, float syp,
+                                            PairAcc &acc) {
     const uint32_t *e = a.nbr + i;
     const int64_t n = a.n;
+    const float w = a.cell_w;
     for (int t0 = 0; t0 < cnt; t0 += kListBatch) {
         uint32_t ent[kListBatch];
 #pragma unroll
@@ -145,10 +165,16 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, int32_
                                         : make_float2(1.0e18f, 1.0e18f);
 #pragma unroll
         for (int u = 0; u < kListBatch; ++u) {
-            const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
-            const float sx = ox == 0u ? sxm : (ox == 2u ? sxp : 0.0f);
-            const float sy = oy == 0u ? sym : (oy == 2u ? syp : 0.0f);
-            pair_term<STATS>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
+            float sx, sy;
+            if (REGULAR) {
+                sx = fmaf((float)((ent[u] >> 28) & 3u), w, -w);
+                sy = fmaf((float)(ent[u] >> 30), w, -w);
+            } else {
+                const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
+                sx = ox == 0u ? sxm : (ox == 2u ? sxp : 0.0f);
+                sy = oy == 0u ? sym : (oy == 2u ? syp : 0.0f);
+            }
+            pair_term_masked<STATS>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
         }
     }
 }
@@ -180,7 +206,15 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
             const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
             if (cnt <= a.cap) {
-                forces_list<STATS>(a, i, cx, cy, p, cnt, acc);
+                const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                const float w = a.cell_w;
+                if (sxm == -w && sxp == w && sym == -w && syp == w)
+                    forces_list<STATS, true>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
+                else
+                    forces_list<STATS, false>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
             } else {
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);
@@ -394,13 +428,9 @@ __global__ void k_sort_scatter(SortArgs a) {
         const unsigned long long et = a.entry[t];
         const int32_t from = (int32_t)(et & 0xffffffffu);
         const uint32_t my_pid = (uint32_t)(et >> 32);
-        const uint32_t cw = a.key[from];
-        const int32_t c = lin(geo, cw);
-        const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
-        int32_t rank = 0;
-        for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
-        const int32_t to = s + rank;
+        // every gather from the old order first (independent of the rank), and
         // every load before any store (see k_bin_state)
+        const uint32_t cw = a.key[from];
         const uint32_t ow = a.cell_in[from];
         const float2 p = a.cl_in[from];
         const float2 vv = a.v_in[from];
@@ -408,6 +438,11 @@ __global__ void k_sort_scatter(SortArgs a) {
         uint32_t lp[kMaxLags];
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l) lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
+        const int32_t c = lin(geo, cw);
+        const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
+        int32_t rank = 0;
+        for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
+        const int32_t to = s + rank;
         const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
         const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
         a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
@@ -439,15 +474,49 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
             const uint32_t cw = a.cell_out[i];
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
             const float2 p = a.cl_out[i];
+            // x offsets of the three columns (wrapped at the periodic edges)
+            const float sxm = (float)wrap_half((wrap_mod(cx - 1, geo.nc[0]) - cx) * geo.k, geo.lg[0]) * geo.g;
+            const float sxp = (float)wrap_half((wrap_mod(cx + 1, geo.nc[0]) - cx) * geo.k, geo.lg[0]) * geo.g;
+            const bool interior = cx >= 1 && cx + 1 < geo.nc[0];
             for (int oy = -1; oy <= 1; ++oy) {
                 const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
                 const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
+                const uint32_t ycode = (uint32_t)(oy + 1) << 30;
+                const int32_t row = ny * geo.nc[0];
+                if (interior) {
+                    // cells cx-1, cx, cx+1 of this row are one contiguous range
+                    const int32_t s = __ldg(a.cell_start + row + cx - 1);
+                    const int32_t m1 = __ldg(a.cell_start + row + cx);
+                    const int32_t m2 = __ldg(a.cell_start + row + cx + 1);
+                    const int32_t e = __ldg(a.cell_start + row + cx + 2);
+                    for (int32_t b = s; b < e; b += 4) {
+                        float2 q[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            q[u] = (b + u < e) ? __ldg(a.cl_out + b + u)
+                                               : make_float2(1.0e18f, 1.0e18f);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int32_t j = b + u;
+                            const int ox = (j >= m1) + (j >= m2) - 1;
+                            const float odx = ox < 0 ? sxm : (ox > 0 ? sxp : 0.0f);
+                            const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
+                            if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
+                                if (cnt < a.cap)
+                                    s_ent[cnt * kNlistThreads + threadIdx.x] =
+                                        (uint32_t)j | ((uint32_t)(ox + 1) << 28) | ycode;
+                                ++cnt;
+                            }
+                        }
+                    }
+                    continue;
+                }
                 for (int ox = -1; ox <= 1; ++ox) {
                     const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
-                    const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
-                    const int32_t cn = ny * geo.nc[0] + nx;
+                    const float odx = ox < 0 ? sxm : (ox > 0 ? sxp : 0.0f);
+                    const int32_t cn = row + nx;
                     const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
-                    const uint32_t code = ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
+                    const uint32_t code = ((uint32_t)(ox + 1) << 28) | ycode;
                     for (int32_t b = s; b < e; b += 4) {
                         float2 q[4];
 #pragma unroll

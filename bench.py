@@ -252,6 +252,9 @@ def run_ours(args, rank, world, local_rank):
     # ideal-gas single pass (binning throughput), rotating buffers > 2x L2
     ig = _idealgas(m, torch, dev, stream, hbm_gbs)
 
+    # batched replicas (256 systems) against the same systems one context at a time
+    batched = _batched(m, torch, stream, local_rank) if rank == 0 else None
+
     # end to end through the C ABI: pinned host state in, f_i out, every step
     e2e = _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev)
 
@@ -260,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(c, world), "roofline": roofline,
             "gpu_launches": launches, "kernels": kernels, "clocks": clk, "e2e": e2e,
-            "idealgas": ig, "status": st["status"]}
+            "idealgas": ig, "batched": batched, "status": st["status"]}
     if rank == 0:
         if world == 1:
             v, secs = _oracle_sample(c, x0, v0)
@@ -299,6 +302,47 @@ def _idealgas(m, torch, dev, stream, hbm_gbs):
     return {"workload": "idealgas_n4194304_L2048_9combos", "particles_per_s": n / s,
             "us_per_pass": s * 1e6, "achieved_gbs": gbs, "frac_hbm": gbs / hbm_gbs,
             "bin_decisions_per_s": n * len(combos) / s}
+
+
+def _batched(m, torch, stream, local_rank, md_steps=140, warm=14):
+    """256 replicas (N log-uniform in [1k, 64k], rho uniform in [0.1, 0.6], T = 1,
+    dx = 4, lag 50): particle-steps/s advanced as one batch versus one context per
+    system, same sort interval for both."""
+    ns, boxes, seeds = mi.batch_recipe()
+    x0, v0 = mi.batch_states(ns, boxes, seeds)
+    params = m.Params(n=0, box=64.0, dx=4.0, lag_steps=(50,), sort_every=7)
+    total = int(ns.sum())
+    with m.BatchSimulation(params, ns, boxes, x0, v0, stream=stream, device=local_rank) as bt:
+        bt.step(warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.step(md_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3
+        st, _, _ = bt.stats()
+    sims, off = [], 0
+    for n, b in zip(ns, boxes):
+        p = m.Params(n=int(n), box=float(b[0]), dx=4.0, lag_steps=(50,), sort_every=7)
+        sims.append(m.Simulation(p, x0[off:off + n], v0[off:off + n], stream=stream,
+                                 device=local_rank))
+        off += int(n)
+    for sm in sims:
+        sm.step(warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sm in sims:
+        sm.step(md_steps)
+    torch.cuda.synchronize()
+    t_alone = time.perf_counter() - t0
+    for sm in sims:
+        sm.close()
+    return {"workload": "lj2d_batch256_n1k-64k_rho0.1-0.6_T1", "systems": len(ns),
+            "particles": total, "md_steps": md_steps,
+            "batched_particle_steps_per_s": total * md_steps / t_batch,
+            "one_context_each_particle_steps_per_s": total * md_steps / t_alone,
+            "speedup": t_alone / t_batch, "status": st["status"]}
 
 
 def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev):

@@ -129,6 +129,35 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
                 const mdlg_allocator *allocator, void *stream, mdlg_ctx **out);
 
 /*
+ * mdlg_create_batch -- one context holding nsys independent systems that share
+ * every parameter except the particle count and the box (an ensemble for the
+ * averages of Eq. fieq, Sec. IV-A).  All systems advance together: each
+ * kernel launch of mdlg_step covers every system, and each system's forces,
+ * trajectory and counts are exactly those of a context made for it alone with
+ * the same sort_every (set sort_every > 0 to compare).
+ *   params : shared parameters; params->n and params->box are ignored and
+ *            params->site_mode must be 0.
+ *   nsys   : systems, 1..65535.
+ *   n      : host, nsys particle counts (the total below 2^28).
+ *   box    : host, nsys x 2 box sides, each a multiple of params->dx.
+ *   x0, v0 : host, (sum n) x 2 FP64 positions and velocities, system after
+ *            system in the order of n.
+ * mdlg_stats then reports all systems together (counts added, f_i over the
+ * total particle number); mdlg_stats_system reports one.  mdlg_get_state
+ * returns the concatenated state.  Errors as mdlg_create.
+ */
+int mdlg_create_batch(const mdlg_params *params, int32_t nsys, const int64_t *n,
+                      const double *box, const double *x0, const double *v0,
+                      const mdlg_allocator *allocator, void *stream, mdlg_ctx **out);
+
+/*
+ * mdlg_stats_system -- mdlg_stats for one system of a batch (0-based index);
+ * MDLG_EINVAL for a context made by mdlg_create or an index out of range.
+ */
+int mdlg_stats_system(mdlg_ctx *ctx, int32_t system, mdlg_stats_out *out, uint64_t *counts,
+                      double *fi);
+
+/*
  * mdlg_step -- enqueue nsteps velocity-Verlet steps of the Newton equations
  * (Sec. III) with Lennard-Jones forces (Sec. IV).  After every MD step whose
  * count is a multiple of lag_steps[k], the particles are binned for lag k

@@ -178,3 +178,27 @@ PRODUCTION_LJ_DENSE = LJConfig("lj2d_n4194304_rho0.6_T0.8", n=4_194_304, rho=0.6
 IDEALGAS_N = 1 << 22
 IDEALGAS_BOX = 2048.0
 IDEALGAS_COMBOS = tuple((dx, dt) for dx in (1.0, 2.0, 4.0) for dt in (0.5, 1.0, 2.0))
+
+
+def batch_recipe(nsys: int = 256, seed: int = 4, n_lo: int = 1000, n_hi: int = 65536,
+                 rho_lo: float = 0.1, rho_hi: float = 0.6, dx: float = 4.0):
+    """Replica ensemble: N log-uniform in [n_lo, n_hi], rho uniform in [rho_lo, rho_hi].
+
+    Returns (ns, boxes, seeds); each box is sqrt(N / rho) rounded up to a multiple of dx.
+    """
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), nsys)).astype(np.int64)
+    rhos = rng.uniform(rho_lo, rho_hi, nsys)
+    boxes = np.array([[box_for(int(n), float(r), dx)] * 2 for n, r in zip(ns, rhos)])
+    seeds = 1000 + np.arange(nsys)
+    return ns, boxes, seeds
+
+
+def batch_states(ns, boxes, seeds, temperature: float = 1.0):
+    """Concatenated initial states of a replica ensemble."""
+    xs, vs = [], []
+    for n, b, sd in zip(ns, boxes, seeds):
+        x, v = lj_initial_state(int(n), float(b[0]), temperature, int(sd))
+        xs.append(x)
+        vs.append(v)
+    return np.concatenate(xs), np.concatenate(vs)

@@ -75,6 +75,9 @@ _P = ctypes.c_void_p
 _SIGNATURES = {
     "mdlg_create": (ctypes.c_int, [ctypes.POINTER(_Params), _P, _P, ctypes.POINTER(_Allocator), _P,
                                    ctypes.POINTER(_P)]),
+    "mdlg_create_batch": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int32, _P, _P, _P, _P,
+                                         ctypes.POINTER(_Allocator), _P, ctypes.POINTER(_P)]),
+    "mdlg_stats_system": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_Stats), _P, _P]),
     "mdlg_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "mdlg_stats": (ctypes.c_int, [_P, ctypes.POINTER(_Stats), _P, _P]),
     "mdlg_get_state": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -293,6 +296,51 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class BatchSimulation(Simulation):
+    """Several independent systems advanced together (mdlg_create_batch).
+
+    ``ns`` particle counts, ``boxes`` (nsys, 2) box sides, ``x0``/``v0`` the
+    concatenated (sum ns, 2) initial states.  ``params.n``/``params.box`` are
+    ignored.  ``stats()`` adds all systems; ``stats_system(k)`` reports one.
+    """
+
+    def __init__(self, params: Params, ns, boxes, x0, v0, stream=None, device: int = 0,
+                 torch_memory: bool = True):
+        self.ns = np.ascontiguousarray(ns, dtype=np.int64)
+        self.boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 2)
+        total = int(self.ns.sum())
+        self.params = Params(**{**params.__dict__, "n": total})
+        self._lib = lib()
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        if x0.shape != (total, 2) or v0.shape != (total, 2):
+            raise ValueError("x0 and v0 must be (sum ns, 2)")
+        self._stream = _stream_handle(stream)
+        self._alloc = _TorchAllocator(device, self._stream) if torch_memory else None
+        self._cparams = self.params.to_c()
+        h = ctypes.c_void_p()
+        rc = self._lib.mdlg_create_batch(ctypes.byref(self._cparams), len(self.ns),
+                                         self.ns.ctypes.data, self.boxes.ctypes.data,
+                                         x0.ctypes.data, v0.ctypes.data,
+                                         ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                         self._stream, ctypes.byref(h))
+        _check(rc, "mdlg_create_batch")
+        self._h = h
+
+    def stats_system(self, k: int):
+        out = _Stats()
+        nl, q1 = len(self.params.lag_steps), self.params.q1
+        counts = np.zeros((nl, q1), np.uint64)
+        fi = np.zeros((nl, q1), np.float64)
+        _check(self._lib.mdlg_stats_system(self._h, int(k), ctypes.byref(out), counts.ctypes.data,
+                                           fi.ctypes.data), "mdlg_stats_system")
+        d = {k2: getattr(out, k2) for k2 in ("step", "stats_step", "kinetic", "potential",
+                                             "virial", "temperature", "pressure", "status")}
+        d["momentum"] = (out.momentum[0], out.momentum[1])
+        d["intervals"] = [out.intervals[i] for i in range(nl)]
+        return d, counts, fi
 
 
 def bin_snapshots(base: Sequence[int], ratio: int, vmax: int, idx_prev, idx_cur, counts,

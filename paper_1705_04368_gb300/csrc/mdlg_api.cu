@@ -19,7 +19,13 @@ struct mdlg_ctx {
     mdlg_allocator alloc{};
     bool use_cuda_malloc = true;
     std::vector<void *> owned;
-    int64_t ncells = 0;
+    int64_t ncells = 0;            // all cells (a batch: every system's cells + its ghost cell)
+    int64_t slots = 0;             // particle array length (a batch: padded per system)
+    int32_t nsys = 0;              // 0: one system (geo); >0: a batch of nsys systems
+    std::vector<SysInfo> sys_host;
+    SysInfo *sys_dev = nullptr;
+    uint16_t *chunk_sys = nullptr;
+    long long *bstats = nullptr;   // nsys x 5 fixed-point sums (batch statistics)
     int32_t ratio_shift = -1;
     int32_t q1 = 0;
     // double-buffered state: position/velocity swap every step, the rest at sorts
@@ -69,6 +75,12 @@ int cuda_err(cudaError_t e) {
     do {                               \
         int rc__ = (expr);             \
         if (rc__ != MDLG_OK) return rc__; \
+    } while (0)
+
+#define MDLG_TRY_OR(expr, handler)            \
+    do {                                      \
+        int rc__ = (expr);                    \
+        if (rc__ != MDLG_OK) return handler(rc__); \
     } while (0)
 
 void *dev_alloc(mdlg_ctx *c, size_t bytes) {
@@ -175,10 +187,22 @@ int validate(const mdlg_params *p) {
     return MDLG_OK;
 }
 
+Batch batch_of(mdlg_ctx *c) {
+    Batch b{};
+    if (c->nsys > 0) {
+        b.sys = c->sys_dev;
+        b.chunk_sys = c->chunk_sys;
+        b.stats = c->bstats;
+        b.nsys = c->nsys;
+    }
+    return b;
+}
+
 StepArgs step_args(mdlg_ctx *c) {
     StepArgs a{};
     a.geo = c->geo;
-    a.n = c->p.n;
+    a.n = c->slots;
+    a.batch = batch_of(c);
     a.cell = c->cell[c->meta_cur];
     a.cell_start = c->cell_start;
     a.cl_in = c->cl[c->pos_cur];
@@ -214,7 +238,8 @@ StepArgs step_args(mdlg_ctx *c) {
 StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
     StateBinArgs b{};
     b.geo = c->geo;
-    b.n = c->p.n;
+    b.n = c->slots;
+    b.batch = batch_of(c);
     b.ratio_shift = c->ratio_shift;
     b.nlags = c->p.nlags;
     b.mask = mask;
@@ -232,7 +257,8 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
 int do_sort(mdlg_ctx *c) {
     SortArgs s{};
     s.geo = c->geo;
-    s.n = c->p.n;
+    s.n = c->slots;
+    s.batch = batch_of(c);
     s.nlags = c->p.nlags;
     s.ncells = c->ncells;
     const int pi = c->pos_cur, mi = c->meta_cur;
@@ -269,7 +295,15 @@ int do_sort(mdlg_ctx *c) {
     return MDLG_OK;
 }
 
+// A batch's per-system statistics are accumulated with atomics: zero them
+// before every statistics launch.
+int zero_bstats(mdlg_ctx *c) {
+    if (c->nsys == 0) return MDLG_OK;
+    return cuda_err(cudaMemsetAsync(c->bstats, 0, sizeof(long long) * 5 * c->nsys, c->stream));
+}
+
 int sync_stats(mdlg_ctx *c, bool with_force) {
+    MDLG_TRY(zero_bstats(c));
     StepArgs a = step_args(c);
     a.stats = 1;
     if (!with_force) a.f_sync = c->fsync;   // buffer always present; harmless
@@ -307,27 +341,12 @@ const char *mdlg_strerror(int code) {
     }
 }
 
-int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
-                const mdlg_allocator *allocator, void *stream, mdlg_ctx **out) {
-    if (!out) return MDLG_EINVAL;
-    *out = nullptr;
-    MDLG_TRY(validate(params));
-    if (!x0 || !v0) return MDLG_EINVAL;
-    if (allocator && (!allocator->alloc || !allocator->free)) return MDLG_EINVAL;
+}  // extern "C"
 
-    mdlg_ctx *c = new (std::nothrow) mdlg_ctx();
-    if (!c) return MDLG_ENOMEM;
-    c->p = *params;
-    c->stream = static_cast<cudaStream_t>(stream);
-    if (allocator) {
-        c->alloc = *allocator;
-        c->use_cuda_malloc = false;
-    }
-    const mdlg_params &p = c->p;
-    const int64_t n = p.n;
+namespace {
 
-    // geometry
-    Geom &g = c->geo;
+// Geometry of one system (box per axis) under the shared parameters.
+int system_geom(const mdlg_params &p, const double box[2], Geom &g) {
     g.g = (float)p.grid;
     g.inv_g = (float)(1.0 / p.grid);
     g.ratio = (int32_t)exact_ratio(p.dx, p.grid);
@@ -335,17 +354,96 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     g.k = (int32_t)std::ceil(reach / p.grid - 1e-12);
     if (g.k < 1) g.k = 1;
     for (int a = 0; a < 2; ++a) {
-        g.lg[a] = (int32_t)exact_ratio(p.box[a], p.grid);
-        g.lat[a] = (int32_t)exact_ratio(p.box[a], p.dx);
+        g.lg[a] = (int32_t)exact_ratio(box[a], p.grid);
+        g.lat[a] = (int32_t)exact_ratio(box[a], p.dx);
         g.nc[a] = g.lg[a] / g.k;
-        if (g.lg[a] % g.ratio) { delete c; return MDLG_EINVAL; }
+        if (g.lg[a] % g.ratio) return MDLG_EINVAL;
     }
     g.vmax = p.vmax;
-    if (p.potential == MDLG_POT_LJ_TS && (g.nc[0] < 3 || g.nc[1] < 3)) { delete c; return MDLG_EINVAL; }
+    if (p.potential == MDLG_POT_LJ_TS && (g.nc[0] < 3 || g.nc[1] < 3)) return MDLG_EINVAL;
     if (g.nc[0] < 1) g.nc[0] = 1;
     if (g.nc[1] < 1) g.nc[1] = 1;
-    c->ncells = (int64_t)g.nc[0] * g.nc[1];
-    if (c->ncells > (int64_t)4096 * 4096) { delete c; return MDLG_EINVAL; }
+    return MDLG_OK;
+}
+
+// One system (nsys = 0: params->n, params->box) or a batch of nsys systems
+// (ns[s] particles in box boxes[2s], boxes[2s+1]; x0/v0 concatenated).
+int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, const double *boxes,
+                const double *x0, const double *v0, const mdlg_allocator *allocator, void *stream,
+                mdlg_ctx **out) {
+    if (!out) return MDLG_EINVAL;
+    *out = nullptr;
+    if (!params || !x0 || !v0) return MDLG_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->free)) return MDLG_EINVAL;
+    int64_t ntot = params->n;
+    if (nsys > 0) {
+        if (!ns || !boxes || nsys > 65535) return MDLG_EINVAL;
+        if (params->site_mode) return MDLG_EINVAL;   // per-site outputs: single systems only
+        ntot = 0;
+        for (int32_t k = 0; k < nsys; ++k) {
+            mdlg_params q = *params;
+            q.n = ns[k];
+            q.box[0] = boxes[2 * k];
+            q.box[1] = boxes[2 * k + 1];
+            MDLG_TRY(validate(&q));
+            ntot += ns[k];
+        }
+        if (ntot >= (1LL << 28)) return MDLG_EINVAL;
+    } else if (nsys < 0) {
+        return MDLG_EINVAL;
+    } else {
+        MDLG_TRY(validate(params));
+    }
+
+    mdlg_ctx *c = new (std::nothrow) mdlg_ctx();
+    if (!c) return MDLG_ENOMEM;
+    c->p = *params;
+    c->p.n = ntot;
+    c->nsys = nsys;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (allocator) {
+        c->alloc = *allocator;
+        c->use_cuda_malloc = false;
+    }
+    const mdlg_params &p = c->p;
+    const int64_t n = ntot;
+    auto early = [&](int code) {
+        delete c;
+        return code;
+    };
+
+    // geometry (a batch: per system, slots padded to whole chunks, cells numbered
+    // system after system with one ghost cell each)
+    Geom &g = c->geo;
+    double rho_max = 0.0;
+    if (nsys == 0) {
+        MDLG_TRY_OR(system_geom(p, p.box, g), early);
+        c->ncells = (int64_t)g.nc[0] * g.nc[1];
+        c->slots = n;
+        rho_max = (double)n / (p.box[0] * p.box[1]);
+    } else {
+        c->sys_host.resize(nsys);
+        int64_t slot = 0, q = 0, cell = 0;
+        for (int32_t k = 0; k < nsys; ++k) {
+            SysInfo &si = c->sys_host[k];
+            memset(&si, 0, sizeof(si));
+            const double box[2] = {boxes[2 * k], boxes[2 * k + 1]};
+            MDLG_TRY_OR(system_geom(p, box, si.geo), early);
+            si.p0 = slot;
+            si.q0 = q;
+            si.n = ns[k];
+            si.cell0 = cell;
+            si.ncells = si.geo.nc[0] * si.geo.nc[1];
+            slot += (ns[k] + kChunk - 1) / kChunk * kChunk;
+            q += ns[k];
+            cell += (int64_t)si.ncells + 1;
+            rho_max = std::fmax(rho_max, (double)ns[k] / (box[0] * box[1]));
+        }
+        g = c->sys_host[0].geo;   // k, g, ratio, vmax shared by every system
+        c->slots = slot;
+        c->ncells = cell;
+    }
+    if (c->ncells > (int64_t)4096 * 4096) return early(MDLG_EINVAL);
     c->ratio_shift = log2_exact(g.ratio);
     c->q1 = (2 * p.vmax + 1) * (2 * p.vmax + 1) + 1;
     c->rc = (float)p.rcut;
@@ -376,7 +474,9 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
         delete c;
         return code;
     };
-    const size_t N = (size_t)n;
+    const size_t N = (size_t)c->slots;
+    const size_t NQ = (size_t)(n > c->slots ? n : c->slots);
+    const int32_t nsb = nsys > 0 ? nsys : 1;
     for (int b = 0; b < 2; ++b) {
         if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N)) ||
             (rc = alloc_n(c, &c->vel[b], N)) || (rc = alloc_n(c, &c->pid[b], N)))
@@ -389,13 +489,19 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
         (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
         (rc = alloc_n(c, &c->count, (size_t)c->ncells)) ||
         (rc = alloc_n(c, &c->block_sums, (size_t)nb)) || (rc = alloc_n(c, &c->entry, N)) ||
-        (rc = alloc_n(c, &c->partials, (size_t)mdlg::step_blocks(n) * 5)) ||
+        (rc = alloc_n(c, &c->partials, (size_t)mdlg::step_blocks(c->slots) * 5)) ||
         (rc = alloc_n(c, &c->ctl, 1)) ||
-        (rc = alloc_n(c, &c->counts, (size_t)p.nlags * c->q1)) ||
+        (rc = alloc_n(c, &c->counts, (size_t)nsb * p.nlags * c->q1)) ||
         (rc = alloc_n(c, &c->vsync, N)) || (rc = alloc_n(c, &c->fsync, N)) ||
-        (rc = alloc_n(c, &c->xbuf, 2 * N)) || (rc = alloc_n(c, &c->vbuf, 2 * N)) ||
-        (rc = alloc_n(c, &c->fbuf, 2 * N)))
+        (rc = alloc_n(c, &c->xbuf, 2 * NQ)) || (rc = alloc_n(c, &c->vbuf, 2 * NQ)) ||
+        (rc = alloc_n(c, &c->fbuf, 2 * NQ)))
         return fail(rc);
+    if (nsys > 0) {
+        if ((rc = alloc_n(c, &c->sys_dev, (size_t)nsys)) ||
+            (rc = alloc_n(c, &c->chunk_sys, N / kChunk)) ||
+            (rc = alloc_n(c, &c->bstats, (size_t)nsys * 5)))
+            return fail(rc);
+    }
     if (p.site_mode) {
         const size_t sites = (size_t)g.lat[0] * g.lat[1];
         if ((rc = alloc_n(c, &c->site_n, sites)) || (rc = alloc_n(c, &c->site_counts, sites * c->q1)))
@@ -403,10 +509,9 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     }
     if (p.potential == MDLG_POT_LJ_TS) {
         // Verlet list of radius = the MD cell width (rc + the whole skin);
-        // capacity three times the mean count at the box density, plus 16
+        // capacity three times the mean count at the highest density, plus 16
         c->list_radius = (float)(g.k * p.grid);
-        const double rho = (double)n / (p.box[0] * p.box[1]);
-        const double mean = rho * 3.14159265358979 * (double)c->list_radius * c->list_radius;
+        const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
         if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x cap words of shared memory
         if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
@@ -416,7 +521,7 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     cudaStream_t s = c->stream;
     auto chk = [&](cudaError_t e) { return cuda_err(e); };
     if ((rc = chk(cudaMemsetAsync(c->ctl, 0, sizeof(Control), s))) ||
-        (rc = chk(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * p.nlags * c->q1, s))))
+        (rc = chk(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * nsb * p.nlags * c->q1, s))))
         return fail(rc);
     for (int b = 0; b < 2; ++b)
         for (int l = 0; l < p.nlags; ++l)
@@ -428,18 +533,39 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
             (rc = chk(cudaMemsetAsync(c->site_counts, 0, sizeof(uint32_t) * sites * c->q1, s))))
             return fail(rc);
     }
+    if (nsys > 0) {
+        std::vector<uint16_t> cs(N / kChunk);
+        for (int32_t k = 0; k < nsys; ++k) {
+            const SysInfo &si = c->sys_host[k];
+            const int64_t np = (si.n + kChunk - 1) / kChunk * kChunk;
+            for (int64_t ch = si.p0 / kChunk; ch < (si.p0 + np) / kChunk; ++ch) cs[ch] = (uint16_t)k;
+        }
+        // pageable sources: the copies complete before the call returns
+        if ((rc = chk(cudaMemcpyAsync(c->sys_dev, c->sys_host.data(), sizeof(SysInfo) * nsys,
+                                      cudaMemcpyHostToDevice, s))) ||
+            (rc = chk(cudaMemcpyAsync(c->chunk_sys, cs.data(), sizeof(uint16_t) * cs.size(),
+                                      cudaMemcpyHostToDevice, s))))
+            return fail(rc);
+    }
     // upload (pageable host memory: the copy completes before the call returns)
-    if ((rc = chk(cudaMemcpyAsync(c->xbuf, x0, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s))) ||
-        (rc = chk(cudaMemcpyAsync(c->vbuf, v0, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s))))
+    if ((rc = chk(cudaMemcpyAsync(c->xbuf, x0, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s))) ||
+        (rc = chk(cudaMemcpyAsync(c->vbuf, v0, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s))))
         return fail(rc);
     // pack into buffer 1 (original order), sort into buffer 0
     c->pos_cur = 1;
     c->meta_cur = 1;
-    if ((rc = chk(launch_pack(g, n, c->xbuf, c->vbuf, c->cell[1], c->cl[1], c->vel[1], c->pid[1],
-                              c->ctl, s))))
+    if (nsys > 0) {
+        const Batch bt = batch_of(c);
+        if ((rc = chk(launch_pack_batch(bt, c->slots, c->xbuf, c->vbuf, c->cell[1], c->cl[1],
+                                        c->vel[1], c->pid[1], c->ctl, s))))
+            return fail(rc);
+    } else if ((rc = chk(launch_pack(g, n, c->xbuf, c->vbuf, c->cell[1], c->cl[1], c->vel[1],
+                                     c->pid[1], c->ctl, s)))) {
         return fail(rc);
+    }
     if ((rc = do_sort(c))) return fail(rc);
     // v_{-1/2} = v_0 - F(x_0) dt / (2m), in place; FP64 observables of step 0
+    if ((rc = zero_bstats(c))) return fail(rc);
     StepArgs a = step_args(c);
     a.v_out = c->vel[c->pos_cur];
     a.stats = 1;
@@ -456,6 +582,42 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
     return MDLG_OK;
 }
 
+// FP64 observables [ke, pe, virial, px, py] of system k (k < 0: all systems).
+int read_observables(mdlg_ctx *c, int32_t k, double *st, int32_t *status) {
+    double one[8];
+    MDLG_TRY(read_status(c, status, one));
+    if (c->nsys == 0) {
+        memcpy(st, one, 5 * sizeof(double));
+        return MDLG_OK;
+    }
+    std::vector<long long> h((size_t)c->nsys * 5);
+    MDLG_TRY(cuda_err(cudaMemcpyAsync(h.data(), c->bstats, sizeof(long long) * h.size(),
+                                      cudaMemcpyDeviceToHost, c->stream)));
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    for (int q = 0; q < 5; ++q) {
+        long long t = 0;
+        for (int32_t s = (k < 0 ? 0 : k); s < (k < 0 ? c->nsys : k + 1); ++s) t += h[(size_t)s * 5 + q];
+        st[q] = (double)t * (1.0 / 16777216.0);
+    }
+    return MDLG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
+                const mdlg_allocator *allocator, void *stream, mdlg_ctx **out) {
+    return create_impl(params, 0, nullptr, nullptr, x0, v0, allocator, stream, out);
+}
+
+int mdlg_create_batch(const mdlg_params *params, int32_t nsys, const int64_t *n,
+                      const double *box, const double *x0, const double *v0,
+                      const mdlg_allocator *allocator, void *stream, mdlg_ctx **out) {
+    if (nsys < 1) return MDLG_EINVAL;
+    return create_impl(params, nsys, n, box, x0, v0, allocator, stream, out);
+}
+
 int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
     if (!c || nsteps < 0) return MDLG_EINVAL;
     const mdlg_params &p = c->p;
@@ -463,6 +625,7 @@ int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
         if (c->step - c->last_sort >= c->sort_every) MDLG_TRY(do_sort(c));
         StepArgs a = step_args(c);
         a.stats = (p.stats_every > 0 && c->step % p.stats_every == 0) ? 1 : 0;
+        if (a.stats) MDLG_TRY(zero_bstats(c));
         {
             ProfScope ps(c, MDLG_PROF_STEP, 1);
             MDLG_TRY(cuda_err(launch_step(a, kModeStep, c->stream)));
@@ -493,13 +656,34 @@ int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
     return MDLG_OK;
 }
 
-int mdlg_stats(mdlg_ctx *c, mdlg_stats_out *out, uint64_t *counts, double *fi) {
+}  // extern "C"
+
+namespace {
+
+// Observables and MDLG totals of system k of a batch, or (k < 0) of the whole
+// context: one system, or every system of a batch added together.
+int stats_impl(mdlg_ctx *c, int32_t k, mdlg_stats_out *out, uint64_t *counts, double *fi) {
     if (!c || !out) return MDLG_EINVAL;
+    if (k >= 0 && (c->nsys == 0 || k >= c->nsys)) return MDLG_EINVAL;
     if (c->stats_step != c->step) MDLG_TRY(sync_stats(c, false));
-    double st[8];
+    double st[5];
     int32_t status = 0;
-    MDLG_TRY(read_status(c, &status, st));
+    MDLG_TRY(read_observables(c, k, st, &status));
     const mdlg_params &p = c->p;
+    int64_t n = p.n;
+    double area = p.box[0] * p.box[1];
+    int32_t nsub = 1;
+    if (c->nsys > 0) {
+        n = 0;
+        area = 0.0;
+        nsub = 0;
+        for (int32_t s = (k < 0 ? 0 : k); s < (k < 0 ? c->nsys : k + 1); ++s) {
+            const SysInfo &si = c->sys_host[s];
+            n += si.n;
+            area += (double)si.geo.lg[0] * si.geo.lg[1] * p.grid * p.grid;
+            ++nsub;
+        }
+    }
     memset(out, 0, sizeof(*out));
     out->step = c->step;
     out->stats_step = c->stats_step;
@@ -508,40 +692,60 @@ int mdlg_stats(mdlg_ctx *c, mdlg_stats_out *out, uint64_t *counts, double *fi) {
     out->virial = st[2];
     out->momentum[0] = st[3];
     out->momentum[1] = st[4];
-    out->temperature = p.n > 1 ? st[0] / (double)(p.n - 1) : 0.0;
-    out->pressure = (st[0] + 0.5 * st[2]) / (p.box[0] * p.box[1]);
+    out->temperature = n > nsub ? st[0] / (double)(n - nsub) : 0.0;
+    out->pressure = (st[0] + 0.5 * st[2]) / area;
     for (int l = 0; l < p.nlags; ++l) out->intervals[l] = c->intervals[l];
     out->status = status;
     if (counts || fi) {
-        std::vector<unsigned long long> h((size_t)p.nlags * c->q1);
+        const int32_t nsb = c->nsys > 0 ? c->nsys : 1;
+        std::vector<unsigned long long> h((size_t)nsb * p.nlags * c->q1);
         MDLG_TRY(cuda_err(cudaMemcpyAsync(h.data(), c->counts, sizeof(unsigned long long) * h.size(),
                                           cudaMemcpyDeviceToHost, c->stream)));
         MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
         for (int l = 0; l < p.nlags; ++l)
             for (int i = 0; i < c->q1; ++i) {
-                const size_t k = (size_t)l * c->q1 + i;
-                if (counts) counts[k] = h[k];
+                unsigned long long t = 0;
+                for (int32_t s = (k < 0 ? 0 : k); s < (k < 0 ? nsb : k + 1); ++s)
+                    t += h[((size_t)s * p.nlags + l) * c->q1 + i];
+                const size_t o = (size_t)l * c->q1 + i;
+                if (counts) counts[o] = t;
                 if (fi) {
-                    const double denom = (double)p.n * (double)c->intervals[l];
-                    fi[k] = denom > 0 ? (double)h[k] / denom : 0.0;
+                    const double denom = (double)n * (double)c->intervals[l];
+                    fi[o] = denom > 0 ? (double)t / denom : 0.0;
                 }
             }
     }
     return status ? status : MDLG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int mdlg_stats(mdlg_ctx *c, mdlg_stats_out *out, uint64_t *counts, double *fi) {
+    return stats_impl(c, -1, out, counts, fi);
+}
+
+int mdlg_stats_system(mdlg_ctx *c, int32_t system, mdlg_stats_out *out, uint64_t *counts,
+                      double *fi) {
+    if (system < 0) return MDLG_EINVAL;
+    return stats_impl(c, system, out, counts, fi);
+}
+
 int mdlg_get_state(mdlg_ctx *c, double *x, double *v, double *f) {
     if (!c) return MDLG_EINVAL;
     const size_t N = (size_t)c->p.n;
     if (v || f) {
+        MDLG_TRY(zero_bstats(c));
         StepArgs a = step_args(c);
         a.stats = 1;
         MDLG_TRY(cuda_err(launch_step(a, kModeSync, c->stream)));
         c->stats_step = c->step;
     }
-    MDLG_TRY(cuda_err(launch_unpack(c->geo, c->p.n, c->cell[c->meta_cur], c->cl[c->pos_cur],
+    const Batch bt = batch_of(c);
+    MDLG_TRY(cuda_err(launch_unpack(c->geo, c->slots, c->cell[c->meta_cur], c->cl[c->pos_cur],
                                     c->vsync, c->fsync, c->pid[c->meta_cur], x ? c->xbuf : nullptr,
-                                    v ? c->vbuf : nullptr, f ? c->fbuf : nullptr, c->stream)));
+                                    v ? c->vbuf : nullptr, f ? c->fbuf : nullptr, c->stream, &bt)));
     if (x) MDLG_TRY(cuda_err(cudaMemcpyAsync(x, c->xbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
     if (v) MDLG_TRY(cuda_err(cudaMemcpyAsync(v, c->vbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
     if (f) MDLG_TRY(cuda_err(cudaMemcpyAsync(f, c->fbuf, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, c->stream)));
@@ -564,7 +768,8 @@ int mdlg_get_sites(mdlg_ctx *c, uint32_t *site_counts, uint32_t *ncell) {
 
 int mdlg_reset_counts(mdlg_ctx *c) {
     if (!c) return MDLG_EINVAL;
-    MDLG_TRY(cuda_err(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * c->p.nlags * c->q1,
+    const size_t nsb = c->nsys > 0 ? (size_t)c->nsys : 1;
+    MDLG_TRY(cuda_err(cudaMemsetAsync(c->counts, 0, sizeof(unsigned long long) * nsb * c->p.nlags * c->q1,
                                       c->stream)));
     if (c->p.site_mode) {
         const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];

@@ -162,12 +162,64 @@ __global__ void k_bin_state(StateBinArgs sa) {
         if ((sa.mask >> l) & 1u) flush_hist(sh + l * q1, q1, sa.counts[l]);
 }
 
+// Batched systems: one chunk (one system) per block iteration, so the block's
+// histogram belongs to one system and is flushed into that system's totals.
+__global__ void __launch_bounds__(kChunk) k_bin_state_batch(StateBinArgs sa) {
+    extern __shared__ uint32_t sh[];
+    const int w = 2 * sa.geo.vmax + 1, q1 = w * w + 1;
+    const int center = sa.geo.vmax * w + sa.geo.vmax;
+    const int64_t nchunks = sa.n / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        for (int b = threadIdx.x; b < q1 * kMaxLags; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+        const int sys = sa.batch.chunk_sys[ch];
+        const Geom &geo = sa.batch.sys[sys].geo;
+        const int64_t j = ch * kChunk + threadIdx.x;
+        const uint32_t c = sa.cell[j];
+        const bool act = c != kGhostCell;
+        uint32_t before[kMaxLags];
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            before[l] = (act && ((sa.mask >> l) & 1u)) ? sa.lprev[l][j] : 0u;
+        int32_t lx = 0, ly = 0;
+        if (act) {
+            const float2 p = sa.cl[j];
+            const int32_t bx = base_cell((int32_t)(c & 0xffffu) * geo.k, p.x, geo.inv_g, geo.lg[0]);
+            const int32_t by = base_cell((int32_t)(c >> 16) * geo.k, p.y, geo.inv_g, geo.lg[1]);
+            lx = lattice_of_base(bx, geo.ratio, sa.ratio_shift);
+            ly = lattice_of_base(by, geo.ratio, sa.ratio_shift);
+        }
+        const uint32_t now = pack_cell(lx, ly);
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l) {
+            if (!((sa.mask >> l) & 1u)) continue;
+            int32_t bin = 0;
+            if (act) {
+                const int32_t vx = lattice_disp(lx - (int32_t)(before[l] & 0xffffu), geo.lat[0]);
+                const int32_t vy = lattice_disp(ly - (int32_t)(before[l] >> 16), geo.lat[1]);
+                bin = vel_index(vx, vy, geo.vmax);
+                sa.lprev[l][j] = now;
+            }
+            hist_add(sh + l * q1, bin, center, act);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            if ((sa.mask >> l) & 1u)
+                flush_hist(sh + l * q1, q1, sa.counts[l] + (size_t)sys * sa.nlags * q1);
+        __syncthreads();
+    }
+}
+
 // Lattice cell of every particle, stored as the starting point of every lag.
+template <bool B>
 __global__ void k_bin_seed(StateBinArgs sa) {
-    const Geom &geo = sa.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < sa.n; j += stride) {
         const uint32_t c = sa.cell[j];
+        if (B && c == kGhostCell) continue;
+        const SysView sv = sys_view<B>(sa.geo, sa.batch, j);
+        const Geom &geo = sv.geo;
         const float2 p = sa.cl[j];
         const int32_t ccx = (int32_t)(c & 0xffffu), ccy = (int32_t)(c >> 16);
         const int32_t bx = base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
@@ -218,9 +270,18 @@ cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *
 }
 
 cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
-    const int threads = 256;
     const int q1 = (2 * sa.geo.vmax + 1) * (2 * sa.geo.vmax + 1) + 1;
     const size_t smem = (size_t)q1 * kMaxLags * sizeof(uint32_t);
+    if (sa.batch.sys) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_bin_state_batch,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_bin_state_batch<<<hist_grid(sa.n, kChunk), kChunk, smem, s>>>(sa);
+        return cudaGetLastError();
+    }
+    const int threads = 256;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_bin_state,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -232,7 +293,8 @@ cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
 
 cudaError_t launch_bin_seed(const StateBinArgs &sa, cudaStream_t s) {
     const int threads = 256;
-    k_bin_seed<<<hist_grid(sa.n, threads), threads, 0, s>>>(sa);
+    if (sa.batch.sys) k_bin_seed<true><<<hist_grid(sa.n, threads), threads, 0, s>>>(sa);
+    else k_bin_seed<false><<<hist_grid(sa.n, threads), threads, 0, s>>>(sa);
     return cudaGetLastError();
 }
 

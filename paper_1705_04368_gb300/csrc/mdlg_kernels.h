@@ -8,6 +8,60 @@
 
 namespace mdlg {
 
+// ---- batches of independent systems ------------------------------------------
+// A batch keeps every system's particles in one contiguous slot range padded to
+// a multiple of kChunk slots; padding slots hold ghost particles (cell word
+// kGhostCell) that take part in nothing.  Every chunk of kChunk slots belongs to
+// one system, so a warp always works on one system and looks its geometry up.
+// Each system owns the global cells [cell0, cell0 + ncells] (the last one holds
+// its ghosts), so one counting sort orders all systems at once.
+constexpr int kChunk = 128;
+constexpr uint32_t kGhostCell = 0xffffffffu;
+
+struct SysInfo {
+    Geom geo;          // this system's lg, nc, lat (k, g, ratio, vmax as the batch's)
+    int64_t p0;        // first slot
+    int64_t q0;        // first particle in the caller's concatenated order
+    int64_t n;         // particles (slots p0 .. p0+n-1; the rest of the range are ghosts)
+    int64_t cell0;     // first global cell
+    int32_t ncells;    // nc[0] * nc[1]; global cell cell0 + ncells is the ghost cell
+    int32_t pad_;
+};
+
+struct Batch {
+    const SysInfo *sys;          // null: a single system described by the kernel's Geom
+    const uint16_t *chunk_sys;   // system of every kChunk-slot chunk
+    long long *stats;            // nsys x 5 exact fixed-point sums of a statistics launch
+    int32_t nsys;
+};
+
+// Geometry and cell range of the system that owns a slot.
+struct SysView {
+    Geom geo;
+    int64_t cell0;
+    int32_t ncells;
+    int32_t sys;
+};
+
+template <bool B>
+__device__ __forceinline__ SysView sys_view(const Geom &single, const Batch &b, int64_t slot) {
+    SysView v;
+    if (!B) {
+        v.geo = single;
+        v.cell0 = 0;
+        v.ncells = single.nc[0] * single.nc[1];
+        v.sys = 0;
+    } else {
+        const int s = b.chunk_sys[slot / kChunk];
+        const SysInfo &si = b.sys[s];
+        v.geo = si.geo;
+        v.cell0 = si.cell0;
+        v.ncells = si.ncells;
+        v.sys = s;
+    }
+    return v;
+}
+
 // ---- binning ---------------------------------------------------------------
 struct LatticeArgs {
     int32_t base[2];   // base cells per axis
@@ -36,6 +90,7 @@ struct StateBinArgs {
     unsigned long long *counts[kMaxLags];
     uint32_t *site_n;       // lag 0 per-site N(x,t), or null
     uint32_t *site_counts;  // lag 0 per-site n_i(x,t), or null
+    Batch batch;            // batched: counts[l] point at system 0, system s at + s*nlags*q1
 };
 
 int hist_grid(int64_t n, int threads);
@@ -87,6 +142,7 @@ struct StepArgs {
     int32_t stats;              // 1: FP64 reductions into partials
     long long *partials;        // gridDim.x x 5 fixed-point block sums
     Control *ctl;
+    Batch batch;
 };
 
 int64_t step_blocks(int64_t n);
@@ -122,6 +178,7 @@ struct SortArgs {
     int32_t *ncount;
     int32_t cap;
     float rl2;               // list radius squared
+    Batch batch;
 };
 
 int64_t sort_scratch_blocks(int64_t ncells);
@@ -131,9 +188,14 @@ cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
                         uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
                         cudaStream_t s);
+// Batched upload: slots of every system, ghosts in the padding (n = slot count).
+cudaError_t launch_pack_batch(const Batch &b, int64_t slots, const double *x, const double *v,
+                              uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                              cudaStream_t s);
 // Download conversion: sorted state -> FP64 arrays in original order.
 cudaError_t launch_unpack(const Geom &geo, int64_t n, const uint32_t *cell, const float2 *cl,
                           const float2 *vsync, const float2 *fsync, const int32_t *pid,
-                          double *x, double *v, double *f, cudaStream_t s);
+                          double *x, double *v, double *f, cudaStream_t s,
+                          const Batch *batch = nullptr);
 
 }  // namespace mdlg

@@ -117,10 +117,9 @@ __device__ __forceinline__ float cell_shift(int32_t c, int off, int32_t nc, int3
 
 // All pairs through the cell stencil (always correct for the current bound D).
 template <bool STATS>
-__device__ __forceinline__ void forces_cells(const StepArgs &a, int64_t i, int32_t cx, int32_t cy,
-                                             float2 p, int lox, int hix, int loy, int hiy,
-                                             PairAcc &acc) {
-    const Geom &geo = a.geo;
+__device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo, const int32_t *cs,
+                                             int64_t i, int32_t cx, int32_t cy, float2 p, int lox,
+                                             int hix, int loy, int hiy, PairAcc &acc) {
     for (int oy = loy; oy <= hiy; ++oy) {
         const int32_t ny = wrap_mod(cy + oy, geo.nc[1]);
         const float ody = (float)wrap_half((ny - cy) * geo.k, geo.lg[1]) * geo.g;
@@ -128,7 +127,7 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, int64_t i, int32
             const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
             const float odx = (float)wrap_half((nx - cx) * geo.k, geo.lg[0]) * geo.g;
             const int32_t cn = ny * geo.nc[0] + nx;
-            const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+            const int32_t s = __ldg(cs + cn), e = __ldg(cs + cn + 1);
             for (int32_t j = s; j < e; ++j) {
                 if (j == i) continue;
                 const float2 q = __ldg(a.cl_in + j);
@@ -179,11 +178,15 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     }
 }
 
-template <int MODE, bool STATS>
+// B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
+// per system); otherwise one system described by a.geo.
+template <int MODE, bool STATS, bool B>
 __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
-    const Geom &geo = a.geo;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = i < a.n;
+    const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
+    const Geom &geo = sv.geo;
+    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
+    const bool act = i < a.n && (!B || cw != kGhostCell);
 
     // Neighbour-cell radius for the displacement bound of the input positions.
     const float D = a.ctl->dbound;
@@ -199,7 +202,6 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
     if (act) {
-        const uint32_t cw = a.cell[i];
         p = a.cl_in[i];
         v = a.v_in[i];
         if (a.potential) {
@@ -219,7 +221,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);
                 stencil(R, geo.nc[1], loy, hiy);
-                forces_cells<STATS>(a, i, cx, cy, p, lox, hix, loy, hiy, acc);
+                forces_cells<STATS>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
+                                    hiy, acc);
             }
         }
     }
@@ -283,7 +286,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             for (int k = 0; k < kStatsN; ++k) {
                 long long t = 0;
                 for (int w = 0; w < kWarps; ++w) t += s_red[w][k];
-                a.partials[(size_t)blockIdx.x * kStatsN + k] = t;
+                // batched: a block is one chunk of one system; integer sums are
+                // exact, so the order of these atomics does not matter
+                if (B) atomicAdd((unsigned long long *)&a.batch.stats[sv.sys * kStatsN + k],
+                                 (unsigned long long)t);
+                else a.partials[(size_t)blockIdx.x * kStatsN + k] = t;
             }
         }
         __threadfence();
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     if (!s_last) return;
     // Last block of the launch: every other block has published its results.
     __threadfence();
-    if (STATS) {
+    if (STATS && !B) {
         if (warp == 0) {
             for (int k = 0; k < kStatsN; ++k) {
                 long long t = 0;
@@ -322,20 +329,27 @@ __device__ __forceinline__ int32_t lin(const Geom &geo, uint32_t cw) {
     return cell_y(cw) * geo.nc[0] + cell_x(cw);
 }
 
+template <bool B>
 __global__ void k_sort_key(SortArgs a) {
-    const Geom &geo = a.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const SysView sv = sys_view<B>(a.geo, a.batch, i);
+        const Geom &geo = sv.geo;
         const uint32_t cw = a.cell_in[i];
-        const float2 p = a.cl_in[i];
-        const int32_t bx = base_cell(cell_x(cw) * geo.k, p.x, geo.inv_g, geo.lg[0]);
-        const int32_t by = base_cell(cell_y(cw) * geo.k, p.y, geo.inv_g, geo.lg[1]);
-        int32_t nx = bx / geo.k, ny = by / geo.k;
-        nx = nx < geo.nc[0] ? nx : geo.nc[0] - 1;
-        ny = ny < geo.nc[1] ? ny : geo.nc[1] - 1;
-        const uint32_t key = (uint32_t)nx | ((uint32_t)ny << 16);
+        uint32_t key = kGhostCell;
+        int64_t c = sv.cell0 + sv.ncells;   // a system's ghost cell
+        if (!B || cw != kGhostCell) {
+            const float2 p = a.cl_in[i];
+            const int32_t bx = base_cell(cell_x(cw) * geo.k, p.x, geo.inv_g, geo.lg[0]);
+            const int32_t by = base_cell(cell_y(cw) * geo.k, p.y, geo.inv_g, geo.lg[1]);
+            int32_t nx = bx / geo.k, ny = by / geo.k;
+            nx = nx < geo.nc[0] ? nx : geo.nc[0] - 1;
+            ny = ny < geo.nc[1] ? ny : geo.nc[1] - 1;
+            key = (uint32_t)nx | ((uint32_t)ny << 16);
+            c = sv.cell0 + ny * geo.nc[0] + nx;
+        }
         a.key[i] = key;
-        a.slot[i] = atomicAdd(&a.count[lin(geo, key)], 1);
+        a.slot[i] = atomicAdd(&a.count[c], 1);
     }
 }
 
@@ -397,10 +411,19 @@ __device__ __forceinline__ int32_t cell_begin(const SortArgs &a, int64_t c) {
     return a.count[c] + a.block_sums[c / kScanChunk];
 }
 
+// Global cell of a sort key (the system's ghost cell for a ghost).
+template <bool B>
+__device__ __forceinline__ int64_t key_cell(const SysView &sv, uint32_t key) {
+    if (B && key == kGhostCell) return sv.cell0 + sv.ncells;
+    return sv.cell0 + cell_y(key) * sv.geo.nc[0] + cell_x(key);
+}
+
+template <bool B>
 __global__ void k_sort_place(SortArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const int64_t at = (int64_t)cell_begin(a, lin(a.geo, a.key[i])) + a.slot[i];
+        const SysView sv = sys_view<B>(a.geo, a.batch, i);
+        const int64_t at = (int64_t)cell_begin(a, key_cell<B>(sv, a.key[i])) + a.slot[i];
         a.entry[at] = ((unsigned long long)(uint32_t)a.pid_in[i] << 32) | (uint32_t)i;
     }
 }
@@ -421,10 +444,12 @@ __global__ void k_cell_start(SortArgs a) {
 // finds its rank by particle number among its cell's arrivals, then is copied
 // from the old order to its final place, its position re-expressed against the
 // new cell's origin.
+template <bool B>
 __global__ void k_sort_scatter(SortArgs a) {
-    const Geom &geo = a.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+        const SysView sv = sys_view<B>(a.geo, a.batch, t);
+        const Geom &geo = sv.geo;
         const unsigned long long et = a.entry[t];
         const int32_t from = (int32_t)(et & 0xffffffffu);
         const uint32_t my_pid = (uint32_t)(et >> 32);
@@ -438,14 +463,18 @@ __global__ void k_sort_scatter(SortArgs a) {
         uint32_t lp[kMaxLags];
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l) lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
-        const int32_t c = lin(geo, cw);
+        const int64_t c = key_cell<B>(sv, cw);
         const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
         int32_t rank = 0;
         for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
         const int32_t to = s + rank;
-        const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
-        const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
-        a.cl_out[to] = make_float2(p.x + sx, p.y + sy);
+        float2 pn = p;
+        if (!B || cw != kGhostCell) {
+            const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
+            const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
+            pn = make_float2(p.x + sx, p.y + sy);
+        }
+        a.cl_out[to] = pn;
         a.v_out[to] = vv;
         a.pid_out[to] = pid;
         a.cell_out[to] = cw;
@@ -461,17 +490,21 @@ __global__ void k_sort_scatter(SortArgs a) {
 // (predicated) so their loads overlap.  Column-major: entry t of particle i at
 // nbr[t n + i].  A particle with more than `cap` entries stores cap + 1 as its
 // count and is handled through the cell stencil by the step kernel.
+template <bool B>
 __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
     // entries are staged in shared memory and written after the search, so
     // that no global store precedes a candidate load (see k_bin_state)
     extern __shared__ uint32_t s_ent[];          // kNlistThreads x cap, column-major
-    const Geom &geo = a.geo;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
         int cnt = 0;
-        if (i < a.n) {
-            const uint32_t cw = a.cell_out[i];
+        const uint32_t cw = i < a.n ? a.cell_out[i] : kGhostCell;
+        if (i < a.n && B && cw == kGhostCell) a.ncount[i] = 0;
+        if (i < a.n && (!B || cw != kGhostCell)) {
+            const SysView sv = sys_view<B>(a.geo, a.batch, i);
+            const Geom &geo = sv.geo;
+            const int32_t *cs = a.cell_start + sv.cell0;
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
             const float2 p = a.cl_out[i];
             // x offsets of the three columns (wrapped at the periodic edges)
@@ -485,10 +518,10 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                 const int32_t row = ny * geo.nc[0];
                 if (interior) {
                     // cells cx-1, cx, cx+1 of this row are one contiguous range
-                    const int32_t s = __ldg(a.cell_start + row + cx - 1);
-                    const int32_t m1 = __ldg(a.cell_start + row + cx);
-                    const int32_t m2 = __ldg(a.cell_start + row + cx + 1);
-                    const int32_t e = __ldg(a.cell_start + row + cx + 2);
+                    const int32_t s = __ldg(cs + row + cx - 1);
+                    const int32_t m1 = __ldg(cs + row + cx);
+                    const int32_t m2 = __ldg(cs + row + cx + 1);
+                    const int32_t e = __ldg(cs + row + cx + 2);
                     for (int32_t b = s; b < e; b += 4) {
                         float2 q[4];
 #pragma unroll
@@ -515,7 +548,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                     const int32_t nx = wrap_mod(cx + ox, geo.nc[0]);
                     const float odx = ox < 0 ? sxm : (ox > 0 ? sxp : 0.0f);
                     const int32_t cn = row + nx;
-                    const int32_t s = __ldg(a.cell_start + cn), e = __ldg(a.cell_start + cn + 1);
+                    const int32_t s = __ldg(cs + cn), e = __ldg(cs + cn + 1);
                     const uint32_t code = ((uint32_t)(ox + 1) << 28) | ycode;
                     for (int32_t b = s; b < e; b += 4) {
                         float2 q[4];
@@ -570,14 +603,57 @@ __global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, ui
     }
 }
 
-__global__ void k_unpack(Geom geo, int64_t n, const uint32_t *cell, const float2 *cl,
-                         const float2 *vsync, const float2 *fsync, const int32_t *pid, double *x,
-                         double *v, double *f) {
+// Batched upload: slot t of system s holds particle q0 + (t - p0) of the
+// caller's concatenated arrays, or a ghost in the padding.
+__global__ void k_pack_batch(Batch b, int64_t slots, const double *x, const double *v,
+                             uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const double g = geo.g;
-    const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < slots; t += stride) {
+        const SysInfo &si = b.sys[b.chunk_sys[t / kChunk]];
+        const Geom &geo = si.geo;
+        const int64_t local = t - si.p0;
+        if (local >= si.n) {
+            // ghosts need distinct particle numbers: the sort ranks a cell's
+            // particles by number, and equal numbers would share a slot
+            cell[t] = kGhostCell;
+            cl[t] = make_float2(0.f, 0.f);
+            vel[t] = make_float2(0.f, 0.f);
+            pid[t] = -1 - (int32_t)(local - si.n);
+            continue;
+        }
+        const int64_t q = si.q0 + local;
+        const double g = geo.g, inv_g = geo.inv_g;
+        const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
+        const double px = x[2 * q], py = x[2 * q + 1];
+        if (!(px > 0.0 && px <= L0 && py > 0.0 && py <= L1) || !isfinite(v[2 * q]) ||
+            !isfinite(v[2 * q + 1]))
+            set_status(ctl, kErrNonFinite);
+        int64_t bx = (int64_t)ceil(px * inv_g) - 1, by = (int64_t)ceil(py * inv_g) - 1;
+        bx = bx < 0 ? 0 : (bx >= geo.lg[0] ? geo.lg[0] - 1 : bx);
+        by = by < 0 ? 0 : (by >= geo.lg[1] ? geo.lg[1] - 1 : by);
+        int32_t cx = (int32_t)(bx / geo.k), cy = (int32_t)(by / geo.k);
+        cx = cx < geo.nc[0] ? cx : geo.nc[0] - 1;
+        cy = cy < geo.nc[1] ? cy : geo.nc[1] - 1;
+        cell[t] = (uint32_t)cx | ((uint32_t)cy << 16);
+        cl[t] = make_float2((float)(px - (double)(cx * geo.k) * g),
+                            (float)(py - (double)(cy * geo.k) * g));
+        vel[t] = make_float2((float)v[2 * q], (float)v[2 * q + 1]);
+        pid[t] = (int32_t)q;
+    }
+}
+
+template <bool B>
+__global__ void k_unpack(Geom single, Batch batch, int64_t n, const uint32_t *cell,
+                         const float2 *cl, const float2 *vsync, const float2 *fsync,
+                         const int32_t *pid, double *x, double *v, double *f) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const uint32_t cw = cell[j];
+        if (B && cw == kGhostCell) continue;
+        const SysView sv = sys_view<B>(single, batch, j);
+        const Geom &geo = sv.geo;
+        const double g = geo.g;
+        const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
         const float2 p = cl[j];
         double px = (double)(cell_x(cw) * geo.k) * g + (double)p.x;
         double py = (double)(cell_y(cw) * geo.k) * g + (double)p.y;
@@ -604,43 +680,56 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 
 int64_t step_blocks(int64_t n) { return (n + kStepThreads - 1) / kStepThreads; }
 
+template <bool B>
+void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
+    if (mode == kModeStep) {
+        if (a.stats) k_step<kModeStep, true, B><<<grid, block, 0, s>>>(a);
+        else k_step<kModeStep, false, B><<<grid, block, 0, s>>>(a);
+    } else if (mode == kModeInit) {
+        k_step<kModeInit, true, B><<<grid, block, 0, s>>>(a);
+    } else {
+        k_step<kModeSync, true, B><<<grid, block, 0, s>>>(a);
+    }
+}
+
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
     const int64_t blocks = step_blocks(a.n);
     if (blocks < 1) return cudaSuccess;
     const dim3 grid((unsigned)blocks), block(kStepThreads);
-    if (mode == kModeStep) {
-        if (a.stats) k_step<kModeStep, true><<<grid, block, 0, s>>>(a);
-        else k_step<kModeStep, false><<<grid, block, 0, s>>>(a);
-    } else if (mode == kModeInit) {
-        k_step<kModeInit, true><<<grid, block, 0, s>>>(a);
-    } else {
-        k_step<kModeSync, true><<<grid, block, 0, s>>>(a);
-    }
+    if (a.batch.sys) launch_step_t<true>(a, mode, grid, block, s);
+    else launch_step_t<false>(a, mode, grid, block, s);
     return cudaGetLastError();
 }
 
 int64_t sort_scratch_blocks(int64_t ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
 
-cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {
+template <bool B>
+cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.count, 0, sizeof(int32_t) * (size_t)a.ncells, s);
     if (e != cudaSuccess) return e;
     const int t = 256;
-    k_sort_key<<<grid_for(a.n, t), t, 0, s>>>(a);
+    k_sort_key<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     const int64_t nb = sort_scratch_blocks(a.ncells);
     k_scan_local<<<(unsigned)nb, kScanThreads, 0, s>>>(a.count, a.ncells, a.block_sums);
     k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
-    k_sort_place<<<grid_for(a.n, t), t, 0, s>>>(a);
+    k_sort_place<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
-    k_sort_scatter<<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    k_sort_scatter<B><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     if (a.nbr) {
         const size_t smem = sizeof(uint32_t) * (size_t)kNlistThreads * a.cap;
         if (smem > 48 * 1024) {
-            e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_nlist<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_nlist<<<grid_for(a.n, kNlistThreads, 32), kNlistThreads, smem, s>>>(a);
+        k_nlist<B><<<grid_for(a.n, kNlistThreads, 32), kNlistThreads, smem, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+// In a batch, a.ncells counts every system's cells plus its ghost cell.
+cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {
+    return a.batch.sys ? launch_sort_t<true>(a, s) : launch_sort_t<false>(a, s);
 }
 
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,
@@ -650,10 +739,21 @@ cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_pack_batch(const Batch &b, int64_t slots, const double *x, const double *v,
+                              uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl,
+                              cudaStream_t s) {
+    k_pack_batch<<<grid_for(slots, 256), 256, 0, s>>>(b, slots, x, v, cell, cl, vel, pid, ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const Geom &geo, int64_t n, const uint32_t *cell, const float2 *cl,
                           const float2 *vsync, const float2 *fsync, const int32_t *pid,
-                          double *x, double *v, double *f, cudaStream_t s) {
-    k_unpack<<<grid_for(n, 256), 256, 0, s>>>(geo, n, cell, cl, vsync, fsync, pid, x, v, f);
+                          double *x, double *v, double *f, cudaStream_t s, const Batch *batch) {
+    const Batch b = batch ? *batch : Batch{};
+    if (b.sys)
+        k_unpack<true><<<grid_for(n, 256), 256, 0, s>>>(geo, b, n, cell, cl, vsync, fsync, pid, x, v, f);
+    else
+        k_unpack<false><<<grid_for(n, 256), 256, 0, s>>>(geo, b, n, cell, cl, vsync, fsync, pid, x, v, f);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,10 @@ typedef struct {
     int32_t vmax;         /* window half-width V, 1..MDLG_MAX_VMAX                */
     int32_t site_mode;    /* MDLG_SITES_* flags for lag 0; 0 = totals only         */
     int32_t stats_every;  /* MD steps between FP64 reductions; 0 = only on request */
+    int32_t use_graphs;   /* 1: mdlg_step captures two periods of its launch schedule
+                             (lcm of sort_every, the lags and stats_every) in a CUDA
+                             graph and replays it; stretches shorter than that, and
+                             schedules longer than 8192 steps, launch directly     */
 } mdlg_params;
 
 /*

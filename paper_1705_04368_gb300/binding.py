@@ -44,7 +44,8 @@ class _Params(ctypes.Structure):
                 ("skin", ctypes.c_double), ("sort_every", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("nlags", ctypes.c_int32),
                 ("lag_steps", ctypes.c_int32 * MAX_LAGS), ("vmax", ctypes.c_int32),
-                ("site_mode", ctypes.c_int32), ("stats_every", ctypes.c_int32)]
+                ("site_mode", ctypes.c_int32), ("stats_every", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -177,6 +178,7 @@ class Params:
     vmax: int = 3
     site_mode: int = 0
     stats_every: int = 0
+    use_graphs: bool = False
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -198,6 +200,7 @@ class Params:
         p.vmax = int(self.vmax)
         p.site_mode = int(self.site_mode)
         p.stats_every = int(self.stats_every)
+        p.use_graphs = int(bool(self.use_graphs))
         return p
 
     @property

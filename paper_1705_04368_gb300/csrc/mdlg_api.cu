@@ -55,6 +55,12 @@ struct mdlg_ctx {
     int64_t intervals[kMaxLags]{};
     int32_t sort_every = 1;
     float rc = 0.f, round_margin = 0.f;
+    // CUDA graph of two schedule periods (use_graphs)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_start = -1, graph_len = 0;
+    bool graph_failed = false;
+    int64_t graph_launches[MDLG_PROF_KINDS]{};
     // profiling: event pairs around launch groups
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -254,7 +260,13 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
     return b;
 }
 
-int do_sort(mdlg_ctx *c) {
+int do_sort(mdlg_ctx *c, bool launch = true) {
+    if (!launch) {   // bookkeeping of a sort that a replayed graph performs
+        c->pos_cur ^= 1;
+        c->meta_cur ^= 1;
+        c->last_sort = c->step;
+        return MDLG_OK;
+    }
     SortArgs s{};
     s.geo = c->geo;
     s.n = c->slots;
@@ -618,40 +630,142 @@ int mdlg_create_batch(const mdlg_params *params, int32_t nsys, const int64_t *n,
     return create_impl(params, nsys, n, box, x0, v0, allocator, stream, out);
 }
 
-int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
-    if (!c || nsteps < 0) return MDLG_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// nsteps MD steps as the host schedules them: re-sorts every sort_every
+// steps, statistics on multiples of stats_every, binning on multiples of each
+// lag.  launch = false only advances the bookkeeping (a replayed graph runs the
+// kernels).
+int step_loop(mdlg_ctx *c, int64_t nsteps, bool launch) {
     const mdlg_params &p = c->p;
     for (int64_t it = 0; it < nsteps; ++it) {
-        if (c->step - c->last_sort >= c->sort_every) MDLG_TRY(do_sort(c));
-        StepArgs a = step_args(c);
-        a.stats = (p.stats_every > 0 && c->step % p.stats_every == 0) ? 1 : 0;
-        if (a.stats) MDLG_TRY(zero_bstats(c));
-        {
+        if (c->step - c->last_sort >= c->sort_every) MDLG_TRY(do_sort(c, launch));
+        const bool stats = p.stats_every > 0 && c->step % p.stats_every == 0;
+        if (launch) {
+            StepArgs a = step_args(c);
+            a.stats = stats ? 1 : 0;
+            if (a.stats) MDLG_TRY(zero_bstats(c));
             ProfScope ps(c, MDLG_PROF_STEP, 1);
             MDLG_TRY(cuda_err(launch_step(a, kModeStep, c->stream)));
         }
-        if (a.stats) c->stats_step = c->step;
+        if (stats) c->stats_step = c->step;
         c->pos_cur ^= 1;
         c->step += 1;
         uint32_t mask = 0;
         for (int l = 0; l < p.nlags; ++l)
             if (c->step % p.lag_steps[l] == 0) mask |= 1u << l;
         if (mask) {
-            if ((mask & 1u) && (p.site_mode & MDLG_SITES_FIELD)) {
-                const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
-                MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, c->stream)));
-                MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts, 0,
-                                                  sizeof(uint32_t) * sites * c->q1, c->stream)));
-            }
-            StateBinArgs b = bin_args(c, mask);
-            if (!(mask & 1u)) { b.site_n = nullptr; b.site_counts = nullptr; }
-            {
+            if (launch) {
+                if ((mask & 1u) && (p.site_mode & MDLG_SITES_FIELD)) {
+                    const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+                    MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, c->stream)));
+                    MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts, 0,
+                                                      sizeof(uint32_t) * sites * c->q1, c->stream)));
+                }
+                StateBinArgs b = bin_args(c, mask);
+                if (!(mask & 1u)) { b.site_n = nullptr; b.site_counts = nullptr; }
                 ProfScope ps(c, MDLG_PROF_BIN, 1);
                 MDLG_TRY(cuda_err(launch_bin_state(b, c->stream)));
             }
             for (int l = 0; l < p.nlags; ++l)
                 if ((mask >> l) & 1u) c->intervals[l] += 1;
         }
+    }
+    return MDLG_OK;
+}
+
+int64_t gcd64(int64_t a, int64_t b) {
+    while (b) { const int64_t t = a % b; a = b; b = t; }
+    return a;
+}
+
+// Two periods of the launch schedule: after them the ping-pong buffers are
+// back in place, so one captured graph can be replayed every graph_len steps.
+int64_t schedule_len(const mdlg_ctx *c) {
+    int64_t L = c->sort_every;
+    for (int l = 0; l < c->p.nlags; ++l) L = L / gcd64(L, c->p.lag_steps[l]) * c->p.lag_steps[l];
+    if (c->p.stats_every > 0) L = L / gcd64(L, c->p.stats_every) * c->p.stats_every;
+    return 2 * L;
+}
+
+void drop_graph(mdlg_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_start = -1;
+}
+
+// Capture the next graph_len steps into a graph and launch it.
+int capture_and_launch(mdlg_ctx *c) {
+    const int64_t s0 = c->step;
+    const int pc = c->pos_cur, mc = c->meta_cur;
+    int64_t before[MDLG_PROF_KINDS];
+    for (int k = 0; k < MDLG_PROF_KINDS; ++k) before[k] = c->launches[k];
+    const bool prof = c->prof;
+    c->prof = false;   // no event records inside the graph
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        c->prof = prof;
+        cudaGetLastError();
+        c->graph_failed = true;
+        return MDLG_OK;   // fall back to direct launches
+    }
+    const int rc = step_loop(c, c->graph_len, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+    c->prof = prof;
+    MDLG_TRY(rc);
+    MDLG_TRY(cuda_err(ec));
+    c->graph = g;
+    if (c->pos_cur != pc || c->meta_cur != mc) {   // cannot be replayed in place
+        c->graph_failed = true;
+        cudaGraphExec_t once = nullptr;
+        MDLG_TRY(cuda_err(cudaGraphInstantiate(&once, g, 0)));
+        const cudaError_t el = cudaGraphLaunch(once, c->stream);
+        cudaGraphExecDestroy(once);
+        drop_graph(c);
+        return cuda_err(el);
+    }
+    MDLG_TRY(cuda_err(cudaGraphInstantiate(&c->graph_exec, g, 0)));
+    for (int k = 0; k < MDLG_PROF_KINDS; ++k) c->graph_launches[k] = c->launches[k] - before[k];
+    c->graph_start = s0;
+    ProfScope ps(c, MDLG_PROF_STEP, 0);
+    return cuda_err(cudaGraphLaunch(c->graph_exec, c->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdlg_step(mdlg_ctx *c, int64_t nsteps) {
+    if (!c || nsteps < 0) return MDLG_EINVAL;
+    if (c->p.use_graphs && !c->graph_failed && c->graph_len == 0) {
+        c->graph_len = schedule_len(c);
+        if (c->graph_len > 8192) c->graph_failed = true;   // too long to be worth a graph
+    }
+    while (nsteps > 0) {
+        if (c->p.use_graphs && !c->graph_failed && nsteps >= c->graph_len) {
+            if (c->graph_exec && (c->step - c->graph_start) % c->graph_len == 0) {
+                {
+                    ProfScope ps(c, MDLG_PROF_STEP, 0);
+                    MDLG_TRY(cuda_err(cudaGraphLaunch(c->graph_exec, c->stream)));
+                }
+                for (int k = 0; k < MDLG_PROF_KINDS; ++k) c->launches[k] += c->graph_launches[k];
+                MDLG_TRY(step_loop(c, c->graph_len, false));
+                nsteps -= c->graph_len;
+                continue;
+            }
+            if (!c->graph_exec) {
+                const int64_t s0 = c->step;
+                MDLG_TRY(capture_and_launch(c));
+                nsteps -= c->step - s0;
+                continue;
+            }
+        }
+        MDLG_TRY(step_loop(c, 1, true));
+        nsteps -= 1;
     }
     return MDLG_OK;
 }
@@ -815,6 +929,7 @@ int mdlg_profile(mdlg_ctx *c, int enable, double *ms, int64_t *launches) {
 void mdlg_destroy(mdlg_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graph(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     free_all(c);
     delete c;

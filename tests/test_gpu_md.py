@@ -219,3 +219,34 @@ def test_production_run_invariants(cuda):
     e0, e1 = st0["kinetic"] + st0["potential"], st["kinetic"] + st["potential"]
     assert abs(e1 - e0) / c.n < 1e-3
     assert abs(st["momentum"][0]) / c.n < 1e-5
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_graph_replay_equals_direct_launches(cuda, batched):
+    # use_graphs: two periods of the schedule (sort every 5, lag 50 -> 100 steps)
+    # are captured once and replayed; results equal direct launches bit for bit.
+    import torch
+    c = mi.SMALL_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=5)
+    out = []
+    for graphs in (False, True):
+        p = m.Params(n=c.n, box=c.box, dx=c.dx, lag_steps=(50,), sort_every=5, stats_every=25,
+                     use_graphs=graphs)
+        stream = torch.cuda.Stream()
+        if batched:
+            sim = m.BatchSimulation(p, [c.n, c.n], [(c.box, c.box)] * 2, np.concatenate([x0, x0]),
+                                    np.concatenate([v0, v0]), stream=stream)
+        else:
+            sim = m.Simulation(p, x0, v0, stream=stream)
+        with sim:
+            sim.profile(True)
+            sim.step(250)      # graph: capture steps 0-99, replay 100-199, direct 200-249
+            sim.step(37)       # not aligned with the graph: direct launches
+            prof = sim.profile(False)
+            x, v = sim.get_state()
+            st, counts, _ = sim.stats()
+        out.append((x, v, counts, st, prof))
+    (x1, v1, c1, s1, p1), (x2, v2, c2, s2, p2) = out
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(c1, c2)
+    assert s1["kinetic"] == s2["kinetic"] and s1["intervals"] == s2["intervals"]
+    assert p1["step"][1] == p2["step"][1] and p1["sort"][1] == p2["sort"][1]

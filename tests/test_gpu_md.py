@@ -250,3 +250,15 @@ def test_graph_replay_equals_direct_launches(cuda, batched):
     assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(c1, c2)
     assert s1["kinetic"] == s2["kinetic"] and s1["intervals"] == s2["intervals"]
     assert p1["step"][1] == p2["step"][1] and p1["sort"][1] == p2["sort"][1]
+
+
+def test_tuner_times_candidates_on_gpu(cuda, tmp_path):
+    from paper_1705_04368_gb300 import tune
+    n, L = 4096, mi.box_for(4096, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=41)
+    p = m.Params(n=n, box=L, dx=4.0)
+    best, rep = tune.tune(p, x0, v0, 1.0, candidates=((0.5, 0.5), (0.25, 0.75)), steps=20,
+                          warmup=4, path=str(tmp_path / "t.json"))
+    assert {r["skin"] for r in rep["candidates"]} == {0.5, 0.75}
+    assert all(r["sec_per_step"] > 0 for r in rep["candidates"])
+    assert best.skin in (0.5, 0.75)

@@ -1,0 +1,43 @@
+"""Autotuner host logic (no GPU): candidate filtering, choice, cache round trip."""
+import json
+
+import numpy as np
+
+import paper_1705_04368_gb300 as m
+from paper_1705_04368_gb300 import tune
+
+
+def test_tuner_picks_fastest_and_caches(tmp_path):
+    p = m.Params(n=4096, box=120.0, dx=4.0)
+    calls = []
+
+    def fake_timer(cand, x0, v0, steps, warmup):
+        calls.append((cand.grid, cand.skin))
+        if cand.skin == 1.0:
+            raise RuntimeError("cannot build")
+        return 1e-3 * (1.0 + abs(cand.skin - 0.75)) * (1.1 if cand.grid == 0.25 else 1.0)
+
+    path = str(tmp_path / "tune.json")
+    best, rep = tune.tune(p, None, None, 1.0, timer=fake_timer, path=path)
+    assert (best.grid, best.skin) == (0.5, 0.75) and not rep["cached"]
+    assert any("error" in r for r in rep["candidates"])
+    data = json.load(open(path))
+    assert rep["key"] in data
+    # second call: cached, no timing
+    n_calls = len(calls)
+    best2, rep2 = tune.tune(p, None, None, 1.0, timer=fake_timer, path=path)
+    assert rep2["cached"] and len(calls) == n_calls and best2.skin == 0.75
+
+
+def test_tuner_skips_grids_that_do_not_divide(tmp_path):
+    p = m.Params(n=100, box=10.0, dx=2.5)      # 0.5 divides 2.5 and 10; 0.3 does not
+    seen = []
+
+    def timer(cand, *a):
+        seen.append(cand.grid)
+        return 1.0
+
+    best, rep = tune.tune(p, None, None, 1.0, candidates=((0.5, 0.5), (0.3, 0.5)), timer=timer,
+                          path=str(tmp_path / "t.json"))
+    assert seen == [0.5] and best.grid == 0.5
+    assert "rho=1" in rep["key"] and "n=1e+02" in rep["key"]

@@ -18,14 +18,15 @@ def test_tuner_picks_fastest_and_caches(tmp_path):
         return 1e-3 * (1.0 + abs(cand.skin - 0.75)) * (1.1 if cand.grid == 0.25 else 1.0)
 
     path = str(tmp_path / "tune.json")
-    best, rep = tune.tune(p, None, None, 1.0, timer=fake_timer, path=path)
+    cands = ((0.5, 0.5), (0.5, 0.75), (0.5, 1.0), (0.25, 0.75))
+    best, rep = tune.tune(p, None, None, 1.0, candidates=cands, timer=fake_timer, path=path)
     assert (best.grid, best.skin) == (0.5, 0.75) and not rep["cached"]
     assert any("error" in r for r in rep["candidates"])
     data = json.load(open(path))
     assert rep["key"] in data
     # second call: cached, no timing
     n_calls = len(calls)
-    best2, rep2 = tune.tune(p, None, None, 1.0, timer=fake_timer, path=path)
+    best2, rep2 = tune.tune(p, None, None, 1.0, candidates=cands, timer=fake_timer, path=path)
     assert rep2["cached"] and len(calls) == n_calls and best2.skin == 0.75
 
 

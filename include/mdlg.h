@@ -55,6 +55,8 @@ extern "C" {
 /* ---- potentials --------------------------------------------------------- */
 #define MDLG_POT_NONE   0    /* non-interacting gas (free flight)              */
 #define MDLG_POT_LJ_TS  1    /* Lennard-Jones, truncated at rc, energy shifted */
+#define MDLG_POT_LJ_SF  2    /* Lennard-Jones, shifted force: F(r) - F(rc) for r < rc,
+                                continuous at rc (energy V - V(rc) + (r - rc) F(rc)) */
 
 /* ---- per-site output modes (mdlg_params.site_mode, bit flags) ------------ */
 #define MDLG_SITES_FIELD 1   /* keep n_i(x,t), N(x,t) of the latest interval   */
@@ -69,7 +71,7 @@ typedef struct {
     int32_t dim;          /* must be 2 (the paper's test case, Sec. IV)          */
     int64_t n;            /* particles, >= 1                                     */
     double  box[2];       /* periodic box L_x, L_y; integer multiples of dx       */
-    int32_t potential;    /* MDLG_POT_LJ_TS or MDLG_POT_NONE                      */
+    int32_t potential;    /* MDLG_POT_LJ_TS, MDLG_POT_LJ_SF or MDLG_POT_NONE      */
     double  eps, sigma;   /* Lennard-Jones energy and length (Sec. IV)            */
     double  mass;         /* particle mass m                                     */
     double  rcut;         /* cutoff radius r_c (> 0)                              */
@@ -205,11 +207,36 @@ int mdlg_get_sites(mdlg_ctx *ctx, uint32_t *site_counts, uint32_t *ncell);
 int mdlg_reset_counts(mdlg_ctx *ctx);
 
 /*
- * mdlg_adjoint -- reverse-mode gradients of soft-binned MDLG moments with
- * respect to eps, sigma and the initial state.  Declared for the interface;
- * returns MDLG_ENOTIMPL in this version.
+ * mdlg_adjoint -- advance the context by nsteps MD steps (like mdlg_step) and
+ * return the gradient of a soft-binned MDLG loss over that interval with
+ * respect to eps, sigma and the state at its start.
+ *
+ * Loss: the cell indicator of Sec. III is smoothed with a Gaussian of standard
+ * deviation `width` (length units): u_c(x) = Phi((x - c dx)/w) - Phi((x - (c+1) dx)/w).
+ * The soft occupations of Eq. MDni between the start (t = 0) and the end
+ * (t = nsteps), averaged over particles, are
+ *     ftilde_i = (1/N) sum_j prod_a sum_c u_c(x_ja(end)) u_{c - v_ia}(x_ja(start))
+ * on the (2V+1)^2 window (index as everywhere; no overflow entry), and
+ *     loss = sum_i dloss_i ftilde_i.
+ * Gradients are taken through the leapfrog trajectory by a hand-written
+ * adjoint (Jacobian-vector products of the pair forces, FP32 per particle, FP64
+ * accumulation of the eps and sigma adjoints), re-computing each segment of
+ * ckpt_every steps from a checkpoint stored at its start.  x0 / v0 refer to the
+ * positions and integer-step velocities at the start of the call.
+ *   nsteps, ckpt_every : nsteps a multiple of ckpt_every; the context must have
+ *                        been created with sort_every == ckpt_every and be at a
+ *                        re-sort (true right after mdlg_create).
+ *   width              : 0 < width <= 0.875 dx;  V (params.vmax) <= 7.
+ *   dloss              : host, Q = (2V+1)^2 weights; NULL -> forward only
+ *                        (ftilde and loss, no gradients).
+ *   ftilde, loss       : host outputs (Q, 1), or NULL.
+ *   grad_eps, grad_sigma : host, 1 each, or NULL.
+ *   grad_x0, grad_v0   : host, n x 2 in the original particle order, or NULL.
+ * Single systems only (MDLG_EINVAL for a batch).  Synchronizes.  Allocates its
+ * checkpoints through the context's allocator for the duration of the call.
  */
-int mdlg_adjoint(mdlg_ctx *ctx, const double *dloss, double *grad_eps,
+int mdlg_adjoint(mdlg_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double width,
+                 const double *dloss, double *ftilde, double *loss, double *grad_eps,
                  double *grad_sigma, double *grad_x0, double *grad_v0);
 
 /*

@@ -73,6 +73,8 @@ def _load():
             lib.oracle_mdlg_bin.argtypes = [I64, P, P, D, P, ctypes.c_int, P, P, P, P]
             lib.oracle_stream_bin_f32.argtypes = [I64, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
             lib.oracle_kinetic.argtypes = [I64, P, D, P]
+            lib.oracle_set_shifted_force.argtypes = [ctypes.c_int]
+            lib.oracle_set_shifted_force.restype = None
             for name in ("oracle_lj_forces_direct", "oracle_lj_forces_cells",
                          "oracle_lj_forces_sample", "oracle_vv", "oracle_free_stream",
                          "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic"):
@@ -89,12 +91,14 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def lj_forces(x, box, eps=1.0, sigma=1.0, rc=2.5, cells=False):
+def lj_forces(x, box, eps=1.0, sigma=1.0, rc=2.5, cells=False, shifted_force=False):
     """Lennard-Jones forces, sum_j |F_ij| per particle, potential energy and virial.
 
     x: (n, 2) positions.  Returns (F (n,2), fscale (n,), pe, virial).
+    shifted_force: F(r) - F(rc) instead of the force truncated at rc.
     """
     lib = _load()
+    lib.oracle_set_shifted_force(int(shifted_force))
     x = _f64(x)
     n = x.shape[0]
     L = _f64(box)
@@ -106,9 +110,10 @@ def lj_forces(x, box, eps=1.0, sigma=1.0, rc=2.5, cells=False):
     return f, fs, float(out[0]), float(out[1])
 
 
-def lj_forces_sample(x, box, which, eps=1.0, sigma=1.0, rc=2.5):
+def lj_forces_sample(x, box, which, eps=1.0, sigma=1.0, rc=2.5, shifted_force=False):
     """Direct-sum forces for the particles listed in ``which`` only."""
     lib = _load()
+    lib.oracle_set_shifted_force(int(shifted_force))
     x = _f64(x)
     w = np.ascontiguousarray(which, dtype=np.int64)
     f = np.zeros((w.size, 2))
@@ -121,7 +126,8 @@ def lj_forces_sample(x, box, which, eps=1.0, sigma=1.0, rc=2.5):
 class VV:
     """Velocity-Verlet state (x, v, F) advanced by the oracle (FP64)."""
 
-    def __init__(self, x, v, box, dt, mass=1.0, eps=1.0, sigma=1.0, rc=2.5, cells=None):
+    def __init__(self, x, v, box, dt, mass=1.0, eps=1.0, sigma=1.0, rc=2.5, cells=None,
+                 shifted_force=False):
         self.x = _f64(x).copy()
         self.v = _f64(v).copy()
         self.f = np.zeros_like(self.x)
@@ -129,6 +135,7 @@ class VV:
         self.dt, self.mass, self.eps, self.sigma, self.rc = dt, mass, eps, sigma, rc
         n = self.x.shape[0]
         self.cells = (n > 2048) if cells is None else cells
+        self.shifted_force = bool(shifted_force)
         self.have_force = 0
         self.pe = 0.0
         self.virial = 0.0
@@ -136,6 +143,7 @@ class VV:
 
     def run(self, nsteps: int):
         lib = _load()
+        lib.oracle_set_shifted_force(int(self.shifted_force))
         out = np.zeros(2)
         lib.oracle_vv(self.x.shape[0], _p(self.x), _p(self.v), _p(self.f), self.have_force,
                       _p(self.box), self.mass, self.eps, self.sigma, self.rc, self.dt,
@@ -155,7 +163,7 @@ class VV:
         """Total energy KE + PE (the force routine's PE of the current state)."""
         if not self.have_force:
             _, _, self.pe, self.virial = lj_forces(self.x, self.box, self.eps, self.sigma,
-                                                   self.rc, self.cells)
+                                                   self.rc, self.cells, self.shifted_force)
         return float(self.kinetic()[0]) + self.pe
 
 

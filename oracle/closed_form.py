@@ -76,3 +76,50 @@ def a_ballistic(temperature: float, dt: float, dx: float, mass: float = 1.0) -> 
 def msd_exponential_vacf(temperature: float, tau: float, t: float) -> float:
     """<dx_a^2> for an exponentially decaying velocity autocorrelation (Eq. vca)."""
     return 2.0 * temperature * tau * tau * (math.exp(-t / tau) + t / tau - 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Soft-binned MDLG occupations (the differentiable loss of the adjoint)
+# ---------------------------------------------------------------------------
+# The cell indicator of Sec. III, 1 on (c dx, (c+1) dx], is replaced by the same
+# box smoothed with a Gaussian of standard deviation s:
+#     u_c(x) = Phi((x - c dx) / s) - Phi((x - (c+1) dx) / s),
+# so that sum_c u_c(x) = 1 and u_c -> indicator as s -> 0.  The soft occupation
+# of Eq. MDni over one interval, averaged over particles, is
+#     ft_i = (1/N) sum_j prod_a sum_c u_c(x_ja(t)) u_{c - v_ia}(x_ja(t - dt)).
+
+
+def _phi_cdf(z):
+    from scipy.special import ndtr
+    return ndtr(z)
+
+
+def soft_fi(x_end, x_start, box, dx, width, vmax):
+    """Soft f_i on the (2V+1)^2 window, index i = (v_y+V)(2V+1) + (v_x+V).
+
+    x_end, x_start: (n, 2) positions in (0, L]; the displacement is taken by
+    minimum image.  width: the smoothing s in length units.
+    """
+    x_end = np.asarray(x_end, dtype=np.float64)
+    x_start = np.asarray(x_start, dtype=np.float64)
+    L = np.asarray(box, dtype=np.float64).reshape(2)
+    w = 2 * vmax + 1
+    M = int(math.ceil(8.0 * width / dx)) + 1
+    k_axis = []
+    for a in range(2):
+        d = x_end[:, a] - x_start[:, a]
+        d -= L[a] * np.round(d / L[a])
+        ta = x_end[:, a] / dx                  # lattice units
+        tb = (x_end[:, a] - d) / dx            # start, unwrapped next to the end
+        sw = width / dx
+        base = np.floor(ta).astype(np.int64)
+        kv = np.zeros((x_end.shape[0], w))
+        for dc in range(-M, M + 1):
+            c = base + dc
+            ua = _phi_cdf((ta - c) / sw) - _phi_cdf((ta - c - 1) / sw)
+            for vi, v in enumerate(range(-vmax, vmax + 1)):
+                ub = _phi_cdf((tb - (c - v)) / sw) - _phi_cdf((tb - (c - v) - 1) / sw)
+                kv[:, vi] += ua * ub
+        k_axis.append(kv)
+    kx, ky = k_axis
+    return np.einsum("ny,nx->yx", ky, kx).ravel() / x_end.shape[0]

@@ -60,12 +60,42 @@ static double lj_v(double r2, double eps, double sigma)
 
 /* -(1/r) dV/dr = 24 eps [ 2 (sigma/r)^12 - (sigma/r)^6 ] / r^2 ; the force on
  * particle i from j is this scalar times (x_i - x_j). */
-static double lj_fscalar(double r2, double eps, double sigma)
+static double lj_fscalar_plain(double r2, double eps, double sigma)
 {
     double sr2 = sigma * sigma / r2;
     double sr6 = sr2 * sr2 * sr2;
     return 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
 }
+
+/*
+ * Shifted-force variant (g_sf = 1): the force magnitude is F(r) - F(rc) for
+ * r < rc, so it falls continuously to zero at the cutoff; the matching energy
+ * is V(r) - V(rc) + (r - rc) F(rc).  g_sf = 0: force truncated at rc, energy
+ * shifted by V(rc).
+ */
+static int g_sf = 0;
+static double g_rc = 0.0;
+
+static double lj_fscalar(double r2, double eps, double sigma)
+{
+    double f = lj_fscalar_plain(r2, eps, sigma);
+    if (g_sf) {
+        double fc = lj_fscalar_plain(g_rc * g_rc, eps, sigma) * g_rc;   /* |F(rc)| */
+        f -= fc / sqrt(r2);
+    }
+    return f;
+}
+
+/* pair energy relative to the cutoff: V(r) - V(rc) (+ (r - rc) F(rc) shifted force) */
+static double lj_pair_energy(double r2, double eps, double sigma)
+{
+    double e = lj_v(r2, eps, sigma) - lj_v(g_rc * g_rc, eps, sigma);
+    if (g_sf) e += (sqrt(r2) - g_rc) * lj_fscalar_plain(g_rc * g_rc, eps, sigma) * g_rc;
+    return e;
+}
+
+/* Select the cutoff treatment for the following calls. */
+void oracle_set_shifted_force(int sf) { g_sf = sf; }
 
 /*
  * Direct O(N^2) forces: F_i = -d/dx_i sum_{j != i} V(|x_i - x_j|) over all
@@ -83,8 +113,9 @@ void oracle_lj_forces_direct(int64_t n, const double *x, const double *L,
                              double eps, double sigma, double rc,
                              double *f, double *fscale, double *out)
 {
-    double rc2 = rc * rc, vshift = lj_v(rc2, eps, sigma);
+    double rc2 = rc * rc;
     double pe = 0.0, vir = 0.0;
+    g_rc = rc;
     for (int64_t i = 0; i < n; ++i) {
         double fx = 0.0, fy = 0.0, fs = 0.0;
         for (int64_t j = 0; j < n; ++j) {
@@ -97,7 +128,7 @@ void oracle_lj_forces_direct(int64_t n, const double *x, const double *L,
             fx += s * dx;
             fy += s * dy;
             fs += fabs(s) * sqrt(r2);
-            pe += 0.5 * (lj_v(r2, eps, sigma) - vshift);
+            pe += 0.5 * lj_pair_energy(r2, eps, sigma);
             vir += 0.5 * s * r2;
         }
         f[2 * i] = fx;
@@ -118,6 +149,7 @@ void oracle_lj_forces_sample(int64_t n, const double *x, const double *L,
                              double *f, double *fscale)
 {
     double rc2 = rc * rc;
+    g_rc = rc;
     for (int64_t k = 0; k < ns; ++k) {
         int64_t i = which[k];
         double fx = 0.0, fy = 0.0, fs = 0.0;
@@ -170,8 +202,9 @@ void oracle_lj_forces_cells(int64_t n, const double *x, const double *L,
         next[i] = head[b * ncx + a];
         head[b * ncx + a] = i;
     }
-    double rc2 = rc * rc, vshift = lj_v(rc2, eps, sigma);
+    double rc2 = rc * rc;
     double pe = 0.0, vir = 0.0;
+    g_rc = rc;
     for (int64_t i = 0; i < n; ++i) {
         double fx = 0.0, fy = 0.0, fs = 0.0;
         for (int oy = -1; oy <= 1; ++oy)
@@ -187,7 +220,7 @@ void oracle_lj_forces_cells(int64_t n, const double *x, const double *L,
                     fx += s * dx;
                     fy += s * dy;
                     fs += fabs(s) * sqrt(r2);
-                    pe += 0.5 * (lj_v(r2, eps, sigma) - vshift);
+                    pe += 0.5 * lj_pair_energy(r2, eps, sigma);
                     vir += 0.5 * s * r2;
                 }
             }

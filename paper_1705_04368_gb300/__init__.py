@@ -3,10 +3,10 @@
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/mdlg.h``); this package only marshals arguments to it.
 """
-from .binding import (MAX_LAGS, MAX_VMAX, POT_LJ_TS, POT_NONE, SITES_ACCUM, SITES_FIELD,
+from .binding import (MAX_LAGS, MAX_VMAX, POT_LJ_SF, POT_LJ_TS, POT_NONE, SITES_ACCUM, SITES_FIELD,
                       BatchSimulation, MdlgError, Params, Simulation, bin_snapshots, header_functions,
                       idealgas_bin, lib)
 
-__all__ = ["BatchSimulation", "MAX_LAGS", "MAX_VMAX", "POT_LJ_TS", "POT_NONE", "SITES_ACCUM", "SITES_FIELD",
+__all__ = ["BatchSimulation", "MAX_LAGS", "MAX_VMAX", "POT_LJ_SF", "POT_LJ_TS", "POT_NONE", "SITES_ACCUM", "SITES_FIELD",
            "MdlgError", "Params", "Simulation", "bin_snapshots", "header_functions",
            "idealgas_bin", "lib"]

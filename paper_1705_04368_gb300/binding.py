@@ -23,6 +23,7 @@ MAX_COMBOS = 16
 STATIC_MAX_N = 65536      # mdlg_forces_static particle limit (MDLG_STATIC_MAX_N)
 POT_NONE = 0
 POT_LJ_TS = 1
+POT_LJ_SF = 2
 SITES_FIELD = 1
 SITES_ACCUM = 2
 
@@ -84,7 +85,8 @@ _SIGNATURES = {
     "mdlg_get_state": (ctypes.c_int, [_P, _P, _P, _P]),
     "mdlg_get_sites": (ctypes.c_int, [_P, _P, _P]),
     "mdlg_reset_counts": (ctypes.c_int, [_P]),
-    "mdlg_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "mdlg_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P, _P,
+                                    _P, _P, _P, _P, _P]),
     "mdlg_profile": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "mdlg_destroy": (None, [_P]),
     "mdlg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -266,6 +268,33 @@ class Simulation:
         nc = np.zeros(cy * cx, np.uint32)
         _check(self._lib.mdlg_get_sites(self._h, sc.ctypes.data, nc.ctypes.data), "mdlg_get_sites")
         return sc, nc
+
+    def adjoint(self, nsteps: int, ckpt_every: int, width: float, dloss=None):
+        """mdlg_adjoint: advance nsteps and differentiate the soft-binned loss.
+
+        Returns {"ftilde": (Q,), "loss": float} and, when ``dloss`` (Q weights)
+        is given, "grad_eps", "grad_sigma", "grad_x0" (n, 2), "grad_v0" (n, 2).
+        """
+        q = (2 * self.params.vmax + 1) ** 2
+        ft = np.zeros(q)
+        loss = ctypes.c_double(0.0)
+        out = {"ftilde": ft}
+        if dloss is None:
+            _check(self._lib.mdlg_adjoint(self._h, int(nsteps), int(ckpt_every), float(width),
+                                          None, ft.ctypes.data, ctypes.byref(loss), None, None,
+                                          None, None), "mdlg_adjoint")
+        else:
+            w = np.ascontiguousarray(dloss, dtype=np.float64).reshape(q)
+            ge, gs = ctypes.c_double(0.0), ctypes.c_double(0.0)
+            gx = np.zeros((self.params.n, 2))
+            gv = np.zeros((self.params.n, 2))
+            _check(self._lib.mdlg_adjoint(self._h, int(nsteps), int(ckpt_every), float(width),
+                                          w.ctypes.data, ft.ctypes.data, ctypes.byref(loss),
+                                          ctypes.byref(ge), ctypes.byref(gs), gx.ctypes.data,
+                                          gv.ctypes.data), "mdlg_adjoint")
+            out.update(grad_eps=ge.value, grad_sigma=gs.value, grad_x0=gx, grad_v0=gv)
+        out["loss"] = loss.value
+        return out
 
     PROF_KINDS = ("step", "sort", "bin", "sync")
 

@@ -166,9 +166,12 @@ int log2_exact(int32_t v) {
 int validate(const mdlg_params *p) {
     if (!p) return MDLG_EINVAL;
     if (p->dim != 2 || p->n < 1 || p->n > 2000000000LL) return MDLG_EINVAL;
-    if (p->potential != MDLG_POT_LJ_TS && p->potential != MDLG_POT_NONE) return MDLG_EINVAL;
+    if (p->potential != MDLG_POT_LJ_TS && p->potential != MDLG_POT_LJ_SF &&
+        p->potential != MDLG_POT_NONE)
+        return MDLG_EINVAL;
+    const bool lj = p->potential != MDLG_POT_NONE;
     if (!(p->dt > 0.0) || !(p->mass > 0.0) || !is_pow2(p->grid)) return MDLG_EINVAL;
-    if (p->potential == MDLG_POT_LJ_TS &&
+    if (lj &&
         (!(p->rcut > 0.0) || !(p->sigma > 0.0) || !std::isfinite(p->eps)))
         return MDLG_EINVAL;
     if (!(p->skin >= 0.0)) return MDLG_EINVAL;
@@ -186,10 +189,10 @@ int validate(const mdlg_params *p) {
         if (lat < 1 || lat > 65535) return MDLG_EINVAL;
         int64_t lg = exact_ratio(p->box[a], p->grid);
         if (lg < 1 || lg > 65535) return MDLG_EINVAL;
-        if (p->potential == MDLG_POT_LJ_TS && !(p->rcut < 0.5 * p->box[a])) return MDLG_EINVAL;
+        if (lj && !(p->rcut < 0.5 * p->box[a])) return MDLG_EINVAL;
     }
     // Verlet-list entries carry the particle index in 28 bits
-    if (p->potential == MDLG_POT_LJ_TS && p->n >= (1LL << 28)) return MDLG_EINVAL;
+    if (lj && p->n >= (1LL << 28)) return MDLG_EINVAL;
     return MDLG_OK;
 }
 
@@ -202,6 +205,19 @@ Batch batch_of(mdlg_ctx *c) {
         b.nsys = c->nsys;
     }
     return b;
+}
+
+// Magnitude of the Lennard-Jones pair force at the cutoff, F(rc) =
+// 24 eps (2 (s/rc)^12 - (s/rc)^6) / rc, and its derivative in sigma (the
+// shifted-force potential subtracts F(rc) so the force vanishes at rc).
+double lj_fc(const mdlg_params &p) {
+    const double sr6 = std::pow(p.sigma / p.rcut, 6.0);
+    return 24.0 * p.eps * (2.0 * sr6 * sr6 - sr6) / p.rcut;
+}
+
+double lj_dfc_dsigma(const mdlg_params &p) {
+    const double sr6 = std::pow(p.sigma / p.rcut, 6.0);
+    return 24.0 * p.eps * (24.0 * sr6 * sr6 - 6.0 * sr6) / (p.sigma * p.rcut);
 }
 
 StepArgs step_args(mdlg_ctx *c) {
@@ -231,7 +247,8 @@ StepArgs step_args(mdlg_ctx *c) {
     a.cell_w = (float)(c->geo.k * c->p.grid);
     a.rc = c->p.potential ? (float)rc : 0.f;
     a.round_margin = c->round_margin;
-    a.potential = c->p.potential == MDLG_POT_LJ_TS ? 1 : 0;
+    a.potential = c->p.potential == MDLG_POT_LJ_TS ? 1 : (c->p.potential == MDLG_POT_LJ_SF ? 2 : 0);
+    a.fc = (float)lj_fc(c->p);
     a.partials = c->partials;
     a.ctl = c->ctl;
     a.nbr = c->nbr;
@@ -362,7 +379,7 @@ int system_geom(const mdlg_params &p, const double box[2], Geom &g) {
     g.g = (float)p.grid;
     g.inv_g = (float)(1.0 / p.grid);
     g.ratio = (int32_t)exact_ratio(p.dx, p.grid);
-    const double reach = p.potential == MDLG_POT_LJ_TS ? p.rcut + p.skin : 4.0;
+    const double reach = p.potential != MDLG_POT_NONE ? p.rcut + p.skin : 4.0;
     g.k = (int32_t)std::ceil(reach / p.grid - 1e-12);
     if (g.k < 1) g.k = 1;
     for (int a = 0; a < 2; ++a) {
@@ -372,7 +389,7 @@ int system_geom(const mdlg_params &p, const double box[2], Geom &g) {
         if (g.lg[a] % g.ratio) return MDLG_EINVAL;
     }
     g.vmax = p.vmax;
-    if (p.potential == MDLG_POT_LJ_TS && (g.nc[0] < 3 || g.nc[1] < 3)) return MDLG_EINVAL;
+    if (p.potential != MDLG_POT_NONE && (g.nc[0] < 3 || g.nc[1] < 3)) return MDLG_EINVAL;
     if (g.nc[0] < 1) g.nc[0] = 1;
     if (g.nc[1] < 1) g.nc[1] = 1;
     return MDLG_OK;
@@ -519,7 +536,7 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         if ((rc = alloc_n(c, &c->site_n, sites)) || (rc = alloc_n(c, &c->site_counts, sites * c->q1)))
             return fail(rc);
     }
-    if (p.potential == MDLG_POT_LJ_TS) {
+    if (p.potential != MDLG_POT_NONE) {
         // Verlet list of radius = the MD cell width (rc + the whole skin);
         // capacity three times the mean count at the highest density, plus 16
         c->list_radius = (float)(g.k * p.grid);
@@ -894,10 +911,265 @@ int mdlg_reset_counts(mdlg_ctx *c) {
     return MDLG_OK;
 }
 
-int mdlg_adjoint(mdlg_ctx *c, const double *dloss, double *grad_eps, double *grad_sigma,
-                 double *grad_x0, double *grad_v0) {
-    (void)c; (void)dloss; (void)grad_eps; (void)grad_sigma; (void)grad_x0; (void)grad_v0;
-    return MDLG_ENOTIMPL;
+}  // extern "C"
+
+namespace {
+
+// Device allocations that live for one call (through the context's allocator).
+struct TempAlloc {
+    mdlg_ctx *c;
+    std::vector<void *> ptrs;
+    explicit TempAlloc(mdlg_ctx *ctx) : c(ctx) {}
+    template <typename T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        const size_t bytes = sizeof(T) * (count ? count : 1);
+        if (c->use_cuda_malloc) {
+            if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); p = nullptr; }
+        } else {
+            p = c->alloc.alloc(bytes, c->alloc.user);
+        }
+        if (p) ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    ~TempAlloc() {
+        cudaStreamSynchronize(c->stream);
+        for (void *p : ptrs) {
+            if (c->use_cuda_malloc) cudaFree(p);
+            else c->alloc.free(p, c->alloc.user);
+        }
+    }
+};
+
+struct Checkpoint {
+    float2 *cl, *v;
+    uint32_t *cell, *nbr;
+    int32_t *pid, *cell_start, *ncount;
+};
+
+}  // namespace
+
+extern "C" {
+
+int mdlg_adjoint(mdlg_ctx *c, int64_t nsteps, int32_t ckpt_every, double width,
+                 const double *dloss, double *ftilde, double *loss, double *grad_eps,
+                 double *grad_sigma, double *grad_x0, double *grad_v0) {
+    if (!c || c->nsys != 0 || nsteps < 1 || ckpt_every < 1 || nsteps % ckpt_every) return MDLG_EINVAL;
+    if (c->sort_every != ckpt_every || c->step != c->last_sort) return MDLG_EINVAL;
+    const mdlg_params &p = c->p;
+    if (!(width > 0.0) || width > 0.875 * p.dx || p.vmax > 7) return MDLG_EINVAL;
+    const int64_t N = c->slots;
+    const int Q = (2 * p.vmax + 1) * (2 * p.vmax + 1);
+    const int64_t nseg = nsteps / ckpt_every;
+    const size_t nc1 = (size_t)c->ncells + 1;
+    cudaStream_t s = c->stream;
+    TempAlloc tmp(c);
+    auto chk = [](cudaError_t e) { return cuda_err(e); };
+#define ADJ_ALLOC(ptr, T, count)                 \
+    do {                                         \
+        ptr = tmp.get<T>(count);                 \
+        if (!ptr) return MDLG_ENOMEM;            \
+    } while (0)
+    double *x_start, *gx0, *theta, *fsum, *lossd, *wts = nullptr;
+    float2 *traj, *vbuf, *xb[2], *w[2], *xb_orig, *w_orig;
+    float *dck, *dfinal;
+    ADJ_ALLOC(x_start, double, 2 * N);
+    ADJ_ALLOC(gx0, double, 2 * N);
+    ADJ_ALLOC(theta, double, 2);
+    ADJ_ALLOC(fsum, double, Q);
+    ADJ_ALLOC(lossd, double, 1);
+    ADJ_ALLOC(dck, float, nseg);
+    ADJ_ALLOC(dfinal, float, 1);
+    std::vector<Checkpoint> ck((size_t)nseg);
+    for (auto &k : ck) {
+        ADJ_ALLOC(k.cl, float2, N);
+        ADJ_ALLOC(k.v, float2, N);
+        ADJ_ALLOC(k.cell, uint32_t, N);
+        ADJ_ALLOC(k.pid, int32_t, N);
+        ADJ_ALLOC(k.cell_start, int32_t, nc1);
+        k.nbr = nullptr;
+        k.ncount = nullptr;
+        if (c->nbr) {
+            ADJ_ALLOC(k.nbr, uint32_t, (size_t)c->cap * N);
+            ADJ_ALLOC(k.ncount, int32_t, N);
+        }
+    }
+    if (dloss) {
+        ADJ_ALLOC(wts, double, Q);
+        ADJ_ALLOC(traj, float2, (size_t)(ckpt_every + 1) * N);
+        ADJ_ALLOC(vbuf, float2, 2 * N);
+        for (int b = 0; b < 2; ++b) {
+            ADJ_ALLOC(xb[b], float2, N);
+            ADJ_ALLOC(w[b], float2, N);
+        }
+        ADJ_ALLOC(xb_orig, float2, N);
+        ADJ_ALLOC(w_orig, float2, N);
+    }
+#undef ADJ_ALLOC
+    MDLG_TRY(chk(cudaMemsetAsync(theta, 0, 2 * sizeof(double), s)));
+    MDLG_TRY(chk(cudaMemsetAsync(fsum, 0, Q * sizeof(double), s)));
+    MDLG_TRY(chk(cudaMemsetAsync(lossd, 0, sizeof(double), s)));
+    if (dloss)
+        MDLG_TRY(chk(cudaMemcpyAsync(wts, dloss, Q * sizeof(double), cudaMemcpyHostToDevice, s)));
+
+    // start positions (original order)
+    MDLG_TRY(chk(launch_unpack(c->geo, N, c->cell[c->meta_cur], c->cl[c->pos_cur], c->vsync,
+                               c->fsync, c->pid[c->meta_cur], x_start, nullptr, nullptr, s)));
+    // forward: a checkpoint after every re-sort (the segment boundaries)
+    const int64_t s0 = c->step;
+    for (int64_t g = 0; g < nseg; ++g) {
+        if (g > 0) MDLG_TRY(do_sort(c));
+        Checkpoint &k = ck[(size_t)g];
+        MDLG_TRY(chk(cudaMemcpyAsync(k.cl, c->cl[c->pos_cur], N * sizeof(float2), cudaMemcpyDeviceToDevice, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(k.v, c->vel[c->pos_cur], N * sizeof(float2), cudaMemcpyDeviceToDevice, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(k.cell, c->cell[c->meta_cur], N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(k.pid, c->pid[c->meta_cur], N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(k.cell_start, c->cell_start, nc1 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)));
+        if (c->nbr) {
+            MDLG_TRY(chk(cudaMemcpyAsync(k.nbr, c->nbr, (size_t)c->cap * N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)));
+            MDLG_TRY(chk(cudaMemcpyAsync(k.ncount, c->ncount, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)));
+        }
+        MDLG_TRY(chk(cudaMemcpyAsync(dck + g, &c->ctl->dbound, sizeof(float), cudaMemcpyDeviceToDevice, s)));
+        MDLG_TRY(step_loop(c, ckpt_every, true));
+    }
+    MDLG_TRY(chk(cudaMemcpyAsync(dfinal, &c->ctl->dbound, sizeof(float), cudaMemcpyDeviceToDevice, s)));
+
+    // soft loss on the final state (order of the last segment)
+    SoftArgs la{};
+    la.geo = c->geo;
+    la.n = N;
+    la.ntot = p.n;
+    la.cell = c->cell[c->meta_cur];
+    la.cl = c->cl[c->pos_cur];
+    la.pid = c->pid[c->meta_cur];
+    la.x_start = x_start;
+    la.dx = p.dx;
+    la.width = width;
+    la.vmax = p.vmax;
+    la.M = (int32_t)std::ceil(8.0 * width / p.dx) + 1;
+    la.weights = wts;
+    la.fsum = fsum;
+    la.loss = lossd;
+    la.xb = dloss ? xb[0] : nullptr;
+    la.gx_start = dloss ? gx0 : nullptr;
+    if (dloss) MDLG_TRY(chk(cudaMemsetAsync(gx0, 0, 2 * N * sizeof(double), s)));
+    MDLG_TRY(chk(launch_soft_loss(la, s)));
+
+    if (dloss) {
+        // adjoint state in original order between segments
+        MDLG_TRY(chk(launch_permute(N, c->pid[c->meta_cur], xb[0], xb_orig, true, s)));
+        MDLG_TRY(chk(cudaMemsetAsync(w_orig, 0, N * sizeof(float2), s)));
+        AdjArgs aa{};
+        aa.geo = c->geo;
+        aa.n = N;
+        aa.cap = c->cap;
+        aa.list_skin = c->list_radius - (float)p.rcut;
+        aa.rc = (float)p.rcut;
+        aa.rc2 = (float)(p.rcut * p.rcut);
+        aa.cell_w = (float)(c->geo.k * p.grid);
+        aa.eps24 = (float)(24.0 * p.eps);
+        aa.sig2 = (float)(p.sigma * p.sigma);
+        aa.inv_eps = p.eps != 0.0 ? (float)(1.0 / p.eps) : 0.f;
+        aa.inv_sigma = (float)(1.0 / p.sigma);
+        aa.theta = theta;
+        aa.ctl = c->ctl;
+        aa.potential = p.potential == MDLG_POT_LJ_TS ? 1 : (p.potential == MDLG_POT_LJ_SF ? 2 : 0);
+        aa.fc = (float)lj_fc(p);
+        aa.dfc_dsigma = (float)lj_dfc_dsigma(p);
+        const float dt = (float)p.dt, dt_m = (float)(p.dt / p.mass);
+        for (int64_t g = nseg - 1; g >= 0; --g) {
+            const Checkpoint &k = ck[(size_t)g];
+            MDLG_TRY(chk(launch_permute(N, k.pid, xb_orig, xb[0], false, s)));
+            MDLG_TRY(chk(launch_permute(N, k.pid, w_orig, w[0], false, s)));
+            // recompute the segment from its checkpoint, keeping every position
+            MDLG_TRY(chk(cudaMemcpyAsync(&c->ctl->dbound, dck + g, sizeof(float), cudaMemcpyDeviceToDevice, s)));
+            MDLG_TRY(chk(cudaMemcpyAsync(traj, k.cl, N * sizeof(float2), cudaMemcpyDeviceToDevice, s)));
+            MDLG_TRY(chk(cudaMemcpyAsync(vbuf, k.v, N * sizeof(float2), cudaMemcpyDeviceToDevice, s)));
+            for (int t = 0; t < ckpt_every; ++t) {
+                StepArgs a = step_args(c);
+                a.cell = k.cell;
+                a.cell_start = k.cell_start;
+                a.nbr = k.nbr;
+                a.ncount = k.ncount;
+                a.cl_in = traj + (size_t)t * N;
+                a.cl_out = traj + (size_t)(t + 1) * N;
+                a.v_in = vbuf + (size_t)(t & 1) * N;
+                a.v_out = vbuf + (size_t)((t + 1) & 1) * N;
+                const int64_t step = s0 + g * ckpt_every + t;
+                a.stats = (p.stats_every > 0 && step % p.stats_every == 0) ? 1 : 0;
+                MDLG_TRY(chk(launch_step(a, kModeStep, s)));
+            }
+            // reverse the segment's steps
+            aa.cell = k.cell;
+            aa.cell_start = k.cell_start;
+            aa.nbr = k.nbr;
+            aa.ncount = k.ncount;
+            int cur = 0;
+            for (int t = ckpt_every - 1; t >= 0; --t) {
+                aa.x = traj + (size_t)t * N;
+                aa.a_coef = dt;
+                aa.b_coef = dt_m;
+                aa.w_prev = w[cur];
+                aa.xb = xb[cur];
+                aa.w_out = w[cur ^ 1];
+                aa.xb_out = xb[cur ^ 1];
+                MDLG_TRY(chk(launch_adjoint_step(aa, s)));
+                cur ^= 1;
+            }
+            if (g == 0) {
+                // the half kick that turns the integer-step velocity into v_{-1/2}
+                MDLG_TRY(chk(cudaMemcpyAsync(&c->ctl->dbound, dck, sizeof(float), cudaMemcpyDeviceToDevice, s)));
+                aa.x = traj;
+                aa.a_coef = 0.f;
+                aa.b_coef = -0.5f * dt_m;
+                aa.w_prev = w[cur];
+                aa.xb = xb[cur];
+                aa.w_out = w[cur ^ 1];
+                aa.xb_out = xb[cur ^ 1];
+                MDLG_TRY(chk(launch_adjoint_step(aa, s)));
+                cur ^= 1;
+            }
+            MDLG_TRY(chk(launch_permute(N, k.pid, xb[cur], xb_orig, true, s)));
+            MDLG_TRY(chk(launch_permute(N, k.pid, w[cur], w_orig, true, s)));
+        }
+        MDLG_TRY(chk(cudaMemcpyAsync(&c->ctl->dbound, dfinal, sizeof(float), cudaMemcpyDeviceToDevice, s)));
+    }
+    c->stats_step = -1;   // the recompute overwrote the last statistics
+
+    // results to the host
+    std::vector<double> hf(Q), hx((size_t)2 * p.n), hg((size_t)2 * p.n);
+    std::vector<float2> hxo, hwo;
+    double hl = 0.0, ht[2] = {0.0, 0.0};
+    MDLG_TRY(chk(cudaMemcpyAsync(hf.data(), fsum, Q * sizeof(double), cudaMemcpyDeviceToHost, s)));
+    MDLG_TRY(chk(cudaMemcpyAsync(&hl, lossd, sizeof(double), cudaMemcpyDeviceToHost, s)));
+    if (dloss) {
+        hxo.resize((size_t)p.n);
+        hwo.resize((size_t)p.n);
+        MDLG_TRY(chk(cudaMemcpyAsync(ht, theta, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(hg.data(), gx0, 2 * p.n * sizeof(double), cudaMemcpyDeviceToHost, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(hxo.data(), xb_orig, p.n * sizeof(float2), cudaMemcpyDeviceToHost, s)));
+        MDLG_TRY(chk(cudaMemcpyAsync(hwo.data(), w_orig, p.n * sizeof(float2), cudaMemcpyDeviceToHost, s)));
+    }
+    MDLG_TRY(chk(cudaStreamSynchronize(s)));
+    int32_t status = 0;
+    MDLG_TRY(read_status(c, &status, nullptr));
+    if (ftilde) memcpy(ftilde, hf.data(), Q * sizeof(double));
+    if (loss) *loss = hl;
+    if (dloss) {
+        if (grad_eps) *grad_eps = ht[0];
+        if (grad_sigma) *grad_sigma = ht[1];
+        for (int64_t i = 0; i < p.n; ++i) {
+            if (grad_x0) {
+                grad_x0[2 * i] = (double)hxo[i].x + hg[2 * i];
+                grad_x0[2 * i + 1] = (double)hxo[i].y + hg[2 * i + 1];
+            }
+            if (grad_v0) {
+                grad_v0[2 * i] = hwo[i].x;
+                grad_v0[2 * i + 1] = hwo[i].y;
+            }
+        }
+    }
+    return status ? status : MDLG_OK;
 }
 
 int mdlg_profile(mdlg_ctx *c, int enable, double *ms, int64_t *launches) {

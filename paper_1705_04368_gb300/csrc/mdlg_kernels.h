@@ -138,7 +138,8 @@ struct StepArgs {
     const int32_t *ncount;      // entries per particle (cap + 1: overflowed)
     int32_t cap;                // list capacity per particle
     float list_skin;            // list radius - rc
-    int32_t potential;          // 0 none, 1 LJ
+    int32_t potential;          // 0 none, 1 LJ truncated-shifted, 2 LJ shifted-force
+    float fc;                   // |F(rc)| (shifted-force subtracts it)
     int32_t stats;              // 1: FP64 reductions into partials
     long long *partials;        // gridDim.x x 5 fixed-point block sums
     Control *ctl;
@@ -197,5 +198,50 @@ cudaError_t launch_unpack(const Geom &geo, int64_t n, const uint32_t *cell, cons
                           const float2 *vsync, const float2 *fsync, const int32_t *pid,
                           double *x, double *v, double *f, cudaStream_t s,
                           const Batch *batch = nullptr);
+
+// ---- adjoint ---------------------------------------------------------------
+struct SoftArgs {
+    Geom geo;
+    int64_t n;                  // slots of the (single-system) state
+    int64_t ntot;               // particles
+    const uint32_t *cell;
+    const float2 *cl;
+    const int32_t *pid;
+    const double *x_start;      // start positions, original order (n x 2)
+    double dx, width;           // lattice spacing, smoothing s (length units)
+    int32_t vmax, M;            // window half-width; cells searched each side
+    const double *weights;      // Q loss weights, or null
+    double *fsum;               // Q soft f_i (added to), or null
+    double *loss;               // 1 (added to), or null
+    float2 *xb;                 // dL/dx at the end, state order, or null
+    double *gx_start;           // dL/dx at the start (direct term), original order, or null
+};
+
+struct AdjArgs {
+    Geom geo;
+    int64_t n;
+    const uint32_t *cell;
+    const int32_t *cell_start;
+    const float2 *x;            // positions of the step being reversed
+    const uint32_t *nbr;
+    const int32_t *ncount;
+    int32_t cap;
+    float list_skin, rc, rc2, cell_w;
+    float eps24, sig2, inv_eps, inv_sigma;
+    float a_coef, b_coef;       // w = w_prev + a xb;  xb_out = xb + b (dF/dx)^T w
+    const float2 *w_prev;
+    const float2 *xb;
+    float2 *w_out;
+    float2 *xb_out;
+    double *theta;              // [eps, sigma] adjoint accumulators (added to)
+    Control *ctl;               // displacement bound at the end of the segment
+    int32_t potential;          // 0 none, 1 truncated-shifted, 2 shifted-force
+    float fc, dfc_dsigma;       // |F(rc)| and its sigma derivative (shifted force)
+};
+
+cudaError_t launch_soft_loss(const SoftArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint_step(const AdjArgs &a, cudaStream_t s);
+cudaError_t launch_permute(int64_t n, const int32_t *pid, const float2 *src, float2 *dst,
+                           bool to_original, cudaStream_t s);
 
 }  // namespace mdlg

@@ -79,11 +79,18 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
         const float ir2 = __fdividef(1.0f, r2);   // hardware reciprocal, <= 2 ulp
         const float sr2 = a.sig2 * ir2;
         const float sr6 = sr2 * sr2 * sr2;
-        const float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+        float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+        float ir = 0.f;
+        if (a.potential == 2) {          // shifted force: subtract F(rc) along the pair
+            ir = rsqrtf(r2);
+            fs -= a.fc * ir;
+        }
         acc.fx = fmaf(fs, dx, acc.fx);
         acc.fy = fmaf(fs, dy, acc.fy);
         if (STATS) {
-            acc.pe += a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
+            float e = a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
+            if (a.potential == 2) e = fmaf(a.fc, r2 * ir - a.rc, e);   // + (r - rc) F(rc)
+            acc.pe += e;
             acc.vir = fmaf(fs, r2, acc.vir);
         }
     }
@@ -100,11 +107,19 @@ __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, fl
     const float ir2 = __fdividef(1.0f, r2);   // hardware reciprocal, <= 2 ulp
     const float sr2 = a.sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
-    const float fs = on * (a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f));
+    float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+    float ir = 0.f;
+    if (a.potential == 2) {              // shifted force: subtract F(rc) along the pair
+        ir = rsqrtf(r2);
+        fs -= a.fc * ir;
+    }
+    fs *= on;
     acc.fx = fmaf(fs, dx, acc.fx);
     acc.fy = fmaf(fs, dy, acc.fy);
     if (STATS) {
-        acc.pe = fmaf(on, a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift, acc.pe);
+        float e = a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
+        if (a.potential == 2) e = fmaf(a.fc, r2 * ir - a.rc, e);       // + (r - rc) F(rc)
+        acc.pe = fmaf(on, e, acc.pe);
         acc.vir = fmaf(fs, r2, acc.vir);
     }
 }

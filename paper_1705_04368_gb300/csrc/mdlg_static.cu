@@ -110,7 +110,9 @@ int64_t ratio_of(double value, double unit) {
 extern "C" int mdlg_forces_static(const mdlg_params *p, const double *x, const double *v,
                                   double *f, double *obs, int32_t *status, void *stream) {
     if (!p || !x || !v || !f || !obs) return MDLG_EINVAL;
-    if (p->dim != 2 || p->n < 1 || p->potential != MDLG_POT_LJ_TS) return MDLG_EINVAL;
+    if (p->dim != 2 || p->n < 1 ||
+        (p->potential != MDLG_POT_LJ_TS && p->potential != MDLG_POT_LJ_SF))
+        return MDLG_EINVAL;
     if (!(p->rcut > 0.0) || !(p->sigma > 0.0) || !std::isfinite(p->eps) || !(p->mass > 0.0) ||
         !(p->skin >= 0.0) || !pow2(p->grid))
         return MDLG_EINVAL;
@@ -204,7 +206,8 @@ extern "C" int mdlg_forces_static(const mdlg_params *p, const double *x, const d
     a.mass = (float)p->mass;
     a.cell_w = (float)(geo.k * p->grid);
     a.rc = (float)rcut;
-    a.potential = 1;
+    a.potential = p->potential == MDLG_POT_LJ_SF ? 2 : 1;
+    a.fc = (float)(24.0 * ep * (2.0 * sr6 * sr6 - sr6) / rcut);
     a.stats = 1;
     a.partials = static_cast<long long *>(at(L.partials));
     a.ctl = ctl;

@@ -112,5 +112,5 @@ def test_context_free_entry_points_validate():
     assert L.mdlg_idealgas_bin(0, None, None, 1, d.ctypes.data, d.ctypes.data, 3, buf, None) == 0
 
 
-def test_adjoint_declared_not_implemented():
-    assert m.lib().mdlg_adjoint(None, None, None, None, None, None) == -7
+def test_adjoint_rejects_null_context():
+    assert m.lib().mdlg_adjoint(None, 10, 10, 1.0, None, None, None, None, None, None, None) == -1

@@ -145,3 +145,39 @@ def test_small_config_energy_drift():
     e0 = s.energy()
     s.run(2000)
     assert abs(s.energy() - e0) / c.n < 2e-3
+
+
+def test_shifted_force_vanishes_continuously_at_cutoff():
+    # shifted force: F(rc-) = 0 and the pair energy is 0 at rc, with no jump
+    f_in, _, pe_in, _ = oracle.lj_forces(_pair(2.5 - 1e-7), BOX, shifted_force=True)
+    f_out, _, pe_out, _ = oracle.lj_forces(_pair(2.5 + 1e-7), BOX, shifted_force=True)
+    assert np.abs(f_in).max() < 1e-6 and abs(pe_in) < 1e-12 and pe_out == 0   # F ~ F'(rc) 1e-7
+    # truncated force: a jump of |F(rc)| = 24 (2 rc^-13 - rc^-7) at the cutoff
+    f_ts, _, _, _ = oracle.lj_forces(_pair(2.5 - 1e-9, 0.0), BOX)
+    assert abs(np.hypot(*f_ts[0])) == pytest.approx(abs(24 * (2 * 2.5 ** -13 - 2.5 ** -7)),
+                                                    rel=1e-6)
+
+
+@pytest.mark.parametrize("sf", [False, True])
+def test_force_is_minus_gradient_both_cutoffs(sf):
+    x, _ = mi.lj_initial_state(60, 12.0, 1.0, seed=13)
+    box = (12.0, 12.0)
+    f, _, _, _ = oracle.lj_forces(x, box, shifted_force=sf)
+    h = 1e-6
+    for i in (1, 22, 50):
+        for a in (0, 1):
+            xp, xm = x.copy(), x.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            g = (oracle.lj_forces(xp, box, shifted_force=sf)[2]
+                 - oracle.lj_forces(xm, box, shifted_force=sf)[2]) / (2 * h)
+            assert -g == pytest.approx(f[i, a], rel=1e-6, abs=1e-6)
+
+
+def test_shifted_force_conserves_energy_tightly():
+    # continuous forces: VV energy error is second order without cutoff kicks
+    x, v = mi.lj_initial_state(200, 28.0, 1.0, seed=11)
+    s = oracle.VV(x, v, (28.0, 28.0), dt=0.002, shifted_force=True)
+    e0 = s.energy()
+    s.run(500)
+    assert abs(s.energy() - e0) / 200 < 2e-4

@@ -257,6 +257,9 @@ def run_ours(args, rank, world, local_rank):
     # batched replicas (256 systems) against the same systems one context at a time
     batched = _batched(m, torch, stream, local_rank) if rank == 0 else None
 
+    # adjoint (N = 16 384, rho = 0.3, K = 200, checkpoints every 20) versus the plain forward
+    adjoint = _adjoint(m, torch, stream, local_rank) if rank == 0 else None
+
     # end to end through the C ABI: pinned host state in, f_i out, every step
     e2e = _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev)
 
@@ -265,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(c, world), "roofline": roofline,
             "gpu_launches": launches, "kernels": kernels, "clocks": clk, "e2e": e2e,
-            "idealgas": ig, "batched": batched, "status": st["status"],
+            "idealgas": ig, "batched": batched, "adjoint": adjoint, "status": st["status"],
             "tuned": {"grid": params.grid, "skin": params.skin,
                       "cell_width": params.grid * math.ceil((params.rcut + params.skin) / params.grid - 1e-12),
                       "cached": tune_report["cached"]}}
@@ -350,6 +353,38 @@ def _batched(m, torch, stream, local_rank, md_steps=700):
             "batched_particle_steps_per_s": total * md_steps / t_batch,
             "one_context_each_particle_steps_per_s": total * md_steps / t_alone,
             "speedup": t_alone / t_batch, "status": st["status"]}
+
+
+def _adjoint(m, torch, stream, local_rank, reps=3):
+    """Seconds for the gradient of the soft-binned second moment over 200 steps
+    (shifted-force LJ, N = 16 384, rho = 0.3, T = 1, checkpoints every 20) against
+    the plain 200-step forward of the same system."""
+    n, K, ck = 16384, 200, 20
+    L = mi.box_for(n, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=16387)
+    vel = np.array([(vx, vy) for vy in range(-3, 4) for vx in range(-3, 4)], np.float64)
+    w = (vel ** 2).sum(axis=1)
+    p = m.Params(n=n, box=L, dx=4.0, sort_every=ck, potential=m.POT_LJ_SF)
+
+    def run(kind):
+        with m.Simulation(p, x0, v0, stream=stream, device=local_rank) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if kind == "forward":
+                s.step(K)
+                s.stats()
+            else:
+                s.adjoint(K, ck, 2.0, dloss=w)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0
+
+    run("forward"), run("adjoint")            # warm up
+    tf = min(run("forward") for _ in range(reps))
+    ta = min(run("adjoint") for _ in range(reps))
+    return {"workload": "lj2d_sf_n16384_rho0.3_T1_K200_ckpt20", "forward_s": tf,
+            "adjoint_s": ta, "adjoint_over_forward": ta / tf,
+            "what": "mdlg_adjoint with gradients (forward with checkpoints, segment "
+                    "recompute, reverse sweep, soft loss) vs mdlg_step(200) + mdlg_stats"}
 
 
 def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev):

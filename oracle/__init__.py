@@ -8,7 +8,9 @@ imports the other.
 Contents
   mdlg_oracle.c  plain C, FP64: direct O(N^2) and linked-cell Lennard-Jones
                  forces, velocity-Verlet, MDLG occupation numbers (Eq. MDni),
-                 the binary32 ideal-gas stream-and-bin, FP64 reductions.
+                 the binary32 ideal-gas stream-and-bin, FP64 reductions, the
+                 moving lattice of Sec. IV, the collision operator Xi_i (Eq.
+                 Xi), the mean-square displacement (Sec. IV-A).
   closed_form.py the Gaussian/wedge equilibrium of Eq. fialpha.
 
 Parity status per function (what pins it, see tests/test_oracle_*.py):
@@ -23,6 +25,16 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                      conservation across intervals, boundary convention.
   stream_bin_f32     pinned: equal to mdlg_bin on the same binary32 points; its
                      totals match the closed form within sampling error.
+  mdlg_bin (shifted) pinned: equal to binning the shifted, wrapped positions;
+                     whole-box shifts change nothing; a gas at rest seen from
+                     the moving lattice matches the closed form at mean
+                     velocity u (chi-square).
+  stream_bin_f32 us  pinned: equal to boosting the binary32 velocities first;
+                     closed form at u (chi-square).
+  collision          pinned: particle-by-particle tracking (brute force), mass
+                     conservation without overflow, the Fig. 2 worked example.
+  msd                pinned: exact dyadic free flight across the boundary; the
+                     ballistic value T dt^2 within sampling error.
   closed_form        pinned: numerical quadrature of the wedge integral (Eq.
                      fieqW), Monte-Carlo binning, normalisation and first
                      moment identities, the second-moment offset of Sec. VI.
@@ -71,13 +83,17 @@ def _load():
                                       ctypes.c_int, P]
             lib.oracle_free_stream.argtypes = [I64, P, P, P, D, I64]
             lib.oracle_mdlg_bin.argtypes = [I64, P, P, D, P, ctypes.c_int, P, P, P, P]
-            lib.oracle_stream_bin_f32.argtypes = [I64, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
+            lib.oracle_stream_bin_f32.argtypes = [I64, P, P, ctypes.c_int, P, P, P, ctypes.c_int, P]
+            lib.oracle_mdlg_bin_shifted.argtypes = [I64, P, P, D, P, ctypes.c_int, P, P, P, P, P, P]
+            lib.oracle_collision.argtypes = [P, ctypes.c_int, P, P, P]
+            lib.oracle_msd.argtypes = [I64, P, P, P, P]
             lib.oracle_kinetic.argtypes = [I64, P, D, P]
             lib.oracle_set_shifted_force.argtypes = [ctypes.c_int]
             lib.oracle_set_shifted_force.restype = None
             for name in ("oracle_lj_forces_direct", "oracle_lj_forces_cells",
                          "oracle_lj_forces_sample", "oracle_vv", "oracle_free_stream",
-                         "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic"):
+                         "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic",
+                         "oracle_mdlg_bin_shifted", "oracle_collision", "oracle_msd"):
                 getattr(lib, name).restype = None
             _lib = lib
     return _lib
@@ -174,7 +190,8 @@ def free_stream(x, v, box, dt, nsteps=1):
     return x
 
 
-def mdlg_bin(xprev, xcur, dx, cells, vmax, field=False, counts=None, ncell=None, fld=None):
+def mdlg_bin(xprev, xcur, dx, cells, vmax, field=False, counts=None, ncell=None, fld=None,
+             shift_prev=None, shift_cur=None):
     """Occupation numbers of Eq. MDni for one pair of snapshots.
 
     Returns (counts (Q+1,) uint64, ncell (Cy*Cx,) uint32, field (Cy*Cx, Q+1) uint32
@@ -189,13 +206,20 @@ def mdlg_bin(xprev, xcur, dx, cells, vmax, field=False, counts=None, ncell=None,
     if field and fld is None:
         fld = np.zeros((int(C[0] * C[1]), q1), np.uint32)
     vsum = np.zeros(2, np.int64)
-    lib.oracle_mdlg_bin(xp.shape[0], _p(xp), _p(xc), float(dx), _p(C), int(vmax),
-                        _p(counts), _p(ncell), _p(fld) if fld is not None else None, _p(vsum))
+    sp = _f64(shift_prev) if shift_prev is not None else None
+    sc = _f64(shift_cur) if shift_cur is not None else None
+    lib.oracle_mdlg_bin_shifted(xp.shape[0], _p(xp), _p(xc), float(dx), _p(C), int(vmax),
+                                _p(sp) if sp is not None else None,
+                                _p(sc) if sc is not None else None,
+                                _p(counts), _p(ncell), _p(fld) if fld is not None else None,
+                                _p(vsum))
     return counts, ncell, fld, vsum
 
 
-def stream_bin_f32(pos, vel, dxs, dts, vmax):
-    """Ideal-gas stream + bin in binary32 decisions; returns (ncombo, Q+1) uint64."""
+def stream_bin_f32(pos, vel, dxs, dts, vmax, us=None):
+    """Ideal-gas stream + bin in binary32 decisions; returns (ncombo, Q+1) uint64.
+
+    us: optional (ncombo, 2) lattice velocities U (velocities boosted by U)."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float32)
     vel = np.ascontiguousarray(vel, dtype=np.float32)
@@ -203,9 +227,31 @@ def stream_bin_f32(pos, vel, dxs, dts, vmax):
     dts = np.ascontiguousarray(dts, dtype=np.float32)
     q1 = (2 * vmax + 1) ** 2 + 1
     counts = np.zeros((dxs.size, q1), np.uint64)
+    u = np.ascontiguousarray(us, dtype=np.float32).reshape(-1, 2) if us is not None else None
     lib.oracle_stream_bin_f32(pos.shape[0], _p(pos), _p(vel), dxs.size, _p(dxs), _p(dts),
-                              int(vmax), _p(counts))
+                              _p(u) if u is not None else None, int(vmax), _p(counts))
     return counts
+
+
+def collision(cells, vmax, field_prev, field_cur):
+    """Xi_i(x) = n_i(x + v_i, t+dt) - n_i(x, t) (Eq. Xi); (C_y*C_x, Q) int64."""
+    lib = _load()
+    C = np.ascontiguousarray(cells, dtype=np.int64)
+    q = (2 * vmax + 1) ** 2
+    fp = np.ascontiguousarray(field_prev, dtype=np.uint32)
+    fc = np.ascontiguousarray(field_cur, dtype=np.uint32)
+    xi = np.zeros((int(C[0] * C[1]), q), np.int64)
+    lib.oracle_collision(_p(C), int(vmax), _p(fp), _p(fc), _p(xi))
+    return xi
+
+
+def msd(xprev, xcur, box):
+    """<dx_a^2> per axis between two snapshots (minimum image)."""
+    lib = _load()
+    xp, xc = _f64(xprev), _f64(xcur)
+    out = np.zeros(2)
+    lib.oracle_msd(xp.shape[0], _p(xp), _p(xc), _p(_f64(box)), _p(out))
+    return out
 
 
 def velocity_table(vmax):

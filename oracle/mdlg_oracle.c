@@ -293,6 +293,12 @@ static int64_t lattice_disp(int64_t d, int64_t C)
     return r;
 }
 
+void oracle_mdlg_bin_shifted(int64_t n, const double *xprev, const double *xcur,
+                             double dx, const int64_t *C, int vmax,
+                             const double *s_prev, const double *s_cur,
+                             uint64_t *counts, uint32_t *ncell, uint32_t *field,
+                             int64_t *vsum);
+
 /*
  * n_i(x,t) = sum_j Delta_x(x_j(t)) Delta_{x - v_i}(x_j(t - dt))   (Eq. MDni)
  * and N(x,t) = sum_j Delta_x(x_j(t))                               (Sec. III)
@@ -315,10 +321,34 @@ void oracle_mdlg_bin(int64_t n, const double *xprev, const double *xcur,
                      uint64_t *counts, uint32_t *ncell, uint32_t *field,
                      int64_t *vsum)
 {
+    oracle_mdlg_bin_shifted(n, xprev, xcur, dx, C, vmax, NULL, NULL, counts, ncell, field, vsum);
+}
+
+/*
+ * The same with a moving lattice (Sec. IV: a lattice displaced by -U dt gives
+ * the distribution at mean velocity U): each snapshot is binned at x + S, S the
+ * lattice displacement of its time (S_prev, S_cur; NULL = none), the sum taken
+ * in FP64 and the cell then wrapped into the lattice.
+ */
+void oracle_mdlg_bin_shifted(int64_t n, const double *xprev, const double *xcur,
+                             double dx, const int64_t *C, int vmax,
+                             const double *s_prev, const double *s_cur,
+                             uint64_t *counts, uint32_t *ncell, uint32_t *field,
+                             int64_t *vsum)
+{
     int64_t W = 2 * vmax + 1, Q = W * W;
+    const double zero[2] = {0.0, 0.0};
+    if (!s_prev) s_prev = zero;
+    if (!s_cur) s_cur = zero;
     for (int64_t j = 0; j < n; ++j) {
-        int64_t c0x = lattice_cell(xprev[2 * j], dx), c0y = lattice_cell(xprev[2 * j + 1], dx);
-        int64_t c1x = lattice_cell(xcur[2 * j], dx), c1y = lattice_cell(xcur[2 * j + 1], dx);
+        int64_t c0x = lattice_cell(xprev[2 * j] + s_prev[0], dx);
+        int64_t c0y = lattice_cell(xprev[2 * j + 1] + s_prev[1], dx);
+        int64_t c1x = lattice_cell(xcur[2 * j] + s_cur[0], dx);
+        int64_t c1y = lattice_cell(xcur[2 * j + 1] + s_cur[1], dx);
+        c0x = ((c0x % C[0]) + C[0]) % C[0];
+        c0y = ((c0y % C[1]) + C[1]) % C[1];
+        c1x = ((c1x % C[0]) + C[0]) % C[0];
+        c1y = ((c1y % C[1]) + C[1]) % C[1];
         int64_t vx = lattice_disp(c1x - c0x, C[0]);
         int64_t vy = lattice_disp(c1y - c0y, C[1]);
         int64_t i;
@@ -342,13 +372,15 @@ void oracle_mdlg_bin(int64_t n, const double *xprev, const double *xcur,
  * in: x' = fl(x + fl(v dt)) (not wrapped), cell = ceil(fl(x / dx)) - 1 per
  * axis, lattice velocity = cell(x') - cell(x).  For |v dt| < L/2 this is the
  * periodic definition of Eq. MDni, with the site taken modulo C in integers.
+ * With us (ncombo x 2, NULL = none) every velocity is first boosted by U:
+ * v' = fl(v + U), the moving-lattice reading of Sec. IV.
  *
  *   pos, vel : n x 2 binary32 values, positions in (0, L]
  *   counts   : ncombo x (Q+1) totals (added to)
  */
 void oracle_stream_bin_f32(int64_t n, const float *pos, const float *vel,
                            int ncombo, const float *dxs, const float *dts,
-                           int vmax, uint64_t *counts)
+                           const float *us, int vmax, uint64_t *counts)
 {
     int64_t W = 2 * vmax + 1, Q = W * W;
     for (int k = 0; k < ncombo; ++k) {
@@ -357,7 +389,9 @@ void oracle_stream_bin_f32(int64_t n, const float *pos, const float *vel,
             int64_t c[2][2];
             for (int a = 0; a < 2; ++a) {
                 volatile float x = pos[2 * j + a];
-                volatile float d = vel[2 * j + a] * dt;   /* one rounding */
+                /* moving lattice (Sec. IV): velocity boosted by U, one rounding */
+                volatile float vb = us ? vel[2 * j + a] + us[2 * k + a] : vel[2 * j + a];
+                volatile float d = vb * dt;                /* one rounding */
                 volatile float xn = x + d;                 /* one rounding */
                 volatile float q0 = x / dx, q1 = xn / dx;  /* one rounding each */
                 c[a][0] = (int64_t)ceilf(q0) - 1;
@@ -385,4 +419,45 @@ void oracle_kinetic(int64_t n, const double *v, double mass, double *out)
         py += mass * v[2 * i + 1];
     }
     out[0] = ke; out[1] = px; out[2] = py;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MDLG collision operator (Sec. III, Eq. Xi)                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Xi_i(x) = n_i(x + v_i, t + dt) - n_i(x, t) for the (2V+1)^2 window velocities,
+ * from the occupation fields of two consecutive intervals (site-major, Q+1
+ * entries per site as oracle_mdlg_bin writes them).  xi: C[0]*C[1] x Q.
+ */
+void oracle_collision(const int64_t *C, int vmax, const uint32_t *field_prev,
+                      const uint32_t *field_cur, int64_t *xi)
+{
+    int64_t W = 2 * vmax + 1, Q = W * W;
+    for (int64_t sy = 0; sy < C[1]; ++sy)
+        for (int64_t sx = 0; sx < C[0]; ++sx)
+            for (int64_t i = 0; i < Q; ++i) {
+                int64_t vx = i % W - vmax, vy = i / W - vmax;
+                int64_t tx = ((sx + vx) % C[0] + C[0]) % C[0];
+                int64_t ty = ((sy + vy) % C[1] + C[1]) % C[1];
+                int64_t site = sy * C[0] + sx, dest = ty * C[0] + tx;
+                xi[site * Q + i] = (int64_t)field_cur[dest * (Q + 1) + i] -
+                                   (int64_t)field_prev[site * (Q + 1) + i];
+            }
+}
+
+/* Mean over particles of the squared displacement per axis (minimum image),
+ * <dx_a^2> of Sec. IV-A between two snapshots. */
+void oracle_msd(int64_t n, const double *xprev, const double *xcur, const double *L,
+                double *out)
+{
+    double sx = 0.0, sy = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double dx = min_image(xcur[2 * j] - xprev[2 * j], L[0]);
+        double dy = min_image(xcur[2 * j + 1] - xprev[2 * j + 1], L[1]);
+        sx += dx * dx;
+        sy += dy * dy;
+    }
+    out[0] = n ? sx / (double)n : 0.0;
+    out[1] = n ? sy / (double)n : 0.0;
 }

@@ -61,6 +61,9 @@ extern "C" {
 /* ---- per-site output modes (mdlg_params.site_mode, bit flags) ------------ */
 #define MDLG_SITES_FIELD 1   /* keep n_i(x,t), N(x,t) of the latest interval   */
 #define MDLG_SITES_ACCUM 2   /* accumulate sum_t n_i(x,t), sum_t N(x,t)        */
+#define MDLG_SITES_XI    4   /* with MDLG_SITES_FIELD: also keep the previous
+                                interval's n_i and form the collision operator
+                                Xi_i(x) of Eq. Xi after every interval          */
 
 /*
  * Parameters of one simulation (Sec. III: N particles, periodic box, pair
@@ -88,7 +91,17 @@ typedef struct {
     int32_t use_graphs;   /* 1: mdlg_step captures two periods of its launch schedule
                              (lcm of sort_every, the lags and stats_every) in a CUDA
                              graph and replays it; stretches shorter than that, and
-                             schedules longer than 8192 steps, launch directly     */
+                             schedules longer than 8192 steps, launch directly.
+                             Ignored (direct launches) while the lattice moves.   */
+    double  lattice_u[2]; /* lattice drift U (length / time), Sec. IV: the lattice
+                             is displaced by -U t, i.e. every binning at MD step n
+                             places a particle by x + S(n), S(n) = n * s1 modulo the
+                             box, with the per-step shift s1 = U dt rounded to the
+                             nearest multiple of grid * 2^-24 (the effective U is
+                             reported by mdlg_stats).  The cell decision of x + S is
+                             exact.  {0, 0}: the lattice is at rest.               */
+    int32_t msd;          /* 1: accumulate, for every lag, the mean-square
+                             displacement <dx_a^2> over the lag (Sec. IV-A)       */
 } mdlg_params;
 
 /*
@@ -116,6 +129,10 @@ typedef struct {
     double  pressure;             /* (kinetic + virial / 2) / (L_x L_y)           */
     int64_t intervals[MDLG_MAX_LAGS]; /* coarse intervals binned per lag          */
     int32_t status;               /* MDLG_OK or the first device-side error seen  */
+    double  msd[MDLG_MAX_LAGS][2];/* params.msd: <dx_a^2> per lag and axis, the mean
+                                     over particles and binned intervals of the
+                                     squared displacement over the lag (0 if off) */
+    double  lattice_u[2];         /* effective lattice drift: s1 / dt            */
 } mdlg_stats_out;
 
 /*
@@ -141,8 +158,9 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
  * kernel launch of mdlg_step covers every system, and each system's forces,
  * trajectory and counts are exactly those of a context made for it alone with
  * the same sort_every (set sort_every > 0 to compare).
- *   params : shared parameters; params->n and params->box are ignored and
- *            params->site_mode must be 0.
+ *   params : shared parameters; params->n and params->box are ignored;
+ *            params->site_mode and params->msd must be 0 and
+ *            params->lattice_u {0, 0}.
  *   nsys   : systems, 1..65535.
  *   n      : host, nsys particle counts (the total below 2^28).
  *   box    : host, nsys x 2 box sides, each a multiple of params->dx.
@@ -202,6 +220,24 @@ int mdlg_get_state(mdlg_ctx *ctx, double *x, double *v, double *f);
  */
 int mdlg_get_sites(mdlg_ctx *ctx, uint32_t *site_counts, uint32_t *ncell);
 
+/*
+ * mdlg_get_collision -- synchronize and copy the MDLG collision operator of
+ * the last two lag-0 intervals (site_mode MDLG_SITES_FIELD | MDLG_SITES_XI):
+ * with t the time between them (Sec. III, Eq. Xi)
+ *     Xi_i(x) = n_i(x + v_i, t + dt) - n_i(x, t)
+ * for the (2V+1)^2 window velocities (the overflow entry has no destination
+ * and is left out), and per site its mass and momentum sums
+ *     dmass(x) = sum_i Xi_i(x),  dmom_a(x) = sum_i v_ia Xi_i(x)
+ * (Eqs. masscons, momentumcons: the first vanishes when no move leaves the
+ * window, the second in general does not).
+ *   xi    : host, C_y*C_x*Q int32, site-major (site = c_y*C_x + c_x), or NULL.
+ *   dmass : host, C_y*C_x int32, or NULL.
+ *   dmom  : host, C_y*C_x*2 int32 (x, y per site), or NULL.
+ * MDLG_EINVAL if the mode is off or fewer than two lag-0 intervals have been
+ * binned since creation or the last mdlg_reset_counts.
+ */
+int mdlg_get_collision(mdlg_ctx *ctx, int32_t *xi, int32_t *dmass, int32_t *dmom);
+
 /* mdlg_reset_counts -- enqueue zeroing of all MDLG totals and per-site outputs,
  * keeping the stored earlier lattice cells (to discard an equilibration). */
 int mdlg_reset_counts(mdlg_ctx *ctx);
@@ -232,6 +268,7 @@ int mdlg_reset_counts(mdlg_ctx *ctx);
  *   ftilde, loss       : host outputs (Q, 1), or NULL.
  *   grad_eps, grad_sigma : host, 1 each, or NULL.
  *   grad_x0, grad_v0   : host, n x 2 in the original particle order, or NULL.
+ * The soft-binned loss uses the lattice at rest (lattice_u does not enter it).
  * Single systems only (MDLG_EINVAL for a batch).  Synchronizes.  Allocates its
  * checkpoints through the context's allocator for the duration of the call.
  */
@@ -291,20 +328,43 @@ int mdlg_bin(const mdlg_lattice *lat, int64_t n, const int32_t *idx_prev,
              uint32_t *field, void *stream);
 
 /*
+ * mdlg_collision -- the collision operator of Eq. Xi from two occupation
+ * fields of consecutive intervals (as mdlg_bin or mdlg_get_sites write them):
+ *     Xi_i(x) = n_i(x + v_i, t + dt) - n_i(x, t),  window velocities only,
+ * with x + v_i wrapped into the lattice, plus dmass(x) = sum_i Xi_i(x) and
+ * dmom_a(x) = sum_i v_ia Xi_i(x).
+ *   lat        : lattice (lat->base / lat->ratio cells per axis, lat->vmax).
+ *   field_prev : device, C_y*C_x*(Q+1) uint32 n_i(x, t), site-major.
+ *   field_cur  : device, the same for the next interval, n_i(x, t + dt).
+ *   xi         : device, C_y*C_x*Q int32 (written), or NULL.
+ *   dmass      : device, C_y*C_x int32 (written), or NULL.
+ *   dmom       : device, C_y*C_x*2 int32 (written), or NULL.
+ *   stream     : cudaStream_t (as void*).
+ * Counts above 2^31 - 1 wrap.  Errors: MDLG_EINVAL (bad lattice, NULL field),
+ * MDLG_ECUDA.
+ */
+int mdlg_collision(const mdlg_lattice *lat, const uint32_t *field_prev,
+                   const uint32_t *field_cur, int32_t *xi, int32_t *dmass, int32_t *dmom,
+                   void *stream);
+
+/*
  * mdlg_idealgas_bin -- non-interacting gas of Sec. IV-A (ballistic limit):
  * stream every particle freely for each (dx_k, dt_k) pair and bin its start
  * and end points (Eq. MDni), all pairs in one pass over the particles.  The
  * cell decisions are taken in IEEE binary32:
- *   x' = fl(x + fl(v dt_k)),  cell = ceil(fl(x / dx_k)) - 1 per axis,
+ *   x' = fl(x + fl(v' dt_k)),  cell = ceil(fl(x / dx_k)) - 1 per axis,
  *   v_i = cell(x') - cell(x)  (x' is not wrapped; the box is a multiple of
- *   every dx_k and |v dt_k| < L/2 is assumed, as in the paper's regime).
+ *   every dx_k and |v dt_k| < L/2 is assumed, as in the paper's regime),
+ * where v' = v, or v' = fl(v + U_k) with a lattice drift U_k per pair (the
+ * moving lattice of Sec. IV: the gas seen at mean velocity U_k).
  *   pos, vel : device, n x 2 float (x, y) pairs; positions in (0, L].
  *   dxs, dts : host, ncombo values each; 1 <= ncombo <= MDLG_MAX_COMBOS.
+ *   us       : host, ncombo x 2 drifts (U_x, U_y), or NULL for none.
  *   counts   : device, ncombo x (Q+1) uint64, ADDED to.
  * Errors: MDLG_EINVAL, MDLG_ECUDA.
  */
 int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t ncombo,
-                      const float *dxs, const float *dts, int32_t vmax,
+                      const float *dxs, const float *dts, const float *us, int32_t vmax,
                       uint64_t *counts, void *stream);
 
 /*

@@ -26,6 +26,7 @@ POT_LJ_TS = 1
 POT_LJ_SF = 2
 SITES_FIELD = 1
 SITES_ACCUM = 2
+SITES_XI = 4
 
 ERRORS = {0: "MDLG_OK", -1: "MDLG_EINVAL", -2: "MDLG_ENOMEM", -3: "MDLG_ECUDA",
           -4: "MDLG_EOVERFLOW", -5: "MDLG_ENONFINITE", -6: "MDLG_ETIMEOUT", -7: "MDLG_ENOTIMPL"}
@@ -46,7 +47,8 @@ class _Params(ctypes.Structure):
                 ("dx", ctypes.c_double), ("nlags", ctypes.c_int32),
                 ("lag_steps", ctypes.c_int32 * MAX_LAGS), ("vmax", ctypes.c_int32),
                 ("site_mode", ctypes.c_int32), ("stats_every", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("lattice_u", ctypes.c_double * 2),
+                ("msd", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -54,7 +56,8 @@ class _Stats(ctypes.Structure):
                 ("kinetic", ctypes.c_double), ("potential", ctypes.c_double),
                 ("virial", ctypes.c_double), ("momentum", ctypes.c_double * 2),
                 ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
-                ("intervals", ctypes.c_int64 * MAX_LAGS), ("status", ctypes.c_int32)]
+                ("intervals", ctypes.c_int64 * MAX_LAGS), ("status", ctypes.c_int32),
+                ("msd", (ctypes.c_double * 2) * MAX_LAGS), ("lattice_u", ctypes.c_double * 2)]
 
 
 class _Lattice(ctypes.Structure):
@@ -84,6 +87,8 @@ _SIGNATURES = {
     "mdlg_stats": (ctypes.c_int, [_P, ctypes.POINTER(_Stats), _P, _P]),
     "mdlg_get_state": (ctypes.c_int, [_P, _P, _P, _P]),
     "mdlg_get_sites": (ctypes.c_int, [_P, _P, _P]),
+    "mdlg_get_collision": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mdlg_collision": (ctypes.c_int, [ctypes.POINTER(_Lattice), _P, _P, _P, _P, _P, _P]),
     "mdlg_reset_counts": (ctypes.c_int, [_P]),
     "mdlg_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P, _P,
                                     _P, _P, _P, _P, _P]),
@@ -91,7 +96,7 @@ _SIGNATURES = {
     "mdlg_destroy": (None, [_P]),
     "mdlg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mdlg_bin": (ctypes.c_int, [ctypes.POINTER(_Lattice), ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
-    "mdlg_idealgas_bin": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P,
+    "mdlg_idealgas_bin": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P, _P,
                                          ctypes.c_int32, _P, _P]),
     "mdlg_forces_static": (ctypes.c_int, [ctypes.POINTER(_Params), _P, _P, _P, _P, _P, _P]),
 }
@@ -181,6 +186,8 @@ class Params:
     site_mode: int = 0
     stats_every: int = 0
     use_graphs: bool = False
+    lattice_u: tuple = (0.0, 0.0)
+    msd: bool = False
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -203,6 +210,8 @@ class Params:
         p.site_mode = int(self.site_mode)
         p.stats_every = int(self.stats_every)
         p.use_graphs = int(bool(self.use_graphs))
+        p.lattice_u[0], p.lattice_u[1] = float(self.lattice_u[0]), float(self.lattice_u[1])
+        p.msd = int(bool(self.msd))
         return p
 
     @property
@@ -251,6 +260,8 @@ class Simulation:
                                           "temperature", "pressure", "status")}
         d["momentum"] = (out.momentum[0], out.momentum[1])
         d["intervals"] = [out.intervals[i] for i in range(nl)]
+        d["msd"] = [(out.msd[i][0], out.msd[i][1]) for i in range(nl)]
+        d["lattice_u"] = (out.lattice_u[0], out.lattice_u[1])
         return d, counts, fi
 
     def get_state(self, want_force: bool = False):
@@ -268,6 +279,18 @@ class Simulation:
         nc = np.zeros(cy * cx, np.uint32)
         _check(self._lib.mdlg_get_sites(self._h, sc.ctypes.data, nc.ctypes.data), "mdlg_get_sites")
         return sc, nc
+
+    def get_collision(self):
+        """Xi_i(x) (sites, Q) int32 of the last two lag-0 intervals, with the
+        per-site mass (sites,) and momentum (sites, 2) sums (mdlg_get_collision)."""
+        cx, cy = self.params.lattice_cells
+        q = self.params.q1 - 1
+        xi = np.zeros((cy * cx, q), np.int32)
+        dm = np.zeros(cy * cx, np.int32)
+        dj = np.zeros((cy * cx, 2), np.int32)
+        _check(self._lib.mdlg_get_collision(self._h, xi.ctypes.data, dm.ctypes.data, dj.ctypes.data),
+               "mdlg_get_collision")
+        return xi, dm, dj
 
     def adjoint(self, nsteps: int, ckpt_every: int, width: float, dloss=None):
         """mdlg_adjoint: advance nsteps and differentiate the soft-binned loss.
@@ -386,11 +409,27 @@ def bin_snapshots(base: Sequence[int], ratio: int, vmax: int, idx_prev, idx_cur,
                           _ptr(ncell), _ptr(field), _stream_handle(stream)), "mdlg_bin")
 
 
-def idealgas_bin(pos, vel, combos: Sequence[tuple], vmax: int, counts, stream=None):
-    """mdlg_idealgas_bin: pos/vel float32 (n, 2) on the GPU; counts int64 (ncombo, Q+1)."""
+def idealgas_bin(pos, vel, combos: Sequence[tuple], vmax: int, counts, stream=None, us=None):
+    """mdlg_idealgas_bin: pos/vel float32 (n, 2) on the GPU; counts int64 (ncombo, Q+1);
+    us: optional (ncombo, 2) lattice drifts."""
     dxs = np.ascontiguousarray([c[0] for c in combos], dtype=np.float32)
     dts = np.ascontiguousarray([c[1] for c in combos], dtype=np.float32)
+    u = None
+    if us is not None:
+        u = np.ascontiguousarray(us, dtype=np.float32).reshape(len(combos), 2)
     n = int(pos.shape[0])
     _check(lib().mdlg_idealgas_bin(n, _ptr(pos), _ptr(vel), len(combos), dxs.ctypes.data,
-                                   dts.ctypes.data, int(vmax), _ptr(counts),
-                                   _stream_handle(stream)), "mdlg_idealgas_bin")
+                                   dts.ctypes.data, u.ctypes.data if u is not None else None,
+                                   int(vmax), _ptr(counts), _stream_handle(stream)),
+           "mdlg_idealgas_bin")
+
+
+def collision(lattice_cells: Sequence[int], vmax: int, field_prev, field_cur, xi=None, dmass=None,
+              dmom=None, stream=None):
+    """mdlg_collision: fields uint32/int32 (sites, Q+1) on the GPU; outputs int32
+    xi (sites, Q), dmass (sites,), dmom (sites, 2), each optional."""
+    lat = _Lattice()
+    lat.base[0], lat.base[1] = int(lattice_cells[0]), int(lattice_cells[1])
+    lat.ratio, lat.vmax = 1, int(vmax)
+    _check(lib().mdlg_collision(ctypes.byref(lat), _ptr(field_prev), _ptr(field_cur), _ptr(xi),
+                                _ptr(dmass), _ptr(dmom), _stream_handle(stream)), "mdlg_collision")

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/mdlg.h"
@@ -34,6 +35,8 @@ struct mdlg_ctx {
     float2 *vel[2]{};
     int32_t *pid[2]{};
     uint32_t *lprev[2][kMaxLags]{};
+    float2 *mprev[2][kMaxLags]{};  // mean-square displacement origins (params.msd)
+    double *msd_acc = nullptr;     // nlags x 2
     int pos_cur = 0, meta_cur = 0;
     int32_t *cell_start = nullptr;
     // scratch
@@ -44,6 +47,12 @@ struct mdlg_ctx {
     Control *ctl = nullptr;
     unsigned long long *counts = nullptr;   // nlags x q1
     uint32_t *site_n = nullptr, *site_counts = nullptr;
+    // collision operator (MDLG_SITES_XI): the field before the latest one and Xi
+    uint32_t *site_counts_alt = nullptr;
+    int32_t *xi = nullptr, *dmass = nullptr, *dmom = nullptr;
+    // moving lattice: per-step shift in units of g 2^-24 per axis
+    int64_t shift_m[2]{};
+    bool moving = false;
     float2 *vsync = nullptr, *fsync = nullptr;
     double *xbuf = nullptr, *vbuf = nullptr, *fbuf = nullptr;
     uint32_t *nbr = nullptr;      // Verlet list (cap x n)
@@ -179,8 +188,13 @@ int validate(const mdlg_params *p) {
     if (p->nlags < 1 || p->nlags > MDLG_MAX_LAGS) return MDLG_EINVAL;
     for (int l = 0; l < p->nlags; ++l)
         if (p->lag_steps[l] < 1) return MDLG_EINVAL;
-    if (p->site_mode & ~(MDLG_SITES_FIELD | MDLG_SITES_ACCUM)) return MDLG_EINVAL;
-    if (p->site_mode == (MDLG_SITES_FIELD | MDLG_SITES_ACCUM)) return MDLG_EINVAL;
+    if (p->site_mode & ~(MDLG_SITES_FIELD | MDLG_SITES_ACCUM | MDLG_SITES_XI)) return MDLG_EINVAL;
+    if ((p->site_mode & MDLG_SITES_FIELD) && (p->site_mode & MDLG_SITES_ACCUM)) return MDLG_EINVAL;
+    if ((p->site_mode & MDLG_SITES_XI) && !(p->site_mode & MDLG_SITES_FIELD)) return MDLG_EINVAL;
+    if (p->msd != 0 && p->msd != 1) return MDLG_EINVAL;
+    for (int a = 0; a < 2; ++a)   // per-step shift below 2^16 base cells
+        if (!std::isfinite(p->lattice_u[a]) || std::fabs(p->lattice_u[a] * p->dt) >= 65536.0 * p->grid)
+            return MDLG_EINVAL;
     if (p->sort_every < 0 || p->stats_every < 0) return MDLG_EINVAL;
     int64_t ratio = exact_ratio(p->dx, p->grid);
     if (ratio < 1) return MDLG_EINVAL;
@@ -274,6 +288,23 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
     }
     b.site_n = c->site_n;
     b.site_counts = c->site_counts;
+    if (c->moving) {
+        // S(step) = step * m modulo the box (lg 2^24 units per axis), split into
+        // whole base cells K and the fraction b = frac 2^-24
+        b.shift.on = 1;
+        for (int a = 0; a < 2; ++a) {
+            const __int128 M = (__int128)c->geo.lg[a] << 24;
+            __int128 r = ((__int128)c->step * c->shift_m[a]) % M;
+            if (r < 0) r += M;
+            const int64_t rr = (int64_t)r;
+            b.shift.K[a] = (int32_t)(rr >> 24);
+            b.shift.omb[a] = (float)(16777216 - (rr & 0xffffff)) * (1.0f / 16777216.0f);
+        }
+    }
+    if (c->p.msd) {
+        for (int l = 0; l < c->p.nlags; ++l) b.mprev[l] = c->mprev[c->meta_cur][l];
+        b.msd_acc = c->msd_acc;
+    }
     return b;
 }
 
@@ -302,6 +333,10 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
     for (int l = 0; l < c->p.nlags; ++l) {
         s.lprev_in[l] = c->lprev[mi][l];
         s.lprev_out[l] = c->lprev[mi ^ 1][l];
+        if (c->p.msd) {
+            s.mprev_in[l] = c->mprev[mi][l];
+            s.mprev_out[l] = c->mprev[mi ^ 1][l];
+        }
     }
     s.cell_start = c->cell_start;
     s.key = c->key;
@@ -407,7 +442,10 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     int64_t ntot = params->n;
     if (nsys > 0) {
         if (!ns || !boxes || nsys > 65535) return MDLG_EINVAL;
-        if (params->site_mode) return MDLG_EINVAL;   // per-site outputs: single systems only
+        // per-site outputs, the moving lattice and the displacement sums: single systems only
+        if (params->site_mode || params->msd || params->lattice_u[0] != 0.0 ||
+            params->lattice_u[1] != 0.0)
+            return MDLG_EINVAL;
         ntot = 0;
         for (int32_t k = 0; k < nsys; ++k) {
             mdlg_params q = *params;
@@ -475,6 +513,9 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     if (c->ncells > (int64_t)4096 * 4096) return early(MDLG_EINVAL);
     c->ratio_shift = log2_exact(g.ratio);
     c->q1 = (2 * p.vmax + 1) * (2 * p.vmax + 1) + 1;
+    for (int a = 0; a < 2; ++a) c->shift_m[a] = std::llround(p.lattice_u[a] * p.dt / p.grid * 16777216.0);
+    c->moving = c->shift_m[0] != 0 || c->shift_m[1] != 0;
+    if (c->moving) c->graph_failed = true;   // the shift of each binning is a launch argument
     c->rc = (float)p.rcut;
     // rounding slack of one drift update: a few ulps of the largest offset
     c->round_margin = (float)(4.0 * std::ldexp(1.0, -23) * (2.0 * g.k * p.grid));
@@ -510,9 +551,12 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N)) ||
             (rc = alloc_n(c, &c->vel[b], N)) || (rc = alloc_n(c, &c->pid[b], N)))
             return fail(rc);
-        for (int l = 0; l < p.nlags; ++l)
+        for (int l = 0; l < p.nlags; ++l) {
             if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
+            if (p.msd && (rc = alloc_n(c, &c->mprev[b][l], N))) return fail(rc);
+        }
     }
+    if (p.msd && (rc = alloc_n(c, &c->msd_acc, (size_t)2 * p.nlags))) return fail(rc);
     const int64_t nb = sort_scratch_blocks(c->ncells);
     if ((rc = alloc_n(c, &c->cell_start, (size_t)c->ncells + 1)) ||
         (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
@@ -534,6 +578,11 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     if (p.site_mode) {
         const size_t sites = (size_t)g.lat[0] * g.lat[1];
         if ((rc = alloc_n(c, &c->site_n, sites)) || (rc = alloc_n(c, &c->site_counts, sites * c->q1)))
+            return fail(rc);
+        if ((p.site_mode & MDLG_SITES_XI) &&
+            ((rc = alloc_n(c, &c->site_counts_alt, sites * c->q1)) ||
+             (rc = alloc_n(c, &c->xi, sites * (c->q1 - 1))) || (rc = alloc_n(c, &c->dmass, sites)) ||
+             (rc = alloc_n(c, &c->dmom, 2 * sites))))
             return fail(rc);
     }
     if (p.potential != MDLG_POT_NONE) {
@@ -561,7 +610,15 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         if ((rc = chk(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, s))) ||
             (rc = chk(cudaMemsetAsync(c->site_counts, 0, sizeof(uint32_t) * sites * c->q1, s))))
             return fail(rc);
+        if (c->site_counts_alt &&
+            ((rc = chk(cudaMemsetAsync(c->site_counts_alt, 0, sizeof(uint32_t) * sites * c->q1, s))) ||
+             (rc = chk(cudaMemsetAsync(c->xi, 0, sizeof(int32_t) * sites * (c->q1 - 1), s))) ||
+             (rc = chk(cudaMemsetAsync(c->dmass, 0, sizeof(int32_t) * sites, s))) ||
+             (rc = chk(cudaMemsetAsync(c->dmom, 0, sizeof(int32_t) * 2 * sites, s)))))
+            return fail(rc);
     }
+    if (p.msd && (rc = chk(cudaMemsetAsync(c->msd_acc, 0, sizeof(double) * 2 * p.nlags, s))))
+        return fail(rc);
     if (nsys > 0) {
         std::vector<uint16_t> cs(N / kChunk);
         for (int32_t k = 0; k < nsys; ++k) {
@@ -674,6 +731,10 @@ int step_loop(mdlg_ctx *c, int64_t nsteps, bool launch) {
         for (int l = 0; l < p.nlags; ++l)
             if (c->step % p.lag_steps[l] == 0) mask |= 1u << l;
         if (mask) {
+            // the collision operator keeps the previous interval's field: the
+            // older buffer becomes the one this interval writes
+            const bool xi = (mask & 1u) && (p.site_mode & MDLG_SITES_XI);
+            if (xi) std::swap(c->site_counts, c->site_counts_alt);
             if (launch) {
                 if ((mask & 1u) && (p.site_mode & MDLG_SITES_FIELD)) {
                     const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
@@ -683,8 +744,20 @@ int step_loop(mdlg_ctx *c, int64_t nsteps, bool launch) {
                 }
                 StateBinArgs b = bin_args(c, mask);
                 if (!(mask & 1u)) { b.site_n = nullptr; b.site_counts = nullptr; }
-                ProfScope ps(c, MDLG_PROF_BIN, 1);
+                ProfScope ps(c, MDLG_PROF_BIN, xi ? 2 : 1);
                 MDLG_TRY(cuda_err(launch_bin_state(b, c->stream)));
+                if (xi) {
+                    CollArgs ca{};
+                    ca.lat[0] = c->geo.lat[0];
+                    ca.lat[1] = c->geo.lat[1];
+                    ca.vmax = p.vmax;
+                    ca.prev = c->site_counts_alt;
+                    ca.cur = c->site_counts;
+                    ca.xi = c->xi;
+                    ca.dmass = c->dmass;
+                    ca.dmom = c->dmom;
+                    MDLG_TRY(cuda_err(launch_collision(ca, c->stream)));
+                }
             }
             for (int l = 0; l < p.nlags; ++l)
                 if ((mask >> l) & 1u) c->intervals[l] += 1;
@@ -719,6 +792,7 @@ void drop_graph(mdlg_ctx *c) {
 int capture_and_launch(mdlg_ctx *c) {
     const int64_t s0 = c->step;
     const int pc = c->pos_cur, mc = c->meta_cur;
+    const uint32_t *sc = c->site_counts;
     int64_t before[MDLG_PROF_KINDS];
     for (int k = 0; k < MDLG_PROF_KINDS; ++k) before[k] = c->launches[k];
     const bool prof = c->prof;
@@ -736,7 +810,7 @@ int capture_and_launch(mdlg_ctx *c) {
     MDLG_TRY(rc);
     MDLG_TRY(cuda_err(ec));
     c->graph = g;
-    if (c->pos_cur != pc || c->meta_cur != mc) {   // cannot be replayed in place
+    if (c->pos_cur != pc || c->meta_cur != mc || c->site_counts != sc) {   // cannot be replayed in place
         c->graph_failed = true;
         cudaGraphExec_t once = nullptr;
         MDLG_TRY(cuda_err(cudaGraphInstantiate(&once, g, 0)));
@@ -827,6 +901,19 @@ int stats_impl(mdlg_ctx *c, int32_t k, mdlg_stats_out *out, uint64_t *counts, do
     out->pressure = (st[0] + 0.5 * st[2]) / area;
     for (int l = 0; l < p.nlags; ++l) out->intervals[l] = c->intervals[l];
     out->status = status;
+    for (int a = 0; a < 2; ++a)
+        out->lattice_u[a] = (double)c->shift_m[a] * p.grid * (1.0 / 16777216.0) / p.dt;
+    if (p.msd) {
+        double h[2 * kMaxLags];
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(h, c->msd_acc, sizeof(double) * 2 * p.nlags,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+        MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+        for (int l = 0; l < p.nlags; ++l)
+            for (int a = 0; a < 2; ++a) {
+                const double denom = (double)n * (double)c->intervals[l];
+                out->msd[l][a] = denom > 0 ? h[2 * l + a] / denom : 0.0;
+            }
+    }
     if (counts || fi) {
         const int32_t nsb = c->nsys > 0 ? c->nsys : 1;
         std::vector<unsigned long long> h((size_t)nsb * p.nlags * c->q1);
@@ -897,6 +984,21 @@ int mdlg_get_sites(mdlg_ctx *c, uint32_t *site_counts, uint32_t *ncell) {
     return cuda_err(cudaStreamSynchronize(c->stream));
 }
 
+int mdlg_get_collision(mdlg_ctx *c, int32_t *xi, int32_t *dmass, int32_t *dmom) {
+    if (!c || !(c->p.site_mode & MDLG_SITES_XI) || c->intervals[0] < 2) return MDLG_EINVAL;
+    const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+    if (xi)
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(xi, c->xi, sizeof(int32_t) * sites * (c->q1 - 1),
+                                          cudaMemcpyDeviceToHost, c->stream)));
+    if (dmass)
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(dmass, c->dmass, sizeof(int32_t) * sites,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+    if (dmom)
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(dmom, c->dmom, sizeof(int32_t) * 2 * sites,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+    return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
 int mdlg_reset_counts(mdlg_ctx *c) {
     if (!c) return MDLG_EINVAL;
     const size_t nsb = c->nsys > 0 ? (size_t)c->nsys : 1;
@@ -906,7 +1008,12 @@ int mdlg_reset_counts(mdlg_ctx *c) {
         const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
         MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_n, 0, sizeof(uint32_t) * sites, c->stream)));
         MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts, 0, sizeof(uint32_t) * sites * c->q1, c->stream)));
+        if (c->site_counts_alt)
+            MDLG_TRY(cuda_err(cudaMemsetAsync(c->site_counts_alt, 0, sizeof(uint32_t) * sites * c->q1,
+                                              c->stream)));
     }
+    if (c->msd_acc)
+        MDLG_TRY(cuda_err(cudaMemsetAsync(c->msd_acc, 0, sizeof(double) * 2 * c->p.nlags, c->stream)));
     for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = 0;
     return MDLG_OK;
 }
@@ -1227,9 +1334,29 @@ int mdlg_bin(const mdlg_lattice *lat, int64_t n, const int32_t *idx_prev, const 
                                          field, static_cast<cudaStream_t>(stream)));
 }
 
+int mdlg_collision(const mdlg_lattice *lat, const uint32_t *field_prev,
+                   const uint32_t *field_cur, int32_t *xi, int32_t *dmass, int32_t *dmom,
+                   void *stream) {
+    if (!lat || !field_prev || !field_cur) return MDLG_EINVAL;
+    if (lat->ratio < 1 || lat->vmax < 1 || lat->vmax > MDLG_MAX_VMAX) return MDLG_EINVAL;
+    CollArgs ca{};
+    for (int a = 0; a < 2; ++a) {
+        if (lat->base[a] < 1 || lat->base[a] % lat->ratio) return MDLG_EINVAL;
+        ca.lat[a] = lat->base[a] / lat->ratio;
+    }
+    ca.vmax = lat->vmax;
+    ca.prev = field_prev;
+    ca.cur = field_cur;
+    ca.xi = xi;
+    ca.dmass = dmass;
+    ca.dmom = dmom;
+    if (!xi && !dmass && !dmom) return MDLG_OK;
+    return cuda_err(launch_collision(ca, static_cast<cudaStream_t>(stream)));
+}
+
 int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t ncombo,
-                      const float *dxs, const float *dts, int32_t vmax, uint64_t *counts,
-                      void *stream) {
+                      const float *dxs, const float *dts, const float *us, int32_t vmax,
+                      uint64_t *counts, void *stream) {
     if (n < 0 || !counts || !dxs || !dts) return MDLG_EINVAL;
     if (ncombo < 1 || ncombo > MDLG_MAX_COMBOS || vmax < 1 || vmax > MDLG_MAX_VMAX) return MDLG_EINVAL;
     if (n > 0 && (!pos || !vel)) return MDLG_EINVAL;
@@ -1242,7 +1369,13 @@ int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t nco
         ga.dt[k] = dts[k];
         ga.pow2[k] = is_pow2((double)dxs[k]) ? 1 : 0;
         ga.inv_dx[k] = ga.pow2[k] ? (float)(1.0 / (double)dxs[k]) : 0.f;
+        if (us) {
+            if (!std::isfinite(us[2 * k]) || !std::isfinite(us[2 * k + 1])) return MDLG_EINVAL;
+            ga.ux[k] = us[2 * k];
+            ga.uy[k] = us[2 * k + 1];
+        }
     }
+    ga.boost = us ? 1 : 0;
     if (n == 0) return MDLG_OK;
     return cuda_err(launch_idealgas_bin(ga, n, pos, vel, reinterpret_cast<unsigned long long *>(counts),
                                         static_cast<cudaStream_t>(stream)));

@@ -62,7 +62,8 @@ __global__ void k_bin_snapshots(LatticeArgs la, int64_t n, const int2 *__restric
 
 // Non-interacting gas: stream each particle for every (dx, dt) pair and bin
 // its start and end point.  Cell decisions in binary32 with explicit rounding
-// (no contraction into FMA): x' = fl(x + fl(v dt)), cell = ceil(fl(x / dx)) - 1.
+// (no contraction into FMA): x' = fl(x + fl(v dt)), cell = ceil(fl(x / dx)) - 1,
+// with v boosted first, v = fl(v + U), when the pair has a lattice drift U.
 // Multiplying by 1/dx equals dividing by dx when dx is a power of two.
 __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restrict__ pos,
                                const float2 *__restrict__ vel, unsigned long long *counts) {
@@ -93,8 +94,10 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
                 c0y = __float2int_ru(qy) - 1;
                 last_dx = dx;
             }
-            const float xn = __fadd_rn(p.x, __fmul_rn(v.x, dt));
-            const float yn = __fadd_rn(p.y, __fmul_rn(v.y, dt));
+            const float vx_ = ga.boost ? __fadd_rn(v.x, ga.ux[k]) : v.x;
+            const float vy_ = ga.boost ? __fadd_rn(v.y, ga.uy[k]) : v.y;
+            const float xn = __fadd_rn(p.x, __fmul_rn(vx_, dt));
+            const float yn = __fadd_rn(p.y, __fmul_rn(vy_, dt));
             const float qx = pow2 ? __fmul_rn(xn, inv) : __fdiv_rn(xn, dx);
             const float qy = pow2 ? __fmul_rn(yn, inv) : __fdiv_rn(yn, dx);
             const int32_t vx = __float2int_ru(qx) - 1 - c0x;
@@ -106,34 +109,71 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
     for (int k = 0; k < ga.ncombo; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)k * q1);
 }
 
+// Sum v over the block into out (added to, FP64); every thread calls it.
+__device__ void block_sum_add(float v, float *red, double *out) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) atomicAdd(out, (double)t);
+    }
+    __syncthreads();
+}
+
+// Base cell of one axis of a state particle, on the lattice at rest or moved.
+__device__ __forceinline__ int32_t state_base(const Geom &geo, const LatticeShift &sh, int a,
+                                              int32_t origin, float cl) {
+    return sh.on ? base_cell_moving(origin, cl, geo.inv_g, geo.lg[a], sh.K[a], sh.omb[a])
+                 : base_cell(origin, cl, geo.inv_g, geo.lg[a]);
+}
+
 // Binning of the simulation state (sorted by MD cell) for the lags in `mask`:
 // the lattice cell now versus the one stored at the lag's previous binning,
-// which is then replaced.  Lag 0 may also write per-site outputs.  Every load
-// of an iteration is issued before any of its stores (a store followed by a
-// load the compiler cannot prove independent stalls the thread), and the lag
-// loop is unrolled over the compile-time maximum, predicated by the mask.
+// which is then replaced.  Lag 0 may also write per-site outputs; with
+// msd_acc set every binned lag also adds the squared displacement since its
+// previous binning.  Every load of an iteration is issued before any of its
+// stores (a store followed by a load the compiler cannot prove independent
+// stalls the thread), and the lag loop is unrolled over the compile-time
+// maximum, predicated by the mask.
+template <bool MSD, bool MOVE>
 __global__ void k_bin_state(StateBinArgs sa) {
     extern __shared__ uint32_t sh[];
+    __shared__ float red[32];
     const Geom &geo = sa.geo;
     const int w = 2 * geo.vmax + 1, q1 = w * w + 1;
     const int center = geo.vmax * w + geo.vmax;
+    constexpr bool msd = MSD;
     for (int b = threadIdx.x; b < q1 * kMaxLags; b += blockDim.x) sh[b] = 0;
     __syncthreads();
+    float m2[kMaxLags][2];
+#pragma unroll
+    for (int l = 0; l < kMaxLags; ++l) m2[l][0] = m2[l][1] = 0.0f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < sa.n; base += stride) {
         const int64_t j = base + threadIdx.x;
         const bool act = j < sa.n;
         uint32_t before[kMaxLags];
+        float2 mp[kMaxLags];
 #pragma unroll
-        for (int l = 0; l < kMaxLags; ++l)
-            before[l] = (act && ((sa.mask >> l) & 1u)) ? sa.lprev[l][j] : 0u;
+        for (int l = 0; l < kMaxLags; ++l) {
+            const bool on = act && ((sa.mask >> l) & 1u);
+            before[l] = on ? sa.lprev[l][j] : 0u;
+            mp[l] = (on && msd) ? sa.mprev[l][j] : make_float2(0.f, 0.f);
+        }
         int32_t lx = 0, ly = 0;
+        float2 p = make_float2(0.f, 0.f);
         if (act) {
             const uint32_t c = sa.cell[j];
-            const float2 p = sa.cl[j];
+            p = sa.cl[j];
             const int32_t ccx = (int32_t)(c & 0xffffu), ccy = (int32_t)(c >> 16);
-            const int32_t bx = base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
-            const int32_t by = base_cell(ccy * geo.k, p.y, geo.inv_g, geo.lg[1]);
+            const int32_t bx =
+                MOVE ? base_cell_moving(ccx * geo.k, p.x, geo.inv_g, geo.lg[0], sa.shift.K[0], sa.shift.omb[0])
+                     : base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
+            const int32_t by =
+                MOVE ? base_cell_moving(ccy * geo.k, p.y, geo.inv_g, geo.lg[1], sa.shift.K[1], sa.shift.omb[1])
+                     : base_cell(ccy * geo.k, p.y, geo.inv_g, geo.lg[1]);
             lx = lattice_of_base(bx, geo.ratio, sa.ratio_shift);
             ly = lattice_of_base(by, geo.ratio, sa.ratio_shift);
         }
@@ -147,6 +187,12 @@ __global__ void k_bin_state(StateBinArgs sa) {
                 const int32_t vy = lattice_disp(ly - (int32_t)(before[l] >> 16), geo.lat[1]);
                 bin = vel_index(vx, vy, geo.vmax);
                 sa.lprev[l][j] = now;
+                if (msd) {
+                    const float ddx = p.x - mp[l].x, ddy = p.y - mp[l].y;
+                    m2[l][0] += ddx * ddx;
+                    m2[l][1] += ddy * ddy;
+                    sa.mprev[l][j] = p;
+                }
                 if (l == 0 && sa.site_n) {
                     const int64_t site = (int64_t)ly * geo.lat[0] + lx;
                     atomicAdd(&sa.site_n[site], 1u);
@@ -160,6 +206,14 @@ __global__ void k_bin_state(StateBinArgs sa) {
 #pragma unroll
     for (int l = 0; l < kMaxLags; ++l)
         if ((sa.mask >> l) & 1u) flush_hist(sh + l * q1, q1, sa.counts[l]);
+    if (msd) {
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            if ((sa.mask >> l) & 1u) {
+                block_sum_add(m2[l][0], red, sa.msd_acc + 2 * l);
+                block_sum_add(m2[l][1], red, sa.msd_acc + 2 * l + 1);
+            }
+    }
 }
 
 // Batched systems: one chunk (one system) per block iteration, so the block's
@@ -222,12 +276,55 @@ __global__ void k_bin_seed(StateBinArgs sa) {
         const Geom &geo = sv.geo;
         const float2 p = sa.cl[j];
         const int32_t ccx = (int32_t)(c & 0xffffu), ccy = (int32_t)(c >> 16);
-        const int32_t bx = base_cell(ccx * geo.k, p.x, geo.inv_g, geo.lg[0]);
-        const int32_t by = base_cell(ccy * geo.k, p.y, geo.inv_g, geo.lg[1]);
+        const int32_t bx = state_base(geo, sa.shift, 0, ccx * geo.k, p.x);
+        const int32_t by = state_base(geo, sa.shift, 1, ccy * geo.k, p.y);
         const uint32_t now = pack_cell(lattice_of_base(bx, geo.ratio, sa.ratio_shift),
                                        lattice_of_base(by, geo.ratio, sa.ratio_shift));
         for (int l = 0; l < sa.nlags; ++l)
-            if ((sa.mask >> l) & 1u) sa.lprev[l][j] = now;
+            if ((sa.mask >> l) & 1u) {
+                sa.lprev[l][j] = now;
+                if (sa.msd_acc) sa.mprev[l][j] = p;
+            }
+    }
+}
+
+// Collision operator of Eq. Xi, one warp per lattice site: lane i reads
+// n_i(x, t) at the site and n_i(x + v_i, t + dt) at the velocity's destination
+// (the destinations of one site are 2V+1 rows of (2V+1) neighbouring sites;
+// consecutive sites share them, so the gathers hit in L2).  Writes of Xi are
+// coalesced per site; the mass and momentum sums are warp reductions.
+__global__ void k_collision(CollArgs ca) {
+    const int w = 2 * ca.vmax + 1, q = w * w, q1 = q + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t sites = (int64_t)ca.lat[0] * ca.lat[1];
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < sites; s += nwarp) {
+        const int32_t sx = (int32_t)(s % ca.lat[0]), sy = (int32_t)(s / ca.lat[0]);
+        int32_t m = 0, jx = 0, jy = 0;
+        for (int i = lane; i < q; i += 32) {
+            const int32_t vx = i % w - ca.vmax, vy = i / w - ca.vmax;
+            int32_t tx = (sx + vx) % ca.lat[0], ty = (sy + vy) % ca.lat[1];
+            tx += tx < 0 ? ca.lat[0] : 0;
+            ty += ty < 0 ? ca.lat[1] : 0;
+            const int64_t dest = (int64_t)ty * ca.lat[0] + tx;
+            const int32_t x = (int32_t)(ca.cur[dest * q1 + i] - ca.prev[s * q1 + i]);
+            if (ca.xi) ca.xi[s * q + i] = x;
+            m += x;
+            jx += vx * x;
+            jy += vy * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_down_sync(0xffffffffu, m, o);
+            jx += __shfl_down_sync(0xffffffffu, jx, o);
+            jy += __shfl_down_sync(0xffffffffu, jy, o);
+        }
+        if (lane == 0) {
+            if (ca.dmass) ca.dmass[s] = m;
+            if (ca.dmom) {
+                ca.dmom[2 * s] = jx;
+                ca.dmom[2 * s + 1] = jy;
+            }
+        }
     }
 }
 
@@ -282,12 +379,27 @@ cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int threads = 256;
+    const bool msd = sa.msd_acc != nullptr, move = sa.shift.on != 0;
+    void (*kern)(StateBinArgs) = msd ? (move ? k_bin_state<true, true> : k_bin_state<true, false>)
+                                     : (move ? k_bin_state<false, true> : k_bin_state<false, false>);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_bin_state,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_bin_state<<<hist_grid(sa.n, threads), threads, smem, s>>>(sa);
+    kern<<<hist_grid(sa.n, threads), threads, smem, s>>>(sa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collision(const CollArgs &ca, cudaStream_t s) {
+    const int threads = 256;
+    const int64_t sites = (int64_t)ca.lat[0] * ca.lat[1];
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (sites * 32 + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * 8;
+    const int grid = (int)(need < cap ? need : cap);
+    k_collision<<<grid < 1 ? 1 : grid, threads, 0, s>>>(ca);
     return cudaGetLastError();
 }
 

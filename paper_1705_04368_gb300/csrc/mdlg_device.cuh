@@ -7,6 +7,9 @@
 //   pid[j]   int32   original particle number
 //   lprev[l][j] uint32 lattice cell of the particle at the last binning of
 //            lag l, packed (c_y << 16) | c_x
+//   mprev[l][j] float2 (mean-square displacement only) the particle's offset at
+//            the last binning of lag l, re-expressed against its current MD
+//            cell's origin at every re-sort, so cl - mprev is the displacement
 // A cell's origin is an integer number of base cells g (g a power of two), so
 // every position is "integer + binary32 offset": the base cell of a particle,
 // and therefore its lattice cell, is exact integer arithmetic, and pair
@@ -57,6 +60,26 @@ __device__ __forceinline__ int32_t base_cell(int32_t origin, float cl, float inv
     const float t = fminf(fmaxf(ceilf(cl * inv_g), -lim + 1.0f), lim);
     int32_t b = origin + (int32_t)t - 1;
     b += b < 0 ? lg : 0;
+    b -= b >= lg ? lg : 0;
+    return b;
+}
+
+// Base cell of origin + cl + S on a lattice displaced by S = (K + b) g, K in
+// [0, lg), b in [0, 1) a multiple of 2^-24 (omb = 1 - b, exact).  With a = cl/g
+// (exact), k = floor(a) and f = a - k (exact), ceil(a + b) = k + j where
+// j = 0 if f = b = 0, 2 if f > 1 - b, else 1: every decision is an exact
+// comparison, so the cell of the real number x + S is found without rounding.
+__device__ __forceinline__ int32_t base_cell_moving(int32_t origin, float cl, float inv_g,
+                                                    int32_t lg, int32_t K, float omb) {
+    const float a = cl * inv_g;
+    const float k = floorf(a);
+    const float f = a - k;
+    const float j = (f == 0.0f && omb == 1.0f) ? 0.0f : (f > omb ? 2.0f : 1.0f);
+    const float lim = (float)lg;
+    const float t = fminf(fmaxf(k + j, -lim + 1.0f), lim + 1.0f);
+    int32_t b = origin + K + (int32_t)t - 1;     // in [-lg, 3 lg)
+    b += b < 0 ? lg : 0;
+    b -= b >= lg ? lg : 0;
     b -= b >= lg ? lg : 0;
     return b;
 }

@@ -76,6 +76,16 @@ struct IdealGasArgs {
     int32_t vmax;
     float dx[16], dt[16], inv_dx[16];
     int32_t pow2[16];
+    int32_t boost;             // 1: velocities boosted by (ux[k], uy[k]) per pair
+    float ux[16], uy[16];
+};
+
+// Lattice displacement S = (K + b) g per axis of a moving lattice, K in [0, lg),
+// b in [0, 1) a multiple of 2^-24, passed as 1 - b (exact in binary32).
+struct LatticeShift {
+    int32_t on;
+    int32_t K[2];
+    float omb[2];
 };
 
 struct StateBinArgs {
@@ -91,6 +101,19 @@ struct StateBinArgs {
     uint32_t *site_n;       // lag 0 per-site N(x,t), or null
     uint32_t *site_counts;  // lag 0 per-site n_i(x,t), or null
     Batch batch;            // batched: counts[l] point at system 0, system s at + s*nlags*q1
+    LatticeShift shift;     // moving lattice (single systems)
+    float2 *mprev[kMaxLags];  // per lag: offset at its previous binning, against the
+                              // particle's current MD cell (mean-square displacement), or null
+    double *msd_acc;        // nlags x 2 sums of squared displacements (added to)
+};
+
+struct CollArgs {
+    int32_t lat[2];
+    int32_t vmax;
+    const uint32_t *prev, *cur;   // C_y*C_x*(Q+1) occupation fields
+    int32_t *xi;                  // C_y*C_x*Q, or null
+    int32_t *dmass;               // C_y*C_x, or null
+    int32_t *dmom;                // C_y*C_x*2, or null
 };
 
 int hist_grid(int64_t n, int threads);
@@ -101,6 +124,7 @@ cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *
                                 const float *vel, unsigned long long *counts, cudaStream_t s);
 cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s);
 cudaError_t launch_bin_seed(const StateBinArgs &sa, cudaStream_t s);
+cudaError_t launch_collision(const CollArgs &ca, cudaStream_t s);
 
 // ---- molecular dynamics ------------------------------------------------------
 // Device control block of one context (one allocation).
@@ -166,6 +190,8 @@ struct SortArgs {
     float2 *v_out;
     int32_t *pid_out;
     uint32_t *lprev_out[kMaxLags];
+    const float2 *mprev_in[kMaxLags];   // mean-square displacement origins, or null
+    float2 *mprev_out[kMaxLags];
     int32_t *cell_start;     // ncells + 1
     // scratch
     uint32_t *key;           // n, packed new cell

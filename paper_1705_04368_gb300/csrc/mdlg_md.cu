@@ -476,17 +476,23 @@ __global__ void k_sort_scatter(SortArgs a) {
         const float2 vv = a.v_in[from];
         const int32_t pid = a.pid_in[from];
         uint32_t lp[kMaxLags];
+        float2 mp[kMaxLags];
+        const bool msd = a.mprev_in[0] != nullptr;
 #pragma unroll
-        for (int l = 0; l < kMaxLags; ++l) lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
+        for (int l = 0; l < kMaxLags; ++l) {
+            lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
+            mp[l] = (msd && l < a.nlags) ? a.mprev_in[l][from] : make_float2(0.f, 0.f);
+        }
         const int64_t c = key_cell<B>(sv, cw);
         const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
         int32_t rank = 0;
         for (int32_t u = s; u < e; ++u) rank += (uint32_t)(a.entry[u] >> 32) < my_pid;
         const int32_t to = s + rank;
         float2 pn = p;
+        float sx = 0.f, sy = 0.f;
         if (!B || cw != kGhostCell) {
-            const float sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
-            const float sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
+            sx = (float)wrap_half((cell_x(ow) - cell_x(cw)) * geo.k, geo.lg[0]) * geo.g;
+            sy = (float)wrap_half((cell_y(ow) - cell_y(cw)) * geo.k, geo.lg[1]) * geo.g;
             pn = make_float2(p.x + sx, p.y + sy);
         }
         a.cl_out[to] = pn;
@@ -495,7 +501,10 @@ __global__ void k_sort_scatter(SortArgs a) {
         a.cell_out[to] = cw;
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l)
-            if (l < a.nlags) a.lprev_out[l][to] = lp[l];
+            if (l < a.nlags) {
+                a.lprev_out[l][to] = lp[l];
+                if (msd) a.mprev_out[l][to] = make_float2(mp[l].x + sx, mp[l].y + sy);
+            }
     }
 }
 

@@ -33,9 +33,13 @@ def test_strerror_names_every_code():
 
 
 def _params(**kw):
+    raw = {k: kw.pop(k) for k in ("msd",) if k in kw}     # set on the C struct unchecked
     base = dict(n=16, box=16.0, dx=4.0, grid=0.5, lag_steps=(5,))
     base.update(kw)
-    return m.Params(**base).to_c()
+    p = m.Params(**base).to_c()
+    for k, v in raw.items():
+        setattr(p, k, v)
+    return p
 
 
 BAD = [
@@ -43,6 +47,8 @@ BAD = [
     dict(vmax=0), dict(vmax=16), dict(lag_steps=()), dict(lag_steps=(0,)), dict(dt=0.0),
     dict(rcut=9.0), dict(box=8.0, dx=4.0), dict(potential=7), dict(site_mode=3),
     dict(skin=-1.0), dict(sort_every=-2), dict(mass=0.0),
+    dict(site_mode=4), dict(site_mode=6), dict(msd=2), dict(lattice_u=(float("nan"), 0.0)),
+    dict(lattice_u=(0.0, 1e9)),
 ]
 
 
@@ -105,11 +111,39 @@ def test_context_free_entry_points_validate():
     assert L.mdlg_bin(ctypes.byref(lat), 4, buf, buf, None, None, None, None) == -1
     assert L.mdlg_bin(ctypes.byref(lat), 0, None, None, buf, None, None, None) == 0  # empty: no-op
     d = np.array([1.0], np.float32)
-    assert L.mdlg_idealgas_bin(4, buf, buf, 0, d.ctypes.data, d.ctypes.data, 3, buf, None) == -1
-    assert L.mdlg_idealgas_bin(4, buf, buf, 1, d.ctypes.data, d.ctypes.data, 16, buf, None) == -1
+    assert L.mdlg_idealgas_bin(4, buf, buf, 0, d.ctypes.data, d.ctypes.data, None, 3, buf, None) == -1
+    assert L.mdlg_idealgas_bin(4, buf, buf, 1, d.ctypes.data, d.ctypes.data, None, 16, buf, None) == -1
     z = np.array([0.0], np.float32)
-    assert L.mdlg_idealgas_bin(4, buf, buf, 1, z.ctypes.data, d.ctypes.data, 3, buf, None) == -1
-    assert L.mdlg_idealgas_bin(0, None, None, 1, d.ctypes.data, d.ctypes.data, 3, buf, None) == 0
+    assert L.mdlg_idealgas_bin(4, buf, buf, 1, z.ctypes.data, d.ctypes.data, None, 3, buf, None) == -1
+    assert L.mdlg_idealgas_bin(0, None, None, 1, d.ctypes.data, d.ctypes.data, None, 3, buf, None) == 0
+    nan = np.array([np.nan, 0.0], np.float32)
+    assert L.mdlg_idealgas_bin(4, buf, buf, 1, d.ctypes.data, d.ctypes.data, nan.ctypes.data, 3, buf,
+                               None) == -1
+    # collision operator: lattice and fields are checked before any launch
+    assert L.mdlg_collision(ctypes.byref(lat), None, buf, buf, None, None, None) == -1
+    lat.base[0] = 0
+    assert L.mdlg_collision(ctypes.byref(lat), buf, buf, buf, None, None, None) == -1
+    lat.base[0], lat.vmax = 16, 16
+    assert L.mdlg_collision(ctypes.byref(lat), buf, buf, buf, None, None, None) == -1
+    lat.vmax = 3
+    assert L.mdlg_collision(ctypes.byref(lat), buf, buf, None, None, None, None) == 0  # nothing asked
+
+
+def test_batch_rejects_single_system_analyses():
+    # the moving lattice, displacement sums and per-site outputs are single-system only
+    x = np.full((32, 2), 1.0)
+    ns = np.array([16, 16], np.int64)
+    boxes = np.array([[16.0, 16.0], [16.0, 16.0]])
+    for kw in (dict(msd=1), dict(lattice_u=(0.5, 0.0)), dict(site_mode=1)):
+        p = _params(**kw)
+        h = ctypes.c_void_p()
+        rc = m.lib().mdlg_create_batch(ctypes.byref(p), 2, ns.ctypes.data, boxes.ctypes.data,
+                                       x.ctypes.data, x.ctypes.data, None, None, ctypes.byref(h))
+        assert rc == -1 and not h.value, kw
+
+
+def test_get_collision_rejects_null_context():
+    assert m.lib().mdlg_get_collision(None, None, None, None) == -1
 
 
 def test_adjoint_rejects_null_context():

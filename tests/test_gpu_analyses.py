@@ -1,0 +1,284 @@
+"""GPU parity of the paper analyses against the FP64 oracle: the moving lattice
+(Sec. IV), the MDLG collision operator Xi_i (Eq. Xi) and the per-lag
+mean-square displacement (Sec. IV-A).
+
+Tolerances: every count, Xi value and per-site sum bit-exact on identical
+snapshots; the mean-square displacement within 1e-4 relative (per-particle
+displacements are binary32 differences of offsets, against exact FP64
+differences in the oracle)."""
+import math
+
+import numpy as np
+import pytest
+
+import mdlg_inputs as mi
+import oracle
+import paper_1705_04368_gb300 as m
+
+pytestmark = pytest.mark.gpu
+
+V = 3
+W = 2 * V + 1
+Q = W * W
+Q1 = Q + 1
+
+
+def _llround(x):
+    return int(math.copysign(math.floor(abs(x) + 0.5), x))
+
+
+def _shifts(U, dt, g, L):
+    """S(n) of the library's moving lattice: n * round(U dt / g * 2^24) in units
+    of g 2^-24, reduced modulo the box, as exact FP64 values."""
+    ms = [_llround(U[a] * dt / g * 2.0 ** 24) for a in (0, 1)]
+    M = [int(round(L[a] / g)) << 24 for a in (0, 1)]
+
+    def S(step):
+        return np.array([((step * ms[a]) % M[a]) * g * 2.0 ** -24 for a in (0, 1)])
+    return S, ms
+
+
+def _dyadic_free_flight(n, L, seed):
+    rng = np.random.default_rng(seed)
+    x = mi.dyadic_positions(n, L, seed, bits=12, boundary_frac=0.05)
+    v = np.round(rng.normal(0.0, 2.0, size=(n, 2)) * 1024) / 1024
+    return x, v
+
+
+def _trajectory(x0, v0, L, dt, steps):
+    traj = [x0]
+    xx = x0
+    for _ in range(steps):
+        xx = oracle.free_stream(xx, v0, (L, L), dt, 1)
+        traj.append(xx)
+    return traj
+
+
+# ---- moving lattice ----------------------------------------------------------
+
+@pytest.mark.parametrize("U,lags,sort_every,site_mode", [
+    ((0.37, -0.21), (4, 7), 3, m.SITES_ACCUM),
+    ((-1.9, 2.6), (1, 5, 16), 2, m.SITES_FIELD),
+    ((0.5 / 0.125, 0.0), (3,), 4, m.SITES_ACCUM),     # exactly one base cell per step
+])
+def test_moving_lattice_free_flight_bit_exact(cuda, U, lags, sort_every, site_mode):
+    n, L, dt, g, dx, steps = 20000, 64.0, 0.125, 0.5, 4.0, 48
+    x0, v0 = _dyadic_free_flight(n, L, seed=77)
+    p = m.Params(n=n, box=L, dx=dx, dt=dt, grid=g, potential=m.POT_NONE, lag_steps=lags,
+                 sort_every=sort_every, vmax=V, site_mode=site_mode, lattice_u=U)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(steps)
+        st, counts, _ = s.stats()
+        sites, ncell = s.get_sites()
+    S, ms = _shifts(U, dt, g, (L, L))
+    assert st["lattice_u"] == pytest.approx(tuple(ms[a] * g * 2.0 ** -24 / dt for a in (0, 1)),
+                                            rel=0, abs=1e-15)
+    C = (int(L / dx),) * 2
+    traj = _trajectory(x0, v0, L, dt, steps)
+    ref = np.zeros((len(lags), Q1), np.uint64)
+    ref_sites = np.zeros((C[0] * C[1], Q1), np.uint32)
+    ref_n = np.zeros(C[0] * C[1], np.uint32)
+    for li, lag in enumerate(lags):
+        for t in range(lag, steps + 1, lag):
+            last = t + lag > steps
+            keep = li == 0 and (site_mode == m.SITES_ACCUM or last)
+            oracle.mdlg_bin(traj[t - lag], traj[t], dx, C, V, counts=ref[li],
+                            ncell=ref_n if keep else None, fld=ref_sites if keep else None,
+                            field=keep, shift_prev=S(t - lag), shift_cur=S(t))
+    assert np.array_equal(counts, ref)
+    assert np.array_equal(sites, ref_sites)
+    assert np.array_equal(ncell, ref_n)
+    # the moving lattice changes the counts (the test is not vacuous)
+    plain = np.zeros(Q1, np.uint64)
+    for t in range(lags[0], steps + 1, lags[0]):
+        oracle.mdlg_bin(traj[t - lags[0]], traj[t], dx, C, V, counts=plain)
+    assert not np.array_equal(plain, ref[0])
+
+
+def test_moving_lattice_lj_gas_bit_exact(cuda):
+    # Lennard-Jones gas: the snapshots are the library's own (get_state), the
+    # oracle bins them at x + S(t) in FP64
+    n, L = 20000, mi.box_for(20000, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=13)
+    U, lags, steps, dt, g = (0.83, 0.41), (3, 5), 30, 0.005, 0.5
+    p = m.Params(n=n, box=L, dx=4.0, dt=dt, grid=g, lag_steps=lags, vmax=V, lattice_u=U,
+                 sort_every=4)
+    traj = []
+    with m.Simulation(p, x0, v0) as s:
+        traj.append(s.get_state()[0])
+        for _ in range(steps):
+            s.step(1)
+            traj.append(s.get_state()[0])
+        st, counts, _ = s.stats()
+    assert st["status"] == 0
+    S, _ = _shifts(U, dt, g, (L, L))
+    C = (int(round(L / 4.0)),) * 2
+    ref = np.zeros((len(lags), Q1), np.uint64)
+    for li, lag in enumerate(lags):
+        for t in range(lag, steps + 1, lag):
+            oracle.mdlg_bin(traj[t - lag], traj[t], 4.0, C, V, counts=ref[li],
+                            shift_prev=S(t - lag), shift_cur=S(t))
+    assert np.array_equal(counts, ref)
+
+
+def test_moving_lattice_ignores_graph_request(cuda):
+    # use_graphs with a moving lattice launches directly; the results equal a
+    # run without graphs
+    n, L, dt = 5000, 64.0, 0.125
+    x0, v0 = _dyadic_free_flight(n, L, seed=78)
+    out = []
+    for graphs in (False, True):
+        p = m.Params(n=n, box=L, dx=4.0, dt=dt, potential=m.POT_NONE, lag_steps=(4,), sort_every=2,
+                     vmax=V, lattice_u=(0.3, 0.1), use_graphs=graphs)
+        with m.Simulation(p, x0, v0) as s:
+            s.step(40)
+            out.append(s.stats()[1])
+    assert np.array_equal(out[0], out[1])
+
+
+def test_idealgas_boost_bit_exact(cuda):
+    import torch
+    pos, vel = mi.idealgas_state(300_001, 512.0, 1.0, seed=15)
+    combos = [(2.0, 1.0), (1.0, 0.5), (4.0, 2.0), (3.0, 0.7)]       # last: division path
+    us = np.array([[0.4, 0.0], [-0.3, 0.2], [1.1, -0.9], [0.05, 0.05]], np.float32)
+    p = torch.from_numpy(pos).to(cuda)
+    v = torch.from_numpy(vel).to(cuda)
+    counts = torch.zeros((len(combos), Q1), dtype=torch.int64, device=cuda)
+    m.idealgas_bin(p, v, combos, V, counts, us=us)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().view(np.uint64)
+    ref = oracle.stream_bin_f32(pos, vel, [c[0] for c in combos], [c[1] for c in combos], V, us=us)
+    assert np.array_equal(got, ref)
+
+
+# ---- collision operator --------------------------------------------------------
+
+@pytest.mark.parametrize("cells,vmax,hi", [
+    ((5, 3), 3, 7),          # lattice smaller than the window: destinations wrap twice
+    ((64, 48), 3, 40),
+    ((37, 41), 15, 5),       # largest window, ragged site count
+    ((1, 1), 1, 3),
+])
+def test_collision_entry_point_bit_exact(cuda, cells, vmax, hi):
+    import torch
+    rng = np.random.default_rng(cells[0] * 100 + vmax)
+    q1 = (2 * vmax + 1) ** 2 + 1
+    sites = cells[0] * cells[1]
+    fp = rng.integers(0, hi, size=(sites, q1)).astype(np.uint32)
+    fc = rng.integers(0, hi, size=(sites, q1)).astype(np.uint32)
+    tp = torch.from_numpy(fp.view(np.int32)).to(cuda)
+    tc = torch.from_numpy(fc.view(np.int32)).to(cuda)
+    xi = torch.full((sites, q1 - 1), 12345, dtype=torch.int32, device=cuda)
+    dm = torch.zeros(sites, dtype=torch.int32, device=cuda)
+    dj = torch.zeros((sites, 2), dtype=torch.int32, device=cuda)
+    m.collision(cells, vmax, tp, tc, xi, dm, dj)
+    torch.cuda.synchronize()
+    ref = oracle.collision(cells, vmax, fp, fc)
+    vel = oracle.velocity_table(vmax)
+    assert np.array_equal(xi.cpu().numpy(), ref)
+    assert np.array_equal(dm.cpu().numpy(), ref.sum(axis=1))
+    assert np.array_equal(dj.cpu().numpy(), ref @ vel)
+
+
+def test_collision_field_of_the_simulation(cuda):
+    # site_mode FIELD | XI: after every lag-0 interval the library forms
+    # Xi_i(x) from the last two fields; compare with the oracle on the
+    # oracle's own fields of the same (exact) trajectory
+    n, L, dt, dx, lag = 20000, 64.0, 0.125, 4.0, 4
+    x0, v0 = _dyadic_free_flight(n, L, seed=79)
+    p = m.Params(n=n, box=L, dx=dx, dt=dt, potential=m.POT_NONE, lag_steps=(lag, 6), sort_every=3,
+                 vmax=V, site_mode=m.SITES_FIELD | m.SITES_XI)
+    C = (int(L / dx),) * 2
+    traj = _trajectory(x0, v0, L, dt, 5 * lag)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(lag)
+        with pytest.raises(m.MdlgError):
+            s.get_collision()                  # one interval: no collision yet
+        for k in (2, 3, 5):
+            s.step(k * lag - s.stats()[0]["step"])
+            xi, dm, dj = s.get_collision()
+            sites, ncell = s.get_sites()
+            t = k * lag
+            f_prev = oracle.mdlg_bin(traj[t - 2 * lag], traj[t - lag], dx, C, V, field=True)[2]
+            f_cur = oracle.mdlg_bin(traj[t - lag], traj[t], dx, C, V, field=True)[2]
+            ref = oracle.collision(C, V, f_prev, f_cur)
+            assert np.array_equal(sites, f_cur)
+            assert np.array_equal(xi, ref)
+            assert np.array_equal(dm, ref.sum(axis=1))
+            assert np.array_equal(dj, ref @ oracle.velocity_table(V))
+            overflow = f_prev[:, Q].sum() + f_cur[:, Q].sum()
+            if overflow == 0:
+                assert not dm.any()            # Eq. masscons
+        s.reset_counts()
+        with pytest.raises(m.MdlgError):
+            s.get_collision()
+
+
+def test_collision_mass_conservation_lj(cuda):
+    # Lennard-Jones gas at a short lag: no move leaves the window, so the mass
+    # sum of Xi vanishes at every site (Eq. masscons) while the momentum sum
+    # does not (Sec. III)
+    n, L = 50000, mi.box_for(50000, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=17)
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=(20,), vmax=V,
+                 site_mode=m.SITES_FIELD | m.SITES_XI, use_graphs=True, sort_every=5)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(200)
+        st, counts, _ = s.stats()
+        xi, dm, dj = s.get_collision()
+    assert st["status"] == 0 and counts[0, Q] == 0
+    assert not dm.any()
+    assert np.abs(dj).sum() > 0
+
+
+def test_collision_graph_replay_equals_direct(cuda):
+    n, L, dt = 5000, 64.0, 0.125
+    x0, v0 = _dyadic_free_flight(n, L, seed=80)
+    out = []
+    for graphs in (False, True):
+        p = m.Params(n=n, box=L, dx=4.0, dt=dt, potential=m.POT_NONE, lag_steps=(3,), sort_every=2,
+                     vmax=V, site_mode=m.SITES_FIELD | m.SITES_XI, use_graphs=graphs)
+        with m.Simulation(p, x0, v0) as s:
+            s.step(12 * 3 + 9)      # graph period 12: capture, two replays, then direct
+            out.append(s.get_collision())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+# ---- mean-square displacement ---------------------------------------------------
+
+def test_msd_matches_oracle_lj(cuda):
+    n, L = 20000, mi.box_for(20000, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=19)
+    lags, steps = (1, 4, 10), 40
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=lags, vmax=V, msd=True, sort_every=3)
+    traj = []
+    with m.Simulation(p, x0, v0) as s:
+        traj.append(s.get_state()[0])
+        for _ in range(steps):
+            s.step(1)
+            traj.append(s.get_state()[0])
+        st, _, _ = s.stats()
+    for li, lag in enumerate(lags):
+        ref = np.mean([oracle.msd(traj[t - lag], traj[t], (L, L))
+                       for t in range(lag, steps + 1, lag)], axis=0)
+        assert np.allclose(st["msd"][li], ref, rtol=1e-4, atol=0), (lag, st["msd"][li], ref)
+
+
+def test_msd_free_flight_exact_value(cuda):
+    # dyadic free flight: every displacement over a lag is lag dt v exactly
+    n, L, dt = 30000, 64.0, 0.125
+    x0, v0 = _dyadic_free_flight(n, L, seed=81)
+    lags = (2, 5)
+    p = m.Params(n=n, box=L, dx=4.0, dt=dt, potential=m.POT_NONE, lag_steps=lags, sort_every=3,
+                 vmax=V, msd=True)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(20)
+        st, _, _ = s.stats()
+        s.reset_counts()
+        s.step(10)
+        st2, _, _ = s.stats()
+    for li, lag in enumerate(lags):
+        want = ((v0 * lag * dt) ** 2).mean(axis=0)
+        assert np.allclose(st["msd"][li], want, rtol=1e-6, atol=0)
+        assert np.allclose(st2["msd"][li], want, rtol=1e-6, atol=0)   # after a reset

@@ -37,6 +37,8 @@ METRIC = "MD+MDLG particle-steps/s on 1 GB300 (% FP32/HBM roofline); batched & a
 UNIT = "particle-steps/s"
 STEP_BYTES_PER_PARTICLE = 36      # read cell 4 + cl 8 + v 8, write cl 8 + v 8
 IDEALGAS_BYTES_PER_PARTICLE = 16  # x, y, vx, vy binary32
+COLLISION_BYTES_PER_SITE_Q = 12   # read n_i at x and at x + v_i, write Xi_i: 3 x 4 B per velocity
+COLLISION_BYTES_PER_SITE = 12     # dmass + dmom int32
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -260,6 +262,13 @@ def run_ours(args, rank, world, local_rank):
     # adjoint (N = 16 384, rho = 0.3, K = 200, checkpoints every 20) versus the plain forward
     adjoint = _adjoint(m, torch, stream, local_rank) if rank == 0 else None
 
+    # paper analyses: collision-operator kernel alone, and the production run
+    # with the moving lattice, Xi field and mean-square displacement switched on
+    analyses = _analyses(m, torch, dev, stream, local_rank, params, c, x0, v0, hbm_gbs, value / world) \
+        if rank == 0 else None
+    if analyses:
+        analyses["production_with_analyses"]["plain_bin_ms_per_200_steps"] = prof["bin"][0] / args.steps
+
     # end to end through the C ABI: pinned host state in, f_i out, every step
     e2e = _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev)
 
@@ -268,7 +277,8 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(c, world), "roofline": roofline,
             "gpu_launches": launches, "kernels": kernels, "clocks": clk, "e2e": e2e,
-            "idealgas": ig, "batched": batched, "adjoint": adjoint, "status": st["status"],
+            "idealgas": ig, "batched": batched, "adjoint": adjoint, "analyses": analyses,
+            "status": st["status"],
             "tuned": {"grid": params.grid, "skin": params.skin,
                       "cell_width": params.grid * math.ceil((params.rcut + params.skin) / params.grid - 1e-12),
                       "cached": tune_report["cached"]}}
@@ -387,6 +397,63 @@ def _adjoint(m, torch, stream, local_rank, reps=3):
                     "recompute, reverse sweep, soft loss) vs mdlg_step(200) + mdlg_stats"}
 
 
+def _analyses(m, torch, dev, stream, local_rank, params, c, x0, v0, hbm_gbs, plain_value, reps=20):
+    """(1) mdlg_collision on the production lattice (935 x 935 sites, V = 3) with
+    random fields, algorithmic bytes 12 Q + 12 per site; (2) the production run
+    (200 MD steps per step) with lattice drift U = (0.3, 0.1), the Xi field of
+    lag 0 and the mean-square displacement of every lag, against the plain run."""
+    import dataclasses
+    C = (int(round(c.box / c.dx)),) * 2
+    q = 49
+    sites = C[0] * C[1]
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    with torch.cuda.stream(stream):
+        fields = [torch.randint(0, 20, (sites, q + 1), generator=g, device=dev, dtype=torch.int32)
+                  for _ in range(3)]
+        xi = torch.empty((sites, q), dtype=torch.int32, device=dev)
+        dm = torch.empty(sites, dtype=torch.int32, device=dev)
+        dj = torch.empty((sites, 2), dtype=torch.int32, device=dev)
+    for k in range(3):
+        m.collision(C, 3, fields[k % 3], fields[(k + 1) % 3], xi, dm, dj, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(reps):
+        m.collision(C, 3, fields[k % 3], fields[(k + 1) % 3], xi, dm, dj, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_coll = e0.elapsed_time(e1) / 1e3 / reps
+    coll_bytes = sites * (COLLISION_BYTES_PER_SITE_Q * q + COLLISION_BYTES_PER_SITE)
+    del fields, xi, dm, dj
+
+    p = dataclasses.replace(params, lattice_u=(0.3, 0.1), msd=True,
+                            site_mode=m.SITES_FIELD | m.SITES_XI)
+    with m.Simulation(p, x0, v0, stream=stream, device=local_rank) as s:
+        s.step(MD_STEPS_PER_STEP)
+        torch.cuda.synchronize()
+        s.profile(True)
+        e0.record(stream)
+        for _ in range(3):
+            s.step(MD_STEPS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = s.profile(False)
+        st, _, _ = s.stats()
+    t_run = e0.elapsed_time(e1) / 1e3
+    on_value = c.n * 3 * MD_STEPS_PER_STEP / t_run
+    return {"collision": {"workload": f"lattice_{C[0]}x{C[1]}_V3", "us_per_launch": t_coll * 1e6,
+                          "algorithmic_bytes": coll_bytes,
+                          "achieved_gbs": coll_bytes / t_coll / 1e9,
+                          "frac_hbm": coll_bytes / t_coll / 1e9 / hbm_gbs},
+            "production_with_analyses": {
+                "lattice_u": st["lattice_u"], "msd_lag0": st["msd"][0], "status": st["status"],
+                "particle_steps_per_s": on_value, "plain_particle_steps_per_s": plain_value,
+                "overhead": plain_value / on_value - 1.0,
+                "bin_ms_per_200_steps": prof["bin"][0] / 3, "bin_launches": prof["bin"][1],
+                "what": "moving lattice + SITES_FIELD|SITES_XI + msd, graphs off (both arms)"}}
+
+
 def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev):
     x_pin = torch.empty((c.n, 2), dtype=torch.float64, pin_memory=True)
     v_pin = torch.empty((c.n, 2), dtype=torch.float64, pin_memory=True)
@@ -440,6 +507,25 @@ def run_ncu_target(md_steps):
     torch.cuda.synchronize()
 
 
+def run_ncu_collision(launches):
+    """profiling target: the collision operator on the production lattice
+    (935 x 935 sites, V = 3, random fields), `launches` launches."""
+    import torch
+    import paper_1705_04368_gb300 as m
+    dev = torch.device("cuda", 0)
+    C = (935, 935)
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    f = [torch.randint(0, 20, (C[0] * C[1], 50), generator=g, device=dev, dtype=torch.int32)
+         for _ in range(2)]
+    xi = torch.empty((C[0] * C[1], 49), dtype=torch.int32, device=dev)
+    dm = torch.empty(C[0] * C[1], dtype=torch.int32, device=dev)
+    dj = torch.empty((C[0] * C[1], 2), dtype=torch.int32, device=dev)
+    for k in range(launches):
+        m.collision(C, 3, f[k % 2], f[(k + 1) % 2], xi, dm, dj)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,7 +535,13 @@ def main():
     ap.add_argument("--ncu-target", type=int, default=0, metavar="MD_STEPS",
                     help="profiling target: build the production system, run MD_STEPS MD "
                          "steps (sorts and binning included) and one ideal-gas pass, exit")
+    ap.add_argument("--ncu-collision", type=int, default=0, metavar="LAUNCHES",
+                    help="profiling target: LAUNCHES collision-operator launches on the "
+                         "production lattice, exit")
     args = ap.parse_args()
+    if args.ncu_collision:
+        run_ncu_collision(args.ncu_collision)
+        return
     if args.ncu_target:
         run_ncu_target(args.ncu_target)
         return

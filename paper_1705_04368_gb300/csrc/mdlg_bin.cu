@@ -288,44 +288,128 @@ __global__ void k_bin_seed(StateBinArgs sa) {
     }
 }
 
-// Collision operator of Eq. Xi, one warp per lattice site: lane i reads
-// n_i(x, t) at the site and n_i(x + v_i, t + dt) at the velocity's destination
-// (the destinations of one site are 2V+1 rows of (2V+1) neighbouring sites;
-// consecutive sites share them, so the gathers hit in L2).  Writes of Xi are
-// coalesced per site; the mass and momentum sums are warp reductions.
-__global__ void k_collision(CollArgs ca) {
-    const int w = 2 * ca.vmax + 1, q = w * w, q1 = q + 1;
-    const int lane = threadIdx.x & 31;
-    const int64_t sites = (int64_t)ca.lat[0] * ca.lat[1];
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < sites; s += nwarp) {
-        const int32_t sx = (int32_t)(s % ca.lat[0]), sy = (int32_t)(s / ca.lat[0]);
-        int32_t m = 0, jx = 0, jy = 0;
-        for (int i = lane; i < q; i += 32) {
-            const int32_t vx = i % w - ca.vmax, vy = i / w - ca.vmax;
-            int32_t tx = (sx + vx) % ca.lat[0], ty = (sy + vy) % ca.lat[1];
-            tx += tx < 0 ? ca.lat[0] : 0;
-            ty += ty < 0 ? ca.lat[1] : 0;
-            const int64_t dest = (int64_t)ty * ca.lat[0] + tx;
-            const int32_t x = (int32_t)(ca.cur[dest * q1 + i] - ca.prev[s * q1 + i]);
-            if (ca.xi) ca.xi[s * q + i] = x;
-            m += x;
-            jx += vx * x;
-            jy += vy * x;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            m += __shfl_down_sync(0xffffffffu, m, o);
-            jx += __shfl_down_sync(0xffffffffu, jx, o);
-            jy += __shfl_down_sync(0xffffffffu, jy, o);
-        }
-        if (lane == 0) {
-            if (ca.dmass) ca.dmass[s] = m;
-            if (ca.dmom) {
-                ca.dmom[2 * s] = jx;
-                ca.dmom[2 * s + 1] = jy;
+// Collision operator of Eq. Xi.  One block per tile of `ts` consecutive sites
+// of one lattice row y.  The tile's records of n_i(x, t) are contiguous in the
+// site-major field, so they are read once, coalesced, negated into shared
+// memory.  For each velocity row v_y the needed n_i(x + v_i, t + dt) are the
+// 2V+1 entries of that row group in the sites (x0 - V .. x0 + ts - 1 + V) of
+// row y + v_y: entry k of site lx serves the tile site lx - k, a one-to-one
+// map, so it is added into shared memory without atomics.  Xi leaves as one
+// contiguous block of ts * Q int32, and one warp per site forms the mass and
+// momentum sums from shared memory.  V is a template parameter so that every
+// index division is by a constant.
+__device__ __forceinline__ int32_t wrap_into(int32_t v, int32_t c) {
+    while (v < 0) v += c;      // at most (V + ts) / c + 1 passes
+    while (v >= c) v -= c;
+    return v;
+}
+
+constexpr int kCollBatch = 8;
+
+template <int V>
+__global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
+    extern __shared__ int32_t xs[];                    // ts x Q
+    constexpr int w = 2 * V + 1, q = w * w, q1 = q + 1;
+    const int32_t cx = ca.lat[0], cy = ca.lat[1];
+    const int32_t tiles_x = (cx + ts - 1) / ts;
+    const int64_t ntiles = (int64_t)tiles_x * cy;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int32_t y = (int32_t)(tile / tiles_x);
+        const int32_t x0 = (int32_t)(tile - (int64_t)y * tiles_x) * ts;
+        const int32_t nx = min(ts, cx - x0);
+        const int64_t s0 = (int64_t)y * cx + x0;
+        // -n_i(x, t) of the tile (its nx records are contiguous); eight loads
+        // in flight per thread before any shared-memory write
+        const uint32_t *pv = ca.prev + s0 * q1;
+        const int tot1 = nx * q1;
+        for (int r0 = threadIdx.x; r0 < tot1; r0 += kCollBatch * 256) {
+            uint32_t v[kCollBatch];
+#pragma unroll
+            for (int u = 0; u < kCollBatch; ++u) {
+                const int r = r0 + u * 256;
+                v[u] = r < tot1 ? pv[r] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kCollBatch; ++u) {
+                const int r = r0 + u * 256;
+                const int ls = r / q1, i = r - ls * q1;
+                if (r < tot1 && i < q) xs[ls * q + i] = -(int32_t)v[u];
             }
         }
+        __syncthreads();
+        // + n_i(x + v_i, t + dt): element e = (lx q + row w + k) is entry k of
+        // velocity row `row` (v_y = row - V) of site x0 - V + lx in lattice row
+        // y + v_y; it serves tile site ls = lx - k
+        const int tot2 = (nx + 2 * V) * q;
+        for (int e0 = threadIdx.x; e0 < tot2; e0 += kCollBatch * 256) {
+            uint32_t v[kCollBatch];
+            int dst[kCollBatch];
+#pragma unroll
+            for (int u = 0; u < kCollBatch; ++u) {
+                const int e = e0 + u * 256;
+                const int lx = e / q, rem = e - lx * q;
+                const int row = rem / w, k = rem - row * w;
+                const int ls = lx - k;
+                const bool ok = e < tot2 && ls >= 0 && ls < nx;
+                dst[u] = ok ? ls * q + rem : -1;
+                v[u] = 0u;
+                if (ok) {
+                    const int32_t ty = wrap_into(y + row - V, cy);
+                    const int32_t tx = wrap_into(x0 - V + lx, cx);
+                    v[u] = ca.cur[((int64_t)ty * cx + tx) * q1 + rem];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kCollBatch; ++u)
+                if (dst[u] >= 0) xs[dst[u]] += (int32_t)v[u];
+        }
+        __syncthreads();
+        if (ca.xi) {
+            int32_t *xo = ca.xi + s0 * q;
+            for (int r = threadIdx.x; r < nx * q; r += blockDim.x) xo[r] = xs[r];
+        }
+        if (ca.dmass || ca.dmom) {
+            const int lane = threadIdx.x & 31;
+            for (int ls = threadIdx.x >> 5; ls < nx; ls += blockDim.x >> 5) {
+                int32_t m = 0, jx = 0, jy = 0;
+#pragma unroll
+                for (int i0 = 0; i0 < q; i0 += 32) {
+                    const int i = i0 + lane;
+                    if (i < q) {
+                        const int32_t x = xs[ls * q + i];
+                        m += x;
+                        jx += (i % w - V) * x;
+                        jy += (i / w - V) * x;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    m += __shfl_down_sync(0xffffffffu, m, o);
+                    jx += __shfl_down_sync(0xffffffffu, jx, o);
+                    jy += __shfl_down_sync(0xffffffffu, jy, o);
+                }
+                if (lane == 0) {
+                    if (ca.dmass) ca.dmass[s0 + ls] = m;
+                    if (ca.dmom) {
+                        ca.dmom[2 * (s0 + ls)] = jx;
+                        ca.dmom[2 * (s0 + ls) + 1] = jy;
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
+}
+
+template <int V>
+cudaError_t launch_collision_v(const CollArgs &ca, cudaStream_t s) {
+    constexpr int q = (2 * V + 1) * (2 * V + 1);
+    int32_t ts = 12288 / q;                  // tile of Xi in shared memory: <= 48 KB
+    if (ts > 64) ts = 64;
+    const int64_t ntiles = (int64_t)((ca.lat[0] + ts - 1) / ts) * ca.lat[1];
+    const int64_t cap = (int64_t)1 << 30;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    k_collision<V><<<grid < 1 ? 1 : grid, 256, (size_t)ts * q * sizeof(int32_t), s>>>(ca, ts);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -391,16 +475,24 @@ cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
 }
 
 cudaError_t launch_collision(const CollArgs &ca, cudaStream_t s) {
-    const int threads = 256;
-    const int64_t sites = (int64_t)ca.lat[0] * ca.lat[1];
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t need = (sites * 32 + threads - 1) / threads;
-    const int64_t cap = (int64_t)sms * 8;
-    const int grid = (int)(need < cap ? need : cap);
-    k_collision<<<grid < 1 ? 1 : grid, threads, 0, s>>>(ca);
-    return cudaGetLastError();
+    switch (ca.vmax) {
+        case 1: return launch_collision_v<1>(ca, s);
+        case 2: return launch_collision_v<2>(ca, s);
+        case 3: return launch_collision_v<3>(ca, s);
+        case 4: return launch_collision_v<4>(ca, s);
+        case 5: return launch_collision_v<5>(ca, s);
+        case 6: return launch_collision_v<6>(ca, s);
+        case 7: return launch_collision_v<7>(ca, s);
+        case 8: return launch_collision_v<8>(ca, s);
+        case 9: return launch_collision_v<9>(ca, s);
+        case 10: return launch_collision_v<10>(ca, s);
+        case 11: return launch_collision_v<11>(ca, s);
+        case 12: return launch_collision_v<12>(ca, s);
+        case 13: return launch_collision_v<13>(ca, s);
+        case 14: return launch_collision_v<14>(ca, s);
+        case 15: return launch_collision_v<15>(ca, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_bin_seed(const StateBinArgs &sa, cudaStream_t s) {

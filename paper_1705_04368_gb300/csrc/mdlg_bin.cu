@@ -291,20 +291,19 @@ __global__ void k_bin_seed(StateBinArgs sa) {
 // Collision operator of Eq. Xi.  One block per tile of `ts` consecutive sites
 // of one lattice row y.  The tile's records of n_i(x, t) are contiguous in the
 // site-major field, so they are read once, coalesced, negated into shared
-// memory.  For each velocity row v_y the needed n_i(x + v_i, t + dt) are the
-// 2V+1 entries of that row group in the sites (x0 - V .. x0 + ts - 1 + V) of
-// row y + v_y: entry k of site lx serves the tile site lx - k, a one-to-one
-// map, so it is added into shared memory without atomics.  Xi leaves as one
-// contiguous block of ts * Q int32, and one warp per site forms the mass and
-// momentum sums from shared memory.  V is a template parameter so that every
-// index division is by a constant.
+// memory.  The needed n_i(x + v_i, t + dt) of velocity row v_y are the 2V+1
+// entries of that row group in the sites x0 - V .. x0 + ts - 1 + V of lattice
+// row y + v_y: one thread per such (site lx, row) loads the 2V+1 contiguous
+// entries, and entry k serves tile site lx - k (a one-to-one map, so it is
+// added into shared memory without atomics; neighbouring lanes hit words 2V+1
+// apart, an odd stride, so the banks differ).  Xi leaves as one contiguous
+// block of ts * Q int32; one thread per site forms the mass and momentum sums.
+// V is a template parameter so that every index division is by a constant.
 __device__ __forceinline__ int32_t wrap_into(int32_t v, int32_t c) {
     while (v < 0) v += c;      // at most (V + ts) / c + 1 passes
     while (v >= c) v -= c;
     return v;
 }
-
-constexpr int kCollBatch = 8;
 
 template <int V>
 __global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
@@ -313,55 +312,36 @@ __global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
     const int32_t cx = ca.lat[0], cy = ca.lat[1];
     const int32_t tiles_x = (cx + ts - 1) / ts;
     const int64_t ntiles = (int64_t)tiles_x * cy;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int32_t y = (int32_t)(tile / tiles_x);
         const int32_t x0 = (int32_t)(tile - (int64_t)y * tiles_x) * ts;
         const int32_t nx = min(ts, cx - x0);
         const int64_t s0 = (int64_t)y * cx + x0;
-        // -n_i(x, t) of the tile (its nx records are contiguous); eight loads
-        // in flight per thread before any shared-memory write
+        // -n_i(x, t) of the tile (its nx records are contiguous)
         const uint32_t *pv = ca.prev + s0 * q1;
-        const int tot1 = nx * q1;
-        for (int r0 = threadIdx.x; r0 < tot1; r0 += kCollBatch * 256) {
-            uint32_t v[kCollBatch];
-#pragma unroll
-            for (int u = 0; u < kCollBatch; ++u) {
-                const int r = r0 + u * 256;
-                v[u] = r < tot1 ? pv[r] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < kCollBatch; ++u) {
-                const int r = r0 + u * 256;
-                const int ls = r / q1, i = r - ls * q1;
-                if (r < tot1 && i < q) xs[ls * q + i] = -(int32_t)v[u];
-            }
+        for (int r = threadIdx.x; r < nx * q1; r += blockDim.x) {
+            const int ls = r / q1, i = r - ls * q1;
+            if (i < q) xs[ls * q + i] = -(int32_t)pv[r];
         }
         __syncthreads();
-        // + n_i(x + v_i, t + dt): element e = (lx q + row w + k) is entry k of
-        // velocity row `row` (v_y = row - V) of site x0 - V + lx in lattice row
-        // y + v_y; it serves tile site ls = lx - k
-        const int tot2 = (nx + 2 * V) * q;
-        for (int e0 = threadIdx.x; e0 < tot2; e0 += kCollBatch * 256) {
-            uint32_t v[kCollBatch];
-            int dst[kCollBatch];
+        // + n_i(x + v_i, t + dt): warp per velocity row, lane per halo site
+        const int nl = nx + 2 * V;
+        for (int row = warp; row < w; row += nwarp) {
+            const int32_t ty = wrap_into(y + row - V, cy);
+            const uint32_t *base = ca.cur + (int64_t)ty * cx * q1 + row * w;
+            for (int lx = lane; lx < nl; lx += 32) {
+                const int32_t tx = wrap_into(x0 - V + lx, cx);
+                const uint32_t *src = base + (int64_t)tx * q1;
+                uint32_t v[w];
 #pragma unroll
-            for (int u = 0; u < kCollBatch; ++u) {
-                const int e = e0 + u * 256;
-                const int lx = e / q, rem = e - lx * q;
-                const int row = rem / w, k = rem - row * w;
-                const int ls = lx - k;
-                const bool ok = e < tot2 && ls >= 0 && ls < nx;
-                dst[u] = ok ? ls * q + rem : -1;
-                v[u] = 0u;
-                if (ok) {
-                    const int32_t ty = wrap_into(y + row - V, cy);
-                    const int32_t tx = wrap_into(x0 - V + lx, cx);
-                    v[u] = ca.cur[((int64_t)ty * cx + tx) * q1 + rem];
+                for (int k = 0; k < w; ++k) v[k] = src[k];
+#pragma unroll
+                for (int k = 0; k < w; ++k) {
+                    const int ls = lx - k;
+                    if (ls >= 0 && ls < nx) xs[ls * q + row * w + k] += (int32_t)v[k];
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kCollBatch; ++u)
-                if (dst[u] >= 0) xs[dst[u]] += (int32_t)v[u];
         }
         __syncthreads();
         if (ca.xi) {
@@ -369,30 +349,24 @@ __global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
             for (int r = threadIdx.x; r < nx * q; r += blockDim.x) xo[r] = xs[r];
         }
         if (ca.dmass || ca.dmom) {
-            const int lane = threadIdx.x & 31;
-            for (int ls = threadIdx.x >> 5; ls < nx; ls += blockDim.x >> 5) {
+            for (int ls = threadIdx.x; ls < nx; ls += blockDim.x) {
                 int32_t m = 0, jx = 0, jy = 0;
 #pragma unroll
-                for (int i0 = 0; i0 < q; i0 += 32) {
-                    const int i = i0 + lane;
-                    if (i < q) {
-                        const int32_t x = xs[ls * q + i];
-                        m += x;
-                        jx += (i % w - V) * x;
-                        jy += (i / w - V) * x;
+                for (int row = 0; row < w; ++row) {
+                    int32_t rs = 0;
+#pragma unroll
+                    for (int k = 0; k < w; ++k) {
+                        const int32_t x = xs[ls * q + row * w + k];
+                        rs += x;
+                        jx += (k - V) * x;
                     }
+                    m += rs;
+                    jy += (row - V) * rs;
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    m += __shfl_down_sync(0xffffffffu, m, o);
-                    jx += __shfl_down_sync(0xffffffffu, jx, o);
-                    jy += __shfl_down_sync(0xffffffffu, jy, o);
-                }
-                if (lane == 0) {
-                    if (ca.dmass) ca.dmass[s0 + ls] = m;
-                    if (ca.dmom) {
-                        ca.dmom[2 * (s0 + ls)] = jx;
-                        ca.dmom[2 * (s0 + ls) + 1] = jy;
-                    }
+                if (ca.dmass) ca.dmass[s0 + ls] = m;
+                if (ca.dmom) {
+                    ca.dmom[2 * (s0 + ls)] = jx;
+                    ca.dmom[2 * (s0 + ls) + 1] = jy;
                 }
             }
         }

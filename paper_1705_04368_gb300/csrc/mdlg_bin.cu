@@ -288,58 +288,114 @@ __global__ void k_bin_seed(StateBinArgs sa) {
     }
 }
 
-// Collision operator of Eq. Xi.  One block per tile of `ts` consecutive sites
-// of one lattice row y.  The tile's records of n_i(x, t) are contiguous in the
-// site-major field, so they are read once, coalesced, negated into shared
-// memory.  The needed n_i(x + v_i, t + dt) of velocity row v_y are the 2V+1
-// entries of that row group in the sites x0 - V .. x0 + ts - 1 + V of lattice
-// row y + v_y: one thread per such (site lx, row) loads the 2V+1 contiguous
-// entries, and entry k serves tile site lx - k (a one-to-one map, so it is
-// added into shared memory without atomics; neighbouring lanes hit words 2V+1
-// apart, an odd stride, so the banks differ).  Xi leaves as one contiguous
-// block of ts * Q int32; one thread per site forms the mass and momentum sums.
-// V is a template parameter so that every index division is by a constant.
+// Collision operator of Eq. Xi.  One block per tile of TS consecutive sites
+// of one lattice row y.
+//  1. The tile's records of n_i(x, t) are contiguous in the site-major field:
+//     they are read with 16-byte loads and stored negated into shared memory.
+//  2. The needed n_i(x + v_i, t + dt) of velocity row v_y are the 2V+1
+//     entries of that row group in the sites x0 - V .. x0 + TS - 1 + V of
+//     lattice row y + v_y: one warp per velocity row, one lane per halo site
+//     loads the 2V+1 contiguous entries, and entry k serves tile site lx - k
+//     (a one-to-one map: it is added into shared memory without atomics;
+//     lanes hit words Q apart, an odd stride, so the banks differ).
+//  The first velocity row's loads are issued together with step 1's, so a
+//  tile waits for memory once.  Xi leaves as one contiguous block of TS * Q
+//  int32; one thread per site forms the mass and momentum sums.  V is a
+//  template parameter, so every index division is by a constant.
 __device__ __forceinline__ int32_t wrap_into(int32_t v, int32_t c) {
-    while (v < 0) v += c;      // at most (V + ts) / c + 1 passes
+    while (v < 0) v += c;      // at most (V + TS) / c + 1 passes
     while (v >= c) v -= c;
     return v;
 }
 
 template <int V>
-__global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
-    extern __shared__ int32_t xs[];                    // ts x Q
+__host__ __device__ constexpr int coll_ts() {
+    constexpr int q = (2 * V + 1) * (2 * V + 1);
+    return 12288 / q > 64 ? 64 : 12288 / q;     // TS x Q int32 <= 48 KB
+}
+
+template <int V>
+__global__ void __launch_bounds__(256, V <= 3 ? 4 : 1) k_collision(CollArgs ca) {
     constexpr int w = 2 * V + 1, q = w * w, q1 = q + 1;
+    constexpr int TS = coll_ts<V>();
+    constexpr int NV = ((TS * q1 + 6) / 4 + 255) / 256;     // 16-byte vectors per thread
+    constexpr int NU = (TS + 2 * V + 31) / 32;               // halo sites per lane
+    __shared__ int32_t xs[TS * q];
     const int32_t cx = ca.lat[0], cy = ca.lat[1];
-    const int32_t tiles_x = (cx + ts - 1) / ts;
+    const int64_t cap = (int64_t)cx * cy * q1;                // words of a field
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(ca.prev) & 15) == 0;
+    const int32_t tiles_x = (cx + TS - 1) / TS;
     const int64_t ntiles = (int64_t)tiles_x * cy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int32_t y = (int32_t)(tile / tiles_x);
-        const int32_t x0 = (int32_t)(tile - (int64_t)y * tiles_x) * ts;
-        const int32_t nx = min(ts, cx - x0);
+        const int32_t x0 = (int32_t)(tile - (int64_t)y * tiles_x) * TS;
+        const int32_t nx = min(TS, cx - x0);
+        const int nl = nx + 2 * V;
         const int64_t s0 = (int64_t)y * cx + x0;
-        // -n_i(x, t) of the tile (its nx records are contiguous)
-        const uint32_t *pv = ca.prev + s0 * q1;
-        for (int r = threadIdx.x; r < nx * q1; r += blockDim.x) {
-            const int ls = r / q1, i = r - ls * q1;
-            if (i < q) xs[ls * q + i] = -(int32_t)pv[r];
+        // step 1 loads: words [a, e) of n_i(x, t) as 16-byte vectors from a0
+        const int64_t a = s0 * q1, e = a + (int64_t)nx * q1, a0 = a & ~(int64_t)3;
+        uint4 pv[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int64_t g = a0 + 4 * (int64_t)(threadIdx.x + u * 256);
+            pv[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (g < e) {
+                if (vec_ok && g + 4 <= cap) {
+                    pv[u] = *reinterpret_cast<const uint4 *>(ca.prev + g);
+                } else {
+                    pv[u].x = ca.prev[g];
+                    if (g + 1 < cap) pv[u].y = ca.prev[g + 1];
+                    if (g + 2 < cap) pv[u].z = ca.prev[g + 2];
+                    if (g + 3 < cap) pv[u].w = ca.prev[g + 3];
+                }
+            }
+        }
+        // step 2 loads of this warp's first velocity row
+        uint32_t cv[NU][w];
+        const uint32_t *rowbase = nullptr;
+        if (warp < w) rowbase = ca.cur + (int64_t)wrap_into(y + warp - V, cy) * cx * q1 + warp * w;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int lx = lane + 32 * u;
+            const bool on = warp < w && lx < nl;
+            const uint32_t *src = on ? rowbase + (int64_t)wrap_into(x0 - V + lx, cx) * q1 : nullptr;
+#pragma unroll
+            for (int k = 0; k < w; ++k) cv[u][k] = on ? src[k] : 0u;
+        }
+        // step 1 stores
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int64_t g = a0 + 4 * (int64_t)(threadIdx.x + u * 256);
+            const uint32_t wd[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (g + c < a || g + c >= e) continue;
+                const int r = (int)(g + c - a);
+                const int ls = r / q1, i = r - ls * q1;
+                if (i < q) xs[ls * q + i] = -(int32_t)wd[c];
+            }
         }
         __syncthreads();
-        // + n_i(x + v_i, t + dt): warp per velocity row, lane per halo site
-        const int nl = nx + 2 * V;
+        // step 2: first row from registers, further rows (V >= 4) loaded here
         for (int row = warp; row < w; row += nwarp) {
-            const int32_t ty = wrap_into(y + row - V, cy);
-            const uint32_t *base = ca.cur + (int64_t)ty * cx * q1 + row * w;
-            for (int lx = lane; lx < nl; lx += 32) {
-                const int32_t tx = wrap_into(x0 - V + lx, cx);
-                const uint32_t *src = base + (int64_t)tx * q1;
-                uint32_t v[w];
+            if (row != warp) {
+                const uint32_t *rb = ca.cur + (int64_t)wrap_into(y + row - V, cy) * cx * q1 + row * w;
 #pragma unroll
-                for (int k = 0; k < w; ++k) v[k] = src[k];
+                for (int u = 0; u < NU; ++u) {
+                    const int lx = lane + 32 * u;
+                    const uint32_t *src = lx < nl ? rb + (int64_t)wrap_into(x0 - V + lx, cx) * q1 : nullptr;
+#pragma unroll
+                    for (int k = 0; k < w; ++k) cv[u][k] = lx < nl ? src[k] : 0u;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int lx = lane + 32 * u;
 #pragma unroll
                 for (int k = 0; k < w; ++k) {
                     const int ls = lx - k;
-                    if (ls >= 0 && ls < nx) xs[ls * q + row * w + k] += (int32_t)v[k];
+                    if (lx < nl && ls >= 0 && ls < nx) xs[ls * q + row * w + k] += (int32_t)cv[u][k];
                 }
             }
         }
@@ -376,13 +432,11 @@ __global__ void __launch_bounds__(256) k_collision(CollArgs ca, int32_t ts) {
 
 template <int V>
 cudaError_t launch_collision_v(const CollArgs &ca, cudaStream_t s) {
-    constexpr int q = (2 * V + 1) * (2 * V + 1);
-    int32_t ts = 12288 / q;                  // tile of Xi in shared memory: <= 48 KB
-    if (ts > 64) ts = 64;
-    const int64_t ntiles = (int64_t)((ca.lat[0] + ts - 1) / ts) * ca.lat[1];
+    constexpr int TS = coll_ts<V>();
+    const int64_t ntiles = (int64_t)((ca.lat[0] + TS - 1) / TS) * ca.lat[1];
     const int64_t cap = (int64_t)1 << 30;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    k_collision<V><<<grid < 1 ? 1 : grid, 256, (size_t)ts * q * sizeof(int32_t), s>>>(ca, ts);
+    k_collision<V><<<grid < 1 ? 1 : grid, 256, 0, s>>>(ca);
     return cudaGetLastError();
 }
 

@@ -158,6 +158,9 @@ def test_idealgas_boost_bit_exact(cuda):
     ((64, 48), 3, 40),
     ((37, 41), 15, 5),       # largest window, ragged site count
     ((1, 1), 1, 3),
+    ((23, 9), 7, 4),         # staged kernel, narrow tiles
+    ((300, 2), 9, 3),        # largest staged window
+    ((130, 130), 10, 3),     # smallest window of the unstaged kernel
 ])
 def test_collision_entry_point_bit_exact(cuda, cells, vmax, hi):
     import torch

@@ -285,3 +285,34 @@ def test_msd_free_flight_exact_value(cuda):
         want = ((v0 * lag * dt) ** 2).mean(axis=0)
         assert np.allclose(st["msd"][li], want, rtol=1e-6, atol=0)
         assert np.allclose(st2["msd"][li], want, rtol=1e-6, atol=0)   # after a reset
+
+
+def test_moving_lattice_equilibrium_and_moments(cuda):
+    # Fig. wi_u (Sec. V): the ballistic gas seen from a lattice drifting at U has
+    # the equilibrium of Eq. feqfull at u = U dt / dx; every bin within 4
+    # standard errors, and the moments of the measured f_i (Eq. Psi) agree with
+    # those of the closed form
+    import torch
+    from paper_1705_04368_gb300 import analysis as an
+    n = mi.IDEALGAS_N
+    pos, vel = mi.idealgas_state(n, mi.IDEALGAS_BOX, 1.0, seed=23)
+    combos = [(2.0, 1.0), (4.0, 1.0), (1.0, 0.25)]
+    us = [(0.1, 0.0), (0.3, -0.2), (0.5, 0.05)]            # lattice units
+    U = np.array([[u[0] * dx / dt, u[1] * dx / dt] for (dx, dt), u in zip(combos, us)], np.float32)
+    p = torch.from_numpy(pos).to(cuda)
+    v = torch.from_numpy(vel).to(cuda)
+    counts = torch.zeros((len(combos), Q1), dtype=torch.int64, device=cuda)
+    m.idealgas_bin(p, v, combos, V, counts, us=U)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().astype(np.float64) / n
+    for k, ((dx, dt), u) in enumerate(zip(combos, us)):
+        a = math.sqrt(1.0) * dt / dx
+        ueff = (float(U[k, 0]) * dt / dx, float(U[k, 1]) * dt / dx)
+        pth = an.feq(V, a, ueff)
+        se = np.sqrt(np.maximum(pth * (1 - pth), 1e-300) / n)
+        z = np.abs(got[k] - pth) / se
+        assert np.all(z[pth > 1e-6] < 4.0), (k, z.max())
+        mg = an.moments(got[k], V, ueff, a=a)
+        mt = an.moments(pth, V, ueff, a=a)
+        assert np.allclose(mg["Psi"], mt["Psi"], rtol=5e-3, atol=5e-3), (k, mg["Psi"], mt["Psi"])
+        assert np.allclose(mg["mean"], mt["mean"], atol=2e-3)

@@ -24,8 +24,9 @@ namespace mdlg {
 
 namespace {
 
-constexpr int kStepThreads = 128;
-constexpr int kListBatch = 8;       // list entries loaded before any is used
+constexpr int kStepThreads = 256;   // one system; a batch uses one 128-slot chunk per block
+constexpr int kListBatch = 4;       // list entries loaded before any is used (lists are
+                                    // padded to a multiple of this)
 constexpr int kNlistThreads = 64;   // list-build block (entries staged in shared memory)
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -155,10 +156,15 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
 
 // Pairs from the Verlet list built at the last sort: entry t of particle i is
 // nbr[t n + i] = j | (ox + 1) << 28 | (oy + 1) << 30 with (ox, oy) the offset of
-// j's cell from i's cell.  Entries are fetched kListBatch at a time so that
-// their loads (and the dependent position loads) overlap.  For a particle whose
-// neighbouring cells are all full-width and unwrapped (REGULAR), the origin
-// shift is (code - 1) w; at the periodic edges and next to the wider last
+// j's cell from i's cell.  Each list is padded to a multiple of kListBatch with
+// entries i | 3 << 28 | 3 << 30: the particle itself two cell widths away on
+// both axes, always beyond rc (cells are wider than rc), so every load is
+// unconditional and a padding slot adds zero.  Entries are fetched kListBatch
+// at a time so that their loads (and the dependent position loads) overlap.
+// For a particle whose neighbouring cells are all full-width and unwrapped
+// (REGULAR) the origin shift is (code - 1) w, with the 2-bit code turned into
+// a float by the exponent trick (2^23 + code, minus 2^23: exact, no
+// conversion instruction); at the periodic edges and next to the wider last
 // cell it is looked up from the four per-particle shifts.
 template <bool STATS, bool REGULAR>
 __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
@@ -167,26 +173,26 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     const uint32_t *e = a.nbr + i;
     const int64_t n = a.n;
     const float w = a.cell_w;
-    for (int t0 = 0; t0 < cnt; t0 += kListBatch) {
+    const int npad = (cnt + kListBatch - 1) & ~(kListBatch - 1);
+    for (int t0 = 0; t0 < npad; t0 += kListBatch) {
         uint32_t ent[kListBatch];
 #pragma unroll
-        for (int u = 0; u < kListBatch; ++u)
-            ent[u] = (t0 + u < cnt) ? __ldg(e + (int64_t)(t0 + u) * n) : kNoEntry;
+        for (int u = 0; u < kListBatch; ++u) ent[u] = __ldg(e + (int64_t)(t0 + u) * n);
         float2 q[kListBatch];
 #pragma unroll
-        for (int u = 0; u < kListBatch; ++u)
-            q[u] = (ent[u] != kNoEntry) ? __ldg(a.cl_in + (ent[u] & 0x0fffffffu))
-                                        : make_float2(1.0e18f, 1.0e18f);
+        for (int u = 0; u < kListBatch; ++u) q[u] = __ldg(a.cl_in + (ent[u] & 0x0fffffffu));
 #pragma unroll
         for (int u = 0; u < kListBatch; ++u) {
             float sx, sy;
             if (REGULAR) {
-                sx = fmaf((float)((ent[u] >> 28) & 3u), w, -w);
-                sy = fmaf((float)(ent[u] >> 30), w, -w);
+                const float kx = __int_as_float(0x4B000000u | ((ent[u] >> 28) & 3u)) - 8388608.0f;
+                const float ky = __int_as_float(0x4B000000u | (ent[u] >> 30)) - 8388608.0f;
+                sx = fmaf(kx, w, -w);
+                sy = fmaf(ky, w, -w);
             } else {
                 const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
-                sx = ox == 0u ? sxm : (ox == 2u ? sxp : 0.0f);
-                sy = oy == 0u ? sym : (oy == 2u ? syp : 0.0f);
+                sx = ox == 0u ? sxm : (ox == 2u ? sxp : (ox == 3u ? 2.0f * w : 0.0f));
+                sy = oy == 0u ? sym : (oy == 2u ? syp : (oy == 3u ? 2.0f * w : 0.0f));
             }
             pair_term_masked<STATS>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
         }
@@ -196,7 +202,7 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
 // B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
 // per system); otherwise one system described by a.geo.
 template <int MODE, bool STATS, bool B>
-__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+__global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
     const Geom &geo = sv.geo;
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
         }
     }
 
-    constexpr int kWarps = kStepThreads / 32;
+    constexpr int kWarps = (B ? kChunk : kStepThreads) / 32;
     __shared__ long long s_red[kWarps][kStatsN];
     __shared__ float s_max[kWarps];
     __shared__ int s_last;
@@ -594,6 +600,11 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
             }
             const int keep = cnt < a.cap ? cnt : a.cap;
             for (int t = 0; t < keep; ++t) a.nbr[(int64_t)t * a.n + i] = s_ent[t * kNlistThreads + threadIdx.x];
+            // padding to a multiple of the step kernel's batch (cap is a multiple of it)
+            if (cnt <= a.cap) {
+                const int npad = (cnt + kListBatch - 1) & ~(kListBatch - 1);
+                for (int t = cnt; t < npad; ++t) a.nbr[(int64_t)t * a.n + i] = (uint32_t)i | 0xf0000000u;
+            }
             a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
         }
     }
@@ -702,7 +713,8 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 
 }  // namespace
 
-int64_t step_blocks(int64_t n) { return (n + kStepThreads - 1) / kStepThreads; }
+// Blocks of the largest step launch (a batch launches 128-thread blocks).
+int64_t step_blocks(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 template <bool B>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
@@ -717,9 +729,10 @@ void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStrea
 }
 
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
-    const int64_t blocks = step_blocks(a.n);
+    const int threads = a.batch.sys ? kChunk : kStepThreads;
+    const int64_t blocks = (a.n + threads - 1) / threads;
     if (blocks < 1) return cudaSuccess;
-    const dim3 grid((unsigned)blocks), block(kStepThreads);
+    const dim3 grid((unsigned)blocks), block(threads);
     if (a.batch.sys) launch_step_t<true>(a, mode, grid, block, s);
     else launch_step_t<false>(a, mode, grid, block, s);
     return cudaGetLastError();

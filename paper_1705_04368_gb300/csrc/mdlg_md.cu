@@ -34,7 +34,6 @@ constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 cells per scan b
 constexpr int kStatsN = 5;
 constexpr int kErrNonFinite = -5;
 constexpr int kErrOverflow = -4;
-constexpr uint32_t kNoEntry = 0xffffffffu;
 // Fixed-point scale of the exact reductions: per-particle terms are rounded to
 // multiples of 2^-24 and summed as 64-bit integers.
 constexpr float kFixScale = 16777216.0f;
@@ -346,9 +345,6 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
 // ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
 //      order inside a cell) ---------------------------------------------------
 
-__device__ __forceinline__ int32_t lin(const Geom &geo, uint32_t cw) {
-    return cell_y(cw) * geo.nc[0] + cell_x(cw);
-}
 
 template <bool B>
 __global__ void k_sort_key(SortArgs a) {

@@ -174,6 +174,13 @@ PRODUCTION_LJ = LJConfig("lj2d_n4194304_rho0.3_T1", n=4_194_304, rho=0.3, temper
 PRODUCTION_LJ_DENSE = LJConfig("lj2d_n4194304_rho0.6_T0.8", n=4_194_304, rho=0.6,
                                temperature=0.8, dx=4.0, lags=(10, 20, 50, 100, 200),
                                steps=10_000)
+# The paper's own state point (hot dilute gas): N = 100 000 in L = 1000 sigma
+# (packing fraction 0.0785), T = 50, dt = 1e-4 tau, 3e6 steps of which the first
+# 1e6 are discarded.  dx = 10 sigma here (the paper sweeps dx).
+PAPER_STATE_POINT = LJConfig("lj2d_n100000_L1000_T50", n=100_000, rho=0.1, temperature=50.0,
+                             dx=10.0, dt=1e-4, lags=(100, 300, 1000, 3000, 7000, 10000, 20000,
+                                                     50000),
+                             vmax=7, steps=3_000_000, box=1000.0)
 # Ideal gas: N = 2^22 in L = 2048, all (dx, dt) in {1,2,4} x {0.5,1,2}.
 IDEALGAS_N = 1 << 22
 IDEALGAS_BOX = 2048.0

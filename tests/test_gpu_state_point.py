@@ -1,0 +1,102 @@
+"""The paper's own state point on this engine (Sec. IV): N = 100 000 LJ particles
+in L = 1000 sigma at T = 50, dt = 1e-4 tau.  The paper ran 3e6 steps and
+discarded the first 1e6; the default here is 3e5 steps with the first 1e5
+discarded (MDLG_STATE_POINT_STEPS sets the total, the discarded third scales
+with it).  Checked against what the paper states and the closed forms:
+
+  * energy conservation of the integrator;
+  * the mean-square displacement follows Eq. vca with an exponential velocity
+    correlation of decay time tau ~ 0.5 (Fig. VD: tau = 0.5);
+  * f_i of Eq. MDni matches Eq. feqfull at a^2 = <dx^2>/dx^2 measured in the
+    same run (Fig. fi), for coarse steps from the ballistic to the diffusive
+    regime;
+  * on a lattice moving at u the measured f_i matches Eq. feqfull at u and the
+    first moment equals u (Fig. wi_u; the mean mass flow is exact, Sec. V).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import mdlg_inputs as mi
+import paper_1705_04368_gb300 as m
+from paper_1705_04368_gb300 import analysis as an
+
+pytestmark = pytest.mark.gpu
+
+C = mi.PAPER_STATE_POINT
+TOTAL = int(os.environ.get("MDLG_STATE_POINT_STEPS", "300000"))
+DISCARD = TOTAL // 3
+U_LAG = 7000            # coarse step (0.7 tau) of the moving-lattice check, a^2 ~ 1/6
+U_LATTICE = 0.1         # imposed velocity in lattice units at that step
+
+
+def _run(lattice_u):
+    x0, v0 = mi.lj_initial_state(C.n, C.box, C.temperature, seed=5)
+    p = m.Params(n=C.n, box=C.box, dx=C.dx, dt=C.dt, lag_steps=C.lags, vmax=C.vmax, msd=True,
+                 stats_every=10000, lattice_u=lattice_u)
+    with m.Simulation(p, x0, v0) as s:
+        st0, _, _ = s.stats()
+        s.step(DISCARD)
+        s.reset_counts()
+        s.step(TOTAL - DISCARD)
+        st, counts, fi = s.stats()
+    return st0, st, counts, fi
+
+
+@pytest.fixture(scope="module")
+def rest(cuda):
+    return _run((0.0, 0.0))
+
+
+def test_energy_and_temperature(rest):
+    st0, st, _, _ = rest
+    assert st["status"] == 0
+    e0 = st0["kinetic"] + st0["potential"]
+    e1 = st["kinetic"] + st["potential"]
+    assert abs(e1 - e0) / abs(e0) < 1e-5
+    assert 45.0 < st["temperature"] < 50.5
+
+
+def test_msd_follows_exponential_vacf_with_tau_one_half(rest):
+    _, st, _, _ = rest
+    T = st["temperature"]
+    t = np.array(C.lags) * C.dt
+    msd = np.array([0.5 * (a + b) for a, b in st["msd"]])
+    taus = np.linspace(0.1, 1.5, 1401)
+    err = [np.sum((np.log([an.msd_exponential(T, tau, ti) for ti in t]) - np.log(msd)) ** 2)
+           for tau in taus]
+    tau = float(taus[int(np.argmin(err))])
+    assert 0.45 < tau < 0.55, tau
+    model = np.array([an.msd_exponential(T, 0.5, ti) for ti in t])
+    assert np.all(np.abs(msd / model - 1.0) < 0.03), msd / model
+
+
+def test_fi_matches_closed_form_at_measured_width(rest):
+    _, st, counts, fi = rest
+    for li, lag in enumerate(C.lags):
+        msd = 0.5 * (st["msd"][li][0] + st["msd"][li][1])
+        th = an.feq(C.vmax, math.sqrt(msd) / C.dx)
+        assert np.abs(fi[li] - th).max() < 0.01, (lag, np.abs(fi[li] - th).max())
+        assert int(counts[li].sum()) == C.n * st["intervals"][li]
+
+
+def test_moving_lattice_equilibrium(rest):
+    _, st_rest, _, _ = rest
+    li = C.lags.index(U_LAG)
+    U = U_LATTICE * C.dx / (U_LAG * C.dt)
+    _, st, _, fi = _run((U, 0.0))
+    # the lattice does not touch the dynamics
+    assert np.allclose(st["msd"], st_rest["msd"], rtol=1e-12) and st["kinetic"] == st_rest["kinetic"]
+    u = st["lattice_u"][0] * U_LAG * C.dt / C.dx
+    # the per-step shift U dt is a multiple of grid * 2^-24 (half a quantum off at most)
+    quantum = m.Params(n=1, box=1.0, dx=1.0).grid * 2.0 ** -24
+    assert abs(u - U_LATTICE) <= 0.5 * quantum / (U * C.dt) * U_LATTICE * 1.0001
+    msd = 0.5 * (st["msd"][li][0] + st["msd"][li][1])
+    a = math.sqrt(msd) / C.dx
+    th = an.feq(C.vmax, a, (u, 0.0))
+    assert np.abs(fi[li] - th).max() < 0.01
+    mom = an.moments(fi[li], C.vmax)
+    assert mom["mean"][0] == pytest.approx(u, abs=3e-3)
+    assert abs(mom["mean"][1]) < 3e-3

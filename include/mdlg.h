@@ -294,6 +294,29 @@ int mdlg_adjoint(mdlg_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double width
 #define MDLG_PROF_KINDS 4
 int mdlg_profile(mdlg_ctx *ctx, int enable, double *ms, int64_t *launches);
 
+/*
+ * Checkpoint / resume (no counterpart in the paper: long runs such as its 3e6-
+ * step trajectories are restarted from one).  A checkpoint is the complete run
+ * state of a context -- sorted particle state, every lag's stored lattice cells
+ * (and displacement origins), the Verlet list of the last re-sort, the device
+ * control block, MDLG totals, per-site fields and the host schedule (step, last
+ * re-sort, binned intervals) -- so that a context restored from it continues
+ * bit for bit as the saved one would have.
+ *
+ * mdlg_checkpoint_size -- bytes of this context's checkpoint (host out).
+ * mdlg_save  -- synchronize and write the checkpoint into buf (host memory of at
+ *               least that many bytes).
+ * mdlg_load  -- restore a checkpoint into a context created with the same
+ *               parameters (use_graphs and stats_every may differ) and, for a
+ *               batch, the same systems; the state it was created with is
+ *               replaced.  Synchronizes.
+ * Errors: MDLG_EINVAL (NULL arguments, buffer too small, not a checkpoint, or
+ * made by a context of another shape or parameters), MDLG_ECUDA.
+ */
+int mdlg_checkpoint_size(mdlg_ctx *ctx, uint64_t *bytes);
+int mdlg_save(mdlg_ctx *ctx, void *buf, uint64_t bytes);
+int mdlg_load(mdlg_ctx *ctx, const void *buf, uint64_t bytes);
+
 /* mdlg_destroy -- synchronize, release device state; NULL is ignored. */
 void mdlg_destroy(mdlg_ctx *ctx);
 

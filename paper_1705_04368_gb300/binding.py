@@ -93,6 +93,9 @@ _SIGNATURES = {
     "mdlg_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _P, _P,
                                     _P, _P, _P, _P, _P]),
     "mdlg_profile": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "mdlg_checkpoint_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "mdlg_save": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
+    "mdlg_load": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
     "mdlg_destroy": (None, [_P]),
     "mdlg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mdlg_bin": (ctypes.c_int, [ctypes.POINTER(_Lattice), ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
@@ -334,6 +337,19 @@ class Simulation:
 
     def reset_counts(self):
         _check(self._lib.mdlg_reset_counts(self._h), "mdlg_reset_counts")
+
+    def save(self) -> bytes:
+        """mdlg_save: the complete run state as bytes (see mdlg_checkpoint_size)."""
+        size = ctypes.c_uint64()
+        _check(self._lib.mdlg_checkpoint_size(self._h, ctypes.byref(size)), "mdlg_checkpoint_size")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(self._lib.mdlg_save(self._h, buf, size.value), "mdlg_save")
+        return buf.raw
+
+    def load(self, data: bytes):
+        """mdlg_load: continue from a checkpoint of a context with the same parameters."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(self._lib.mdlg_load(self._h, buf, len(data)), "mdlg_load")
 
     def close(self):
         if getattr(self, "_h", None):

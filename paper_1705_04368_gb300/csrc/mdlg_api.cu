@@ -1279,6 +1279,163 @@ int mdlg_adjoint(mdlg_ctx *c, int64_t nsteps, int32_t ckpt_every, double width,
     return status ? status : MDLG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint layout: a header, then the device regions below in this order.
+constexpr uint64_t kCkptMagic = 0x54504b43474c444dull;   // "MDLGCKPT"
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, nsys;
+    uint64_t total;             // bytes including this header
+    uint64_t shape_hash;        // parameters and geometry the regions depend on
+    int64_t step, last_sort, stats_step;
+    int64_t intervals[kMaxLags];
+    int32_t pos_cur, meta_cur;
+};
+
+struct Region {
+    void *p;
+    size_t bytes;
+};
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t k = 0; k < n; ++k) {
+        h ^= b[k];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+template <typename T>
+uint64_t mix(uint64_t h, const T &v) { return fnv1a(h, &v, sizeof(T)); }
+
+// Everything the saved regions and the schedule depend on (use_graphs and
+// stats_every excluded: they do not change the state).
+uint64_t shape_hash(const mdlg_ctx *c) {
+    const mdlg_params &p = c->p;
+    uint64_t h = 0xcbf29ce484222325ull;
+    h = mix(h, p.n); h = mix(h, p.box[0]); h = mix(h, p.box[1]); h = mix(h, p.potential);
+    h = mix(h, p.eps); h = mix(h, p.sigma); h = mix(h, p.mass); h = mix(h, p.rcut);
+    h = mix(h, p.dt); h = mix(h, p.grid); h = mix(h, p.skin); h = mix(h, p.dx);
+    h = mix(h, p.nlags);
+    for (int l = 0; l < p.nlags; ++l) h = mix(h, p.lag_steps[l]);
+    h = mix(h, p.vmax); h = mix(h, p.site_mode); h = mix(h, p.msd);
+    h = mix(h, p.lattice_u[0]); h = mix(h, p.lattice_u[1]);
+    h = mix(h, c->sort_every); h = mix(h, c->slots); h = mix(h, c->ncells); h = mix(h, c->cap);
+    h = mix(h, c->nsys);
+    if (c->nsys > 0) h = fnv1a(h, c->sys_host.data(), sizeof(SysInfo) * c->sys_host.size());
+    return h;
+}
+
+std::vector<Region> ckpt_regions(mdlg_ctx *c) {
+    const size_t N = (size_t)c->slots;
+    const int nl = c->p.nlags;
+    const int pc = c->pos_cur, mc = c->meta_cur;
+    std::vector<Region> r;
+    r.push_back({c->cell[mc], N * sizeof(uint32_t)});
+    r.push_back({c->pid[mc], N * sizeof(int32_t)});
+    r.push_back({c->cl[pc], N * sizeof(float2)});
+    r.push_back({c->vel[pc], N * sizeof(float2)});
+    for (int l = 0; l < nl; ++l) r.push_back({c->lprev[mc][l], N * sizeof(uint32_t)});
+    if (c->p.msd) {
+        for (int l = 0; l < nl; ++l) r.push_back({c->mprev[mc][l], N * sizeof(float2)});
+        r.push_back({c->msd_acc, 2 * nl * sizeof(double)});
+    }
+    r.push_back({c->cell_start, ((size_t)c->ncells + 1) * sizeof(int32_t)});
+    if (c->nbr) {
+        r.push_back({c->nbr, (size_t)c->cap * N * sizeof(uint32_t)});
+        r.push_back({c->ncount, N * sizeof(int32_t)});
+    }
+    r.push_back({c->ctl, sizeof(Control)});
+    const size_t nsb = c->nsys > 0 ? (size_t)c->nsys : 1;
+    r.push_back({c->counts, nsb * nl * c->q1 * sizeof(unsigned long long)});
+    if (c->nsys > 0) r.push_back({c->bstats, (size_t)c->nsys * 5 * sizeof(long long)});
+    if (c->p.site_mode) {
+        const size_t sites = (size_t)c->geo.lat[0] * c->geo.lat[1];
+        r.push_back({c->site_n, sites * sizeof(uint32_t)});
+        r.push_back({c->site_counts, sites * c->q1 * sizeof(uint32_t)});
+        if (c->site_counts_alt) {
+            r.push_back({c->site_counts_alt, sites * c->q1 * sizeof(uint32_t)});
+            r.push_back({c->xi, sites * (c->q1 - 1) * sizeof(int32_t)});
+            r.push_back({c->dmass, sites * sizeof(int32_t)});
+            r.push_back({c->dmom, 2 * sites * sizeof(int32_t)});
+        }
+    }
+    return r;
+}
+
+uint64_t ckpt_total(mdlg_ctx *c) {
+    uint64_t t = sizeof(CkptHeader);
+    for (const Region &g : ckpt_regions(c)) t += g.bytes;
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdlg_checkpoint_size(mdlg_ctx *c, uint64_t *bytes) {
+    if (!c || !bytes) return MDLG_EINVAL;
+    *bytes = ckpt_total(c);
+    return MDLG_OK;
+}
+
+int mdlg_save(mdlg_ctx *c, void *buf, uint64_t bytes) {
+    if (!c || !buf) return MDLG_EINVAL;
+    const uint64_t total = ckpt_total(c);
+    if (bytes < total) return MDLG_EINVAL;
+    CkptHeader h{};
+    h.magic = kCkptMagic;
+    h.version = kCkptVersion;
+    h.nsys = (uint32_t)c->nsys;
+    h.total = total;
+    h.shape_hash = shape_hash(c);
+    h.step = c->step;
+    h.last_sort = c->last_sort;
+    h.stats_step = c->stats_step;
+    for (int l = 0; l < kMaxLags; ++l) h.intervals[l] = c->intervals[l];
+    h.pos_cur = c->pos_cur;
+    h.meta_cur = c->meta_cur;
+    memcpy(buf, &h, sizeof(h));
+    unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(h);
+    for (const Region &g : ckpt_regions(c)) {
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(o, g.p, g.bytes, cudaMemcpyDeviceToHost, c->stream)));
+        o += g.bytes;
+    }
+    return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+int mdlg_load(mdlg_ctx *c, const void *buf, uint64_t bytes) {
+    if (!c || !buf || bytes < sizeof(CkptHeader)) return MDLG_EINVAL;
+    CkptHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kCkptMagic || h.version != kCkptVersion || h.nsys != (uint32_t)c->nsys)
+        return MDLG_EINVAL;
+    if (h.shape_hash != shape_hash(c) || bytes < h.total) return MDLG_EINVAL;
+    if ((h.pos_cur & ~1) || (h.meta_cur & ~1)) return MDLG_EINVAL;
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    drop_graph(c);                 // a captured schedule refers to the old step count
+    c->pos_cur = h.pos_cur;
+    c->meta_cur = h.meta_cur;
+    if (ckpt_total(c) != h.total) return MDLG_EINVAL;
+    const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof(h);
+    for (const Region &g : ckpt_regions(c)) {
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(g.p, o, g.bytes, cudaMemcpyHostToDevice, c->stream)));
+        o += g.bytes;
+    }
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+    c->step = h.step;
+    c->last_sort = h.last_sort;
+    c->stats_step = h.stats_step;
+    for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = h.intervals[l];
+    return MDLG_OK;
+}
+
 int mdlg_profile(mdlg_ctx *c, int enable, double *ms, int64_t *launches) {
     if (!c) return MDLG_EINVAL;
     if (enable) {

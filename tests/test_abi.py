@@ -146,5 +146,14 @@ def test_get_collision_rejects_null_context():
     assert m.lib().mdlg_get_collision(None, None, None, None) == -1
 
 
+def test_checkpoint_entry_points_validate():
+    L = m.lib()
+    size = ctypes.c_uint64()
+    buf = ctypes.create_string_buffer(64)
+    assert L.mdlg_checkpoint_size(None, ctypes.byref(size)) == -1
+    assert L.mdlg_save(None, buf, 64) == -1
+    assert L.mdlg_load(None, buf, 64) == -1
+
+
 def test_adjoint_rejects_null_context():
     assert m.lib().mdlg_adjoint(None, 10, 10, 1.0, None, None, None, None, None, None, None) == -1

@@ -121,6 +121,26 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of the independent system a rank advances (weak scaling: one system each)."""
+    return 1 + rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest of every rank's value (a job takes as long as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
 def _workload():
     c = mi.PRODUCTION_LJ
     return c
@@ -188,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     c = _workload()
-    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1 + rank)
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=rank_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     # neighbour-cell geometry picked by the autotuner (cached per workload; untimed)
     from paper_1705_04368_gb300 import tune
@@ -218,15 +238,11 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     st, counts, fi = sim.stats()
     sim.close()
     md_steps = args.steps * MD_STEPS_PER_STEP
-    value = world * c.n * md_steps / (ms / 1e3)
+    value = job_rate(world, c.n * md_steps, ms / 1e3)
 
     # dominant kernel: fused force + velocity-Verlet step
     hbm_gbs, sm_max_mhz, peak_kind = _peaks()
@@ -475,14 +491,10 @@ def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev
     for _ in range(reps):
         one()
     torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([secs], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = max_over_ranks(time.perf_counter() - t0, dist, dev)
     q1 = params.q1
     nl = len(params.lag_steps)
-    return {"value": world * c.n * MD_STEPS_PER_STEP * reps / secs, "unit": UNIT,
+    return {"value": job_rate(world, c.n * MD_STEPS_PER_STEP * reps, secs), "unit": UNIT,
             "h2d_bytes_per_step": 2 * c.n * 2 * 8,
             "d2h_bytes_per_step": 2 * nl * q1 * 8 + 120,
             "steps": reps,

@@ -27,7 +27,8 @@ namespace {
 constexpr int kStepThreads = 256;   // one system; a batch uses one 128-slot chunk per block
 constexpr int kListBatch = 4;       // list entries loaded before any is used (lists are
                                     // padded to a multiple of this)
-constexpr int kNlistThreads = 64;   // list-build block (entries staged in shared memory)
+constexpr int kNlistThreads = 128;  // list-build block (entries staged in shared memory;
+                                    // 64 when the list capacity is large)
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 cells per scan block
@@ -520,7 +521,8 @@ template <bool B>
 __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
     // entries are staged in shared memory and written after the search, so
     // that no global store precedes a candidate load (see k_bin_state)
-    extern __shared__ uint32_t s_ent[];          // kNlistThreads x cap, column-major
+    extern __shared__ uint32_t s_ent[];          // blockDim.x x cap, column-major
+    const int nt = blockDim.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
                             if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
                                 if (cnt < a.cap)
-                                    s_ent[cnt * kNlistThreads + threadIdx.x] =
+                                    s_ent[cnt * nt + threadIdx.x] =
                                         (uint32_t)j | ((uint32_t)(ox + 1) << 28) | ycode;
                                 ++cnt;
                             }
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const int32_t j = b + u;
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
                             if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
-                                if (cnt < a.cap) s_ent[cnt * kNlistThreads + threadIdx.x] = (uint32_t)j | code;
+                                if (cnt < a.cap) s_ent[cnt * nt + threadIdx.x] = (uint32_t)j | code;
                                 ++cnt;
                             }
                         }
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                 }
             }
             const int keep = cnt < a.cap ? cnt : a.cap;
-            for (int t = 0; t < keep; ++t) a.nbr[(int64_t)t * a.n + i] = s_ent[t * kNlistThreads + threadIdx.x];
+            for (int t = 0; t < keep; ++t) a.nbr[(int64_t)t * a.n + i] = s_ent[t * nt + threadIdx.x];
             // padding to a multiple of the step kernel's batch (cap is a multiple of it)
             if (cnt <= a.cap) {
                 const int npad = (cnt + kListBatch - 1) & ~(kListBatch - 1);
@@ -749,13 +751,14 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
     k_sort_scatter<B><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     if (a.nbr) {
-        const size_t smem = sizeof(uint32_t) * (size_t)kNlistThreads * a.cap;
+        const int nt = (size_t)kNlistThreads * a.cap * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
+        const size_t smem = sizeof(uint32_t) * (size_t)nt * a.cap;
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(k_nlist<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_nlist<B><<<grid_for(a.n, kNlistThreads, 32), kNlistThreads, smem, s>>>(a);
+        k_nlist<B><<<grid_for(a.n, nt, 32), nt, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

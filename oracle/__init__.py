@@ -108,7 +108,8 @@ def _f64(a) -> np.ndarray:
 
 
 def lj_forces(x, box, eps=1.0, sigma=1.0, rc=2.5, cells=False, shifted_force=False):
-    """Lennard-Jones forces, sum_j |F_ij| per particle, potential energy and virial.
+    """Lennard-Jones forces, the per-particle error scale sum_j (|F_rep,ij| + |F_att,ij|),
+    potential energy and virial.
 
     x: (n, 2) positions.  Returns (F (n,2), fscale (n,), pe, virial).
     shifted_force: F(r) - F(rc) instead of the force truncated at rc.

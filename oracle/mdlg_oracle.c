@@ -94,6 +94,22 @@ static double lj_pair_energy(double r2, double eps, double sigma)
     return e;
 }
 
+/*
+ * Error scale of one pair force evaluated in binary32: the magnitudes of its
+ * terms -- the repulsive 2 s^12 and attractive s^6 parts of Sec. IV's force
+ * (and the shifted-force constant) -- summed in absolute value.  Their
+ * difference vanishes at r = 2^(1/6) sigma while the rounding error of each
+ * term remains, so tolerances are stated against this sum, not against |F_ij|.
+ */
+static double lj_fterm_scale(double r2, double eps, double sigma)
+{
+    double sr2 = sigma * sigma / r2;
+    double sr6 = sr2 * sr2 * sr2;
+    double m = fabs(24.0 * eps * (2.0 * sr6 * sr6 + sr6)) / sqrt(r2);
+    if (g_sf) m += fabs(lj_fscalar_plain(g_rc * g_rc, eps, sigma) * g_rc);
+    return m;
+}
+
 /* Select the cutoff treatment for the following calls. */
 void oracle_set_shifted_force(int sf) { g_sf = sf; }
 
@@ -104,8 +120,9 @@ void oracle_set_shifted_force(int sf) { g_sf = sf; }
  *
  *   x      : n x 2 positions (row-major, x then y)
  *   f      : n x 2 output forces
- *   fscale : optional n output, sum_j |F_ij| (a per-particle force magnitude
- *            scale used to state relative force tolerances)
+ *   fscale : optional n output, sum_j of the pair-force term magnitudes
+ *            (lj_fterm_scale): the per-particle scale relative force
+ *            tolerances are stated against
  *   out    : optional [pe, virial] where pe = sum_{i<j} (V(r_ij) - V(rc)) and
  *            virial = sum_{i<j} r_ij . F_ij
  */
@@ -127,7 +144,7 @@ void oracle_lj_forces_direct(int64_t n, const double *x, const double *L,
             double s = lj_fscalar(r2, eps, sigma);
             fx += s * dx;
             fy += s * dy;
-            fs += fabs(s) * sqrt(r2);
+            fs += lj_fterm_scale(r2, eps, sigma);
             pe += 0.5 * lj_pair_energy(r2, eps, sigma);
             vir += 0.5 * s * r2;
         }
@@ -162,7 +179,7 @@ void oracle_lj_forces_sample(int64_t n, const double *x, const double *L,
             double s = lj_fscalar(r2, eps, sigma);
             fx += s * dx;
             fy += s * dy;
-            fs += fabs(s) * sqrt(r2);
+            fs += lj_fterm_scale(r2, eps, sigma);
         }
         f[2 * k] = fx;
         f[2 * k + 1] = fy;
@@ -219,7 +236,7 @@ void oracle_lj_forces_cells(int64_t n, const double *x, const double *L,
                     double s = lj_fscalar(r2, eps, sigma);
                     fx += s * dx;
                     fy += s * dy;
-                    fs += fabs(s) * sqrt(r2);
+                    fs += lj_fterm_scale(r2, eps, sigma);
                     pe += 0.5 * lj_pair_energy(r2, eps, sigma);
                     vir += 0.5 * s * r2;
                 }

@@ -2,7 +2,8 @@
 of the simulation state against the FP64 oracle.
 
 Tolerances (FP32 pair arithmetic against FP64):
-  forces      |F_gpu - F_ref| <= 1e-5 * sum_j |F_ij|  per particle, on positions
+  forces      |F_gpu - F_ref| <= 1e-5 * sum_j (|F_rep,ij| + |F_att,ij|) per particle (the
+              magnitudes of the repulsive and attractive terms), on positions
               exactly representable on both sides (multiples of 2^-20)
   trajectory  10 steps, every coordinate within 1e-4 sigma (minimum image)
   FP64 sums   kinetic energy rel 1e-6, potential energy and virial rel 1e-5

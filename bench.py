@@ -523,6 +523,65 @@ def run_ncu_target(md_steps):
     sim.close()
 
 
+def run_state_point(total: int, discard: int):
+    """The paper's own state point on this engine (Sec. IV, Figs. VD and wi_u):
+    N = 100 000, L = 1000 sigma, T = 50, dt = 1e-4; `total` MD steps of which the
+    first `discard` are dropped (the paper: 3e6 and 1e6).  Lattice dx = 100 sigma,
+    coarse step dt_LG = 34.16 tau (341 600 MD steps), imposed lattice velocity u =
+    0 ... 0.5 (lattice units) by moving the lattice; the MSD of six shorter lags
+    gives the decay time tau of Eq. vca.  Prints one JSON line: per u the
+    measured f_i against Eq. feqfull (at the measured a^2) and against the D2Q9
+    equilibrium of Eq. f0lb (theta = 1/3)."""
+    import torch
+    import paper_1705_04368_gb300 as m
+    from paper_1705_04368_gb300 import analysis as an
+    c = mi.PAPER_STATE_POINT
+    dx, lag = 100.0, 341_600
+    lags = (100, 1000, 3000, 7000, 20000, 50000, lag)
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=5)
+    out = {"workload": "lj2d_n100000_L1000_T50_dt1e-4", "md_steps": total, "discarded": discard,
+           "dx": dx, "dt_lattice_tau": lag * c.dt, "runs": []}
+    t0 = time.perf_counter()
+    for u in (0.0, 0.1, 0.2, 0.3, 0.4, 0.5):
+        U = u * dx / (lag * c.dt)
+        p = m.Params(n=c.n, box=c.box, dx=dx, dt=c.dt, lag_steps=lags, vmax=c.vmax, msd=True,
+                     stats_every=10000, lattice_u=(U, 0.0))
+        with m.Simulation(p, x0, v0) as s:
+            s.step(discard)
+            s.reset_counts()
+            s.step(total - discard)
+            st, _, fi = s.stats()
+        torch.cuda.synchronize()
+        T = st["temperature"]
+        msd = [0.5 * (a + b) for a, b in st["msd"]]
+        if u == 0.0:
+            ts = [l * c.dt for l in lags[:-1]]
+            grid = np.linspace(0.1, 1.5, 1401)
+            err = [sum((math.log(an.msd_exponential(T, tau, t)) - math.log(mm)) ** 2
+                       for t, mm in zip(ts, msd)) for tau in grid]
+            out["tau_fit"] = float(grid[int(np.argmin(err))])
+            out["temperature"] = T
+        ueff = st["lattice_u"][0] * lag * c.dt / dx
+        a = math.sqrt(msd[-1]) / dx
+        f = fi[-1]
+        th = an.feq(c.vmax, a, (ueff, 0.0))
+        lb = an.lb_equilibrium((ueff, 0.0), vmax=c.vmax)
+        shell = np.abs(an.velocity_table(c.vmax)).max(axis=1) <= 1
+        w = 2 * c.vmax + 1
+        pick = {"rest": (0, 0), "east": (1, 0), "west": (-1, 0), "north": (0, 1),
+                "north_east": (1, 1), "north_west": (-1, 1)}
+        out["runs"].append({
+            "u": ueff, "a2": a * a, "intervals": st["intervals"][-1], "status": st["status"],
+            "max_abs_vs_closed_form": float(np.abs(f[:-1] - th[:-1]).max()),
+            "max_abs_vs_lb_one_shell": float(np.abs(f[:-1][shell] - lb[:-1][shell]).max()),
+            "mean_velocity": float(an.moments(f, c.vmax)["mean"][0]),
+            "f": {k: [float(f[(vy + c.vmax) * w + vx + c.vmax]),
+                      float(th[(vy + c.vmax) * w + vx + c.vmax]),
+                      float(lb[(vy + c.vmax) * w + vx + c.vmax])] for k, (vx, vy) in pick.items()}})
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out), flush=True)
+
+
 def run_ncu_collision(launches):
     """profiling target: the collision operator on the production lattice
     (935 x 935 sites, V = 3, random fields), `launches` launches."""
@@ -554,7 +613,14 @@ def main():
     ap.add_argument("--ncu-collision", type=int, default=0, metavar="LAUNCHES",
                     help="profiling target: LAUNCHES collision-operator launches on the "
                          "production lattice, exit")
+    ap.add_argument("--state-point", type=int, nargs=2, default=None, metavar=("TOTAL", "DISCARD"),
+                    help="the paper's state point (N = 100 000, T = 50): TOTAL MD steps, the first "
+                         "DISCARD dropped (the paper: 3000000 1000000); u-sweep of the moving "
+                         "lattice at dx = 100, dt_LG = 34.16; one JSON line")
     args = ap.parse_args()
+    if args.state_point:
+        run_state_point(*args.state_point)
+        return
     if args.ncu_collision:
         run_ncu_collision(args.ncu_collision)
         return

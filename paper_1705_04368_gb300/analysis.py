@@ -21,6 +21,23 @@ import numpy as np
 D2Q9 = {(0, 0): 4.0 / 9.0, (1, 0): 1.0 / 9.0, (1, 1): 1.0 / 36.0}
 
 
+def lb_equilibrium(u: Sequence[float], vmax: int = 1, theta: float = 1.0 / 3.0,
+                   rho: float = 1.0) -> np.ndarray:
+    """Second-order lattice Boltzmann equilibrium of Sec. V (Eq. f0lb) for the
+    D2Q9 weights, f_i^0 = rho w_i (1 + v.u/theta + (v.u)^2/(2 theta^2) - u.u/(2 theta)),
+    laid out on the (2V+1)^2 window (zero outside the first shell) plus an
+    empty overflow entry."""
+    vel = velocity_table(vmax).astype(np.float64)
+    w = np.zeros(len(vel))
+    for k, (vx, vy) in enumerate(vel.astype(int)):
+        if max(abs(vx), abs(vy)) <= 1:
+            w[k] = D2Q9[(max(abs(vx), abs(vy)), min(abs(vx), abs(vy)))]
+    uu = np.asarray(u, dtype=np.float64)
+    vu = vel @ uu
+    f = rho * w * (1.0 + vu / theta + 0.5 * vu * vu / (theta * theta) - 0.5 * (uu @ uu) / theta)
+    return np.concatenate([f, [0.0]])
+
+
 def velocity_table(vmax: int) -> np.ndarray:
     """(Q, 2) integer lattice velocities in index order."""
     w = 2 * vmax + 1

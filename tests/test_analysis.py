@@ -136,3 +136,19 @@ def test_consistent_dt_regimes():
         w = an.D2Q9[v]
         assert cf.feq_over_rho(v, a) == pytest.approx(w, rel=1e-9)
         assert an.msd_exponential(T, tau, dt) == pytest.approx(a2 * 1e4, rel=1e-9)
+
+
+def test_lb_equilibrium_moments():
+    # Eq. f0lb with theta = 1/3 reproduces Eqs. mom0-tet exactly (to second order
+    # in u) and carries the third moment rho u u u on one shell (Sec. V)
+    u = (0.07, -0.04)
+    f = an.lb_equilibrium(u, vmax=2)
+    out = an.moments(f, 2, u)
+    assert out["rho"] == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose(out["mean"], u, atol=1e-15)
+    assert np.allclose(out["M2"], np.eye(2) / 3.0, atol=1e-14)
+    # one shell has v^3 = v, so the central third moment is -rho u_x^3: of the
+    # size rho u u u the paper calls small for u < 0.1
+    assert out["M3"][0, 0, 0] == pytest.approx(-u[0] ** 3, abs=1e-15)
+    assert np.allclose(an.lb_equilibrium((0.0, 0.0))[:9],
+                       [1 / 36, 1 / 9, 1 / 36, 1 / 9, 4 / 9, 1 / 9, 1 / 36, 1 / 9, 1 / 36])

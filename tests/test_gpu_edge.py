@@ -73,3 +73,22 @@ def test_dense_lists_overflow_to_cell_stencil(cuda):
     f_ref, scale, _, _ = oracle.lj_forces(x0, (L, L))
     assert np.all(np.abs(f - f_ref).max(axis=1) <= 1e-5 * np.maximum(scale, 1e-3))
     assert st["status"] == 0
+
+
+@pytest.mark.parametrize("bad", ["nan_x", "zero_x", "outside_x", "inf_v"])
+def test_invalid_initial_state_is_reported(cuda, bad):
+    # the upload kernel flags the state (every index it derives is clamped) and
+    # mdlg_create returns MDLG_ENONFINITE without a context
+    n, L = 64, 32.0
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=9)
+    if bad == "nan_x":
+        x0[5, 0] = np.nan
+    elif bad == "zero_x":
+        x0[7, 1] = 0.0                      # the box is (0, L]
+    elif bad == "outside_x":
+        x0[3, 0] = L + 0.5
+    else:
+        v0[11, 1] = np.inf
+    with pytest.raises(m.MdlgError) as e:
+        m.Simulation(m.Params(n=n, box=L, dx=4.0), x0, v0)
+    assert e.value.code == -5

@@ -72,7 +72,8 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # ORACLE_LIB: an alternative build of the same source (the sanitizer test)
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
             P = ctypes.c_void_p
             I64 = ctypes.c_int64
             D = ctypes.c_double

@@ -1078,7 +1078,8 @@ int mdlg_adjoint(mdlg_ctx *c, int64_t nsteps, int32_t ckpt_every, double width,
         if (!ptr) return MDLG_ENOMEM;            \
     } while (0)
     double *x_start, *gx0, *theta, *fsum, *lossd, *wts = nullptr;
-    float2 *traj, *vbuf, *xb[2], *w[2], *xb_orig, *w_orig;
+    float2 *traj = nullptr, *vbuf = nullptr, *xb[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr};
+    float2 *xb_orig = nullptr, *w_orig = nullptr;
     float *dck, *dfinal;
     ADJ_ALLOC(x_start, double, 2 * N);
     ADJ_ALLOC(gx0, double, 2 * N);

@@ -191,11 +191,12 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(_config(c, 1), md_steps_per_step=1),
+            "data": "synthetic", "config": _config(c, 1),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} velocity-Verlet steps of the full "
-                                       f"{c.n}-particle system, FP64 linked-cell oracle"},
+                             "sample": f"{len(times)} bench steps of one FP64 velocity-Verlet "
+                                       f"step each (not 200) of the full {c.n}-particle "
+                                       f"system, linked-cell oracle, one host thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -602,6 +602,20 @@ def run_ncu_collision(launches):
     torch.cuda.synchronize()
 
 
+def run_ncu_idealgas(launches):
+    """profiling target: `launches` ideal-gas passes over the 2^22-particle gas
+    (9 (dx, dt) pairs), the bench's idealgas leg."""
+    import torch
+    import paper_1705_04368_gb300 as m
+    dev = torch.device("cuda", 0)
+    pos, vel = mi.idealgas_state(mi.IDEALGAS_N, mi.IDEALGAS_BOX, 1.0, seed=7)
+    pos, vel = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+    counts = torch.zeros((len(mi.IDEALGAS_COMBOS), 50), dtype=torch.int64, device=dev)
+    for _ in range(launches):
+        m.idealgas_bin(pos, vel, list(mi.IDEALGAS_COMBOS), 3, counts)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -618,7 +632,12 @@ def main():
                     help="the paper's state point (N = 100 000, T = 50): TOTAL MD steps, the first "
                          "DISCARD dropped (the paper: 3000000 1000000); u-sweep of the moving "
                          "lattice at dx = 100, dt_LG = 34.16; one JSON line")
+    ap.add_argument("--ncu-idealgas", type=int, default=0, metavar="LAUNCHES",
+                    help="profiling target: LAUNCHES ideal-gas passes, exit")
     args = ap.parse_args()
+    if args.ncu_idealgas:
+        run_ncu_idealgas(args.ncu_idealgas)
+        return
     if args.state_point:
         run_state_point(*args.state_point)
         return

@@ -64,13 +64,16 @@ __global__ void k_bin_snapshots(LatticeArgs la, int64_t n, const int2 *__restric
 // its start and end point.  Cell decisions in binary32 with explicit rounding
 // (no contraction into FMA): x' = fl(x + fl(v dt)), cell = ceil(fl(x / dx)) - 1,
 // with v boosted first, v = fl(v + U), when the pair has a lattice drift U.
+// The pair count is a template parameter, so the loop is unrolled and every
+// pair's parameters are compile-time offsets into the argument block.
 // Multiplying by 1/dx equals dividing by dx when dx is a power of two.
+template <int NC>
 __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restrict__ pos,
                                const float2 *__restrict__ vel, unsigned long long *counts) {
     extern __shared__ uint32_t sh[];
     const int w = 2 * ga.vmax + 1, q1 = w * w + 1;
     const int center = ga.vmax * w + ga.vmax;
-    for (int b = threadIdx.x; b < q1 * ga.ncombo; b += blockDim.x) sh[b] = 0;
+    for (int b = threadIdx.x; b < q1 * NC; b += blockDim.x) sh[b] = 0;
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -81,18 +84,17 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
             p = pos[j];
             v = vel[j];
         }
-        float last_dx = -1.f;
         int32_t c0x = 0, c0y = 0;
-        for (int k = 0; k < ga.ncombo; ++k) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
             const float dx = ga.dx[k], dt = ga.dt[k];
             const bool pow2 = ga.pow2[k] != 0;
             const float inv = ga.inv_dx[k];
-            if (dx != last_dx) {
+            if (k == 0 || dx != ga.dx[k - 1]) {
                 const float qx = pow2 ? __fmul_rn(p.x, inv) : __fdiv_rn(p.x, dx);
                 const float qy = pow2 ? __fmul_rn(p.y, inv) : __fdiv_rn(p.y, dx);
-                c0x = __float2int_ru(qx) - 1;
-                c0y = __float2int_ru(qy) - 1;
-                last_dx = dx;
+                c0x = ceil_small(qx) - 1;
+                c0y = ceil_small(qy) - 1;
             }
             const float vx_ = ga.boost ? __fadd_rn(v.x, ga.ux[k]) : v.x;
             const float vy_ = ga.boost ? __fadd_rn(v.y, ga.uy[k]) : v.y;
@@ -100,13 +102,13 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
             const float yn = __fadd_rn(p.y, __fmul_rn(vy_, dt));
             const float qx = pow2 ? __fmul_rn(xn, inv) : __fdiv_rn(xn, dx);
             const float qy = pow2 ? __fmul_rn(yn, inv) : __fdiv_rn(yn, dx);
-            const int32_t vx = __float2int_ru(qx) - 1 - c0x;
-            const int32_t vy = __float2int_ru(qy) - 1 - c0y;
+            const int32_t vx = ceil_small(qx) - 1 - c0x;
+            const int32_t vy = ceil_small(qy) - 1 - c0y;
             hist_add(sh + k * q1, vel_index(vx, vy, ga.vmax), center, act);
         }
     }
     __syncthreads();
-    for (int k = 0; k < ga.ncombo; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)k * q1);
+    for (int k = 0; k < NC; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)k * q1);
 }
 
 // Sum v over the block into out (added to, FP64); every thread calls it.
@@ -463,19 +465,33 @@ cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *pos,
-                                const float *vel, unsigned long long *counts, cudaStream_t s) {
+template <int NC>
+cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *pos,
+                               const float *vel, unsigned long long *counts, cudaStream_t s) {
     const int threads = 256;
     const int q1 = (2 * ga.vmax + 1) * (2 * ga.vmax + 1) + 1;
-    const size_t smem = (size_t)q1 * ga.ncombo * sizeof(uint32_t);
+    const size_t smem = (size_t)q1 * NC * sizeof(uint32_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_idealgas_bin,
+        cudaError_t e = cudaFuncSetAttribute(k_idealgas_bin<NC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_idealgas_bin<<<hist_grid(n, threads), threads, smem, s>>>(
+    k_idealgas_bin<NC><<<hist_grid(n, threads), threads, smem, s>>>(
         ga, n, reinterpret_cast<const float2 *>(pos), reinterpret_cast<const float2 *>(vel), counts);
     return cudaGetLastError();
+}
+
+cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *pos,
+                                const float *vel, unsigned long long *counts, cudaStream_t s) {
+    switch (ga.ncombo) {
+#define MDLG_IG_CASE(K) case K: return launch_idealgas_nc<K>(ga, n, pos, vel, counts, s);
+        MDLG_IG_CASE(1) MDLG_IG_CASE(2) MDLG_IG_CASE(3) MDLG_IG_CASE(4) MDLG_IG_CASE(5)
+        MDLG_IG_CASE(6) MDLG_IG_CASE(7) MDLG_IG_CASE(8) MDLG_IG_CASE(9) MDLG_IG_CASE(10)
+        MDLG_IG_CASE(11) MDLG_IG_CASE(12) MDLG_IG_CASE(13) MDLG_IG_CASE(14) MDLG_IG_CASE(15)
+        MDLG_IG_CASE(16)
+#undef MDLG_IG_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {

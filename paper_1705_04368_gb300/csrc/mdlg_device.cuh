@@ -50,6 +50,14 @@ __device__ __forceinline__ int32_t wrap_mod(int32_t d, int32_t m) {
     return d;
 }
 
+// ceil(t) for |t| < 2^22 without a conversion instruction: t + 1.5 * 2^23
+// rounded up lands on an integer in [2^23, 2^24), where binary32 spacing is 1,
+// so the result is 1.5 * 2^23 + ceil(t) exactly; its bit pattern minus that of
+// 1.5 * 2^23 is ceil(t).
+__device__ __forceinline__ int32_t ceil_small(float t) {
+    return __float_as_int(__fadd_ru(t, 12582912.0f)) - 0x4B400000;
+}
+
 // Base cell of a particle: the cell (b g, (b+1) g] that holds origin + cl.
 // cl / g is exact (g a power of two), ceil(t) - 1 is the left-open rule.  A
 // particle is within a few cells of its MD cell's origin, so one conditional
@@ -57,8 +65,8 @@ __device__ __forceinline__ int32_t wrap_mod(int32_t d, int32_t m) {
 // flagged elsewhere) a valid index.
 __device__ __forceinline__ int32_t base_cell(int32_t origin, float cl, float inv_g, int32_t lg) {
     const float lim = (float)lg;
-    const float t = fminf(fmaxf(ceilf(cl * inv_g), -lim + 1.0f), lim);
-    int32_t b = origin + (int32_t)t - 1;
+    const float t = fminf(fmaxf(cl * inv_g, -lim + 1.0f), lim);   // NaN -> -lim + 1
+    int32_t b = origin + ceil_small(t) - 1;
     b += b < 0 ? lg : 0;
     b -= b >= lg ? lg : 0;
     return b;

@@ -127,3 +127,16 @@ def test_idealgas_matches_closed_form(cuda):
         se = np.sqrt(np.maximum(p * (1 - p), 1e-300) / n)
         z = np.abs(got[k] / n - p) / se
         assert np.all(z[p > 1e-6] < 4.0), (dx, dt, z.max())
+
+
+def test_idealgas_largest_window_and_pair_count(cuda):
+    # 16 (dx, dt) pairs with the V = 15 window: 16 x 962 histogram bins (61.6 KB of
+    # shared memory, above the default 48 KB), non-power-of-two dx among them
+    pos, vel = mi.idealgas_state(200_003, 256.0, 1.0, seed=12)
+    combos = [(dx, dt) for dx in (1.0, 2.0, 4.0, 0.5) for dt in (0.25, 1.0, 3.0, 6.0)]
+    combos[5] = (3.0, 1.5)
+    got = _idealgas(cuda, pos, vel, combos, 15)
+    ref = oracle.stream_bin_f32(pos, vel, [c[0] for c in combos], [c[1] for c in combos], 15)
+    assert np.array_equal(got, ref)
+    assert np.all(got.sum(axis=1) == 200_003)
+

@@ -79,3 +79,25 @@ def test_resume_batch_and_rejects_other_shapes(cuda):
     with pytest.raises(m.MdlgError):
         with m.BatchSimulation(p, ns, boxes, x0, v0) as d:
             d.load(ck[:-8])
+
+
+def test_resume_into_context_with_captured_graph(cuda):
+    # the loading context has replayed graphs of its own schedule (sort every 5,
+    # lag 10, statistics every 10: 20-step graphs); the load drops them, the
+    # next steps capture new ones, and the result equals an uninterrupted run
+    n, L = 8000, mi.box_for(8000, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=51)
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=(10,), sort_every=5, stats_every=10,
+                 use_graphs=True)
+    with m.Simulation(p, x0, v0) as ref:
+        ref.step(333)
+        want = _record(ref)
+    with m.Simulation(p, x0, v0) as a:
+        a.step(133)
+        ck = a.save()
+    with m.Simulation(p, x0, v0) as b:
+        b.step(60)                      # captures and replays a graph
+        b.load(ck)
+        b.step(200)
+        got = _record(b)
+    _same(want, got)

@@ -316,3 +316,22 @@ def test_moving_lattice_equilibrium_and_moments(cuda):
         mt = an.moments(pth, V, ueff, a=a)
         assert np.allclose(mg["Psi"], mt["Psi"], rtol=5e-3, atol=5e-3), (k, mg["Psi"], mt["Psi"])
         assert np.allclose(mg["mean"], mt["mean"], atol=2e-3)
+
+
+def test_collision_full_production_lattice(cuda):
+    # the bench's size: 935 x 935 sites (L = 3740, dx = 4), V = 3, random fields
+    import torch
+    C, vmax = (935, 935), 3
+    rng = np.random.default_rng(935)
+    fp = rng.integers(0, 20, size=(C[0] * C[1], 50)).astype(np.uint32)
+    fc = rng.integers(0, 20, size=(C[0] * C[1], 50)).astype(np.uint32)
+    xi = torch.empty((C[0] * C[1], 49), dtype=torch.int32, device=cuda)
+    dm = torch.empty(C[0] * C[1], dtype=torch.int32, device=cuda)
+    dj = torch.empty((C[0] * C[1], 2), dtype=torch.int32, device=cuda)
+    m.collision(C, vmax, torch.from_numpy(fp.view(np.int32)).to(cuda),
+                torch.from_numpy(fc.view(np.int32)).to(cuda), xi, dm, dj)
+    torch.cuda.synchronize()
+    ref = oracle.collision(C, vmax, fp, fc)
+    assert np.array_equal(xi.cpu().numpy(), ref)
+    assert np.array_equal(dm.cpu().numpy(), ref.sum(axis=1))
+    assert np.array_equal(dj.cpu().numpy(), ref @ oracle.velocity_table(vmax))

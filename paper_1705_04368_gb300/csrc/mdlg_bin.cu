@@ -65,9 +65,10 @@ __global__ void k_bin_snapshots(LatticeArgs la, int64_t n, const int2 *__restric
 // (no contraction into FMA): x' = fl(x + fl(v dt)), cell = ceil(fl(x / dx)) - 1,
 // with v boosted first, v = fl(v + U), when the pair has a lattice drift U.
 // The pair count is a template parameter, so the loop is unrolled and every
-// pair's parameters are compile-time offsets into the argument block.
+// pair's parameters are compile-time offsets into the argument block; when
+// every dx is a power of two (ALLPOW2) the division path is not compiled in.
 // Multiplying by 1/dx equals dividing by dx when dx is a power of two.
-template <int NC>
+template <int NC, bool ALLPOW2>
 __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restrict__ pos,
                                const float2 *__restrict__ vel, unsigned long long *counts) {
     extern __shared__ uint32_t sh[];
@@ -88,7 +89,7 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float dx = ga.dx[k], dt = ga.dt[k];
-            const bool pow2 = ga.pow2[k] != 0;
+            const bool pow2 = ALLPOW2 || ga.pow2[k] != 0;
             const float inv = ga.inv_dx[k];
             if (k == 0 || dx != ga.dx[k - 1]) {
                 const float qx = pow2 ? __fmul_rn(p.x, inv) : __fdiv_rn(p.x, dx);
@@ -465,26 +466,29 @@ cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t
     return cudaGetLastError();
 }
 
-template <int NC>
+template <int NC, bool ALLPOW2>
 cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *pos,
                                const float *vel, unsigned long long *counts, cudaStream_t s) {
     const int threads = 256;
     const int q1 = (2 * ga.vmax + 1) * (2 * ga.vmax + 1) + 1;
     const size_t smem = (size_t)q1 * NC * sizeof(uint32_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_idealgas_bin<NC>,
+        cudaError_t e = cudaFuncSetAttribute(k_idealgas_bin<NC, ALLPOW2>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_idealgas_bin<NC><<<hist_grid(n, threads), threads, smem, s>>>(
+    k_idealgas_bin<NC, ALLPOW2><<<hist_grid(n, threads), threads, smem, s>>>(
         ga, n, reinterpret_cast<const float2 *>(pos), reinterpret_cast<const float2 *>(vel), counts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *pos,
                                 const float *vel, unsigned long long *counts, cudaStream_t s) {
+    bool allpow2 = true;
+    for (int k = 0; k < ga.ncombo; ++k) allpow2 = allpow2 && ga.pow2[k];
     switch (ga.ncombo) {
-#define MDLG_IG_CASE(K) case K: return launch_idealgas_nc<K>(ga, n, pos, vel, counts, s);
+#define MDLG_IG_CASE(K) case K: return allpow2 ? launch_idealgas_nc<K, true>(ga, n, pos, vel, counts, s) \
+                                               : launch_idealgas_nc<K, false>(ga, n, pos, vel, counts, s);
         MDLG_IG_CASE(1) MDLG_IG_CASE(2) MDLG_IG_CASE(3) MDLG_IG_CASE(4) MDLG_IG_CASE(5)
         MDLG_IG_CASE(6) MDLG_IG_CASE(7) MDLG_IG_CASE(8) MDLG_IG_CASE(9) MDLG_IG_CASE(10)
         MDLG_IG_CASE(11) MDLG_IG_CASE(12) MDLG_IG_CASE(13) MDLG_IG_CASE(14) MDLG_IG_CASE(15)

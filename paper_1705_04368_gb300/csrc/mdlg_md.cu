@@ -70,10 +70,11 @@ struct PairAcc {
     float fx, fy, pe, vir;
 };
 
-// One pair term of the truncated-shifted Lennard-Jones interaction:
+// One pair term of the Lennard-Jones interaction (SF: the shifted-force variant,
+// a compile-time choice so the truncated-shifted step carries none of its code):
 // force on i from j is 24 eps (2 s^12 - s^6) / r^2 (x_i - x_j), s = sigma / r;
 // pe adds V(r) - V(rc), vir adds r . F (both halved later: each pair is seen twice).
-template <bool STATS>
+template <bool STATS, bool SF>
 __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy, PairAcc &acc) {
     const float r2 = fmaf(dx, dx, dy * dy);
     if (r2 < a.rc2) {
@@ -82,7 +83,7 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
         const float sr6 = sr2 * sr2 * sr2;
         float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
         float ir = 0.f;
-        if (a.potential == 2) {          // shifted force: subtract F(rc) along the pair
+        if (SF) {          // shifted force: subtract F(rc) along the pair
             ir = rsqrtf(r2);
             fs -= a.fc * ir;
         }
@@ -90,7 +91,7 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
         acc.fy = fmaf(fs, dy, acc.fy);
         if (STATS) {
             float e = a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
-            if (a.potential == 2) e = fmaf(a.fc, r2 * ir - a.rc, e);   // + (r - rc) F(rc)
+            if (SF) e = fmaf(a.fc, r2 * ir - a.rc, e);   // + (r - rc) F(rc)
             acc.pe += e;
             acc.vir = fmaf(fs, r2, acc.vir);
         }
@@ -100,7 +101,7 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
 // The same term without a branch: evaluated for every list slot and masked, so
 // the lanes of a warp never diverge inside a batch.  Far or empty slots give a
 // tiny finite r^-2, multiplied by a zero mask.
-template <bool STATS>
+template <bool STATS, bool SF>
 __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, float dy,
                                                  PairAcc &acc) {
     const float r2 = fmaf(dx, dx, dy * dy);
@@ -110,7 +111,7 @@ __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, fl
     const float sr6 = sr2 * sr2 * sr2;
     float fs = a.eps24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
     float ir = 0.f;
-    if (a.potential == 2) {              // shifted force: subtract F(rc) along the pair
+    if (SF) {              // shifted force: subtract F(rc) along the pair
         ir = rsqrtf(r2);
         fs -= a.fc * ir;
     }
@@ -119,7 +120,7 @@ __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, fl
     acc.fy = fmaf(fs, dy, acc.fy);
     if (STATS) {
         float e = a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
-        if (a.potential == 2) e = fmaf(a.fc, r2 * ir - a.rc, e);       // + (r - rc) F(rc)
+        if (SF) e = fmaf(a.fc, r2 * ir - a.rc, e);       // + (r - rc) F(rc)
         acc.pe = fmaf(on, e, acc.pe);
         acc.vir = fmaf(fs, r2, acc.vir);
     }
@@ -132,7 +133,7 @@ __device__ __forceinline__ float cell_shift(int32_t c, int off, int32_t nc, int3
 }
 
 // All pairs through the cell stencil (always correct for the current bound D).
-template <bool STATS>
+template <bool STATS, bool SF>
 __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo, const int32_t *cs,
                                              int64_t i, int32_t cx, int32_t cy, float2 p, int lox,
                                              int hix, int loy, int hiy, PairAcc &acc) {
@@ -148,7 +149,7 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
                 if (j == i) continue;
                 const float2 q = __ldg(a.cl_in + j);
                 // x_i - x_j = (cl_i - cl_j) - (origin_j - origin_i)
-                pair_term<STATS>(a, (p.x - q.x) - odx, (p.y - q.y) - ody, acc);
+                pair_term<STATS, SF>(a, (p.x - q.x) - odx, (p.y - q.y) - ody, acc);
             }
         }
     }
@@ -166,7 +167,7 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
 // a float by the exponent trick (2^23 + code, minus 2^23: exact, no
 // conversion instruction); at the periodic edges and next to the wider last
 // cell it is looked up from the four per-particle shifts.
-template <bool STATS, bool REGULAR>
+template <bool STATS, bool REGULAR, bool SF>
 __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
                                             float sxm, float sxp, float sym, float syp,
                                             PairAcc &acc) {
@@ -194,14 +195,14 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
                 sx = ox == 0u ? sxm : (ox == 2u ? sxp : (ox == 3u ? 2.0f * w : 0.0f));
                 sy = oy == 0u ? sym : (oy == 2u ? syp : (oy == 3u ? 2.0f * w : 0.0f));
             }
-            pair_term_masked<STATS>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
+            pair_term_masked<STATS, SF>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
         }
     }
 }
 
 // B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
 // per system); otherwise one system described by a.geo.
-template <int MODE, bool STATS, bool B>
+template <int MODE, bool STATS, bool B, bool SF>
 __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
@@ -235,14 +236,14 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
                 const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
                 const float w = a.cell_w;
                 if (sxm == -w && sxp == w && sym == -w && syp == w)
-                    forces_list<STATS, true>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
+                    forces_list<STATS, true, SF>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
                 else
-                    forces_list<STATS, false>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
+                    forces_list<STATS, false, SF>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
             } else {
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);
                 stencil(R, geo.nc[1], loy, hiy);
-                forces_cells<STATS>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
+                forces_cells<STATS, SF>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
                                     hiy, acc);
             }
         }
@@ -714,15 +715,15 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 // Blocks of the largest step launch (a batch launches 128-thread blocks).
 int64_t step_blocks(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
-template <bool B>
+template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
     if (mode == kModeStep) {
-        if (a.stats) k_step<kModeStep, true, B><<<grid, block, 0, s>>>(a);
-        else k_step<kModeStep, false, B><<<grid, block, 0, s>>>(a);
+        if (a.stats) k_step<kModeStep, true, B, SF><<<grid, block, 0, s>>>(a);
+        else k_step<kModeStep, false, B, SF><<<grid, block, 0, s>>>(a);
     } else if (mode == kModeInit) {
-        k_step<kModeInit, true, B><<<grid, block, 0, s>>>(a);
+        k_step<kModeInit, true, B, SF><<<grid, block, 0, s>>>(a);
     } else {
-        k_step<kModeSync, true, B><<<grid, block, 0, s>>>(a);
+        k_step<kModeSync, true, B, SF><<<grid, block, 0, s>>>(a);
     }
 }
 
@@ -731,8 +732,14 @@ cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
     const int64_t blocks = (a.n + threads - 1) / threads;
     if (blocks < 1) return cudaSuccess;
     const dim3 grid((unsigned)blocks), block(threads);
-    if (a.batch.sys) launch_step_t<true>(a, mode, grid, block, s);
-    else launch_step_t<false>(a, mode, grid, block, s);
+    const bool sf = a.potential == 2;
+    if (a.batch.sys) {
+        if (sf) launch_step_t<true, true>(a, mode, grid, block, s);
+        else launch_step_t<true, false>(a, mode, grid, block, s);
+    } else {
+        if (sf) launch_step_t<false, true>(a, mode, grid, block, s);
+        else launch_step_t<false, false>(a, mode, grid, block, s);
+    }
     return cudaGetLastError();
 }
 

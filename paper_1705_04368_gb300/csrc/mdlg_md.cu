@@ -230,15 +230,16 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
             const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
             if (cnt <= a.cap) {
-                const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                const float w = a.cell_w;
-                if (sxm == -w && sxp == w && sym == -w && syp == w)
-                    forces_list<STATS, true, SF>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
-                else
+                // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
+                if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
+                    forces_list<STATS, true, SF>(a, i, p, cnt, 0.f, 0.f, 0.f, 0.f, acc);
+                } else {
+                    const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                    const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                    const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                    const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
                     forces_list<STATS, false, SF>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
+                }
             } else {
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);

@@ -587,7 +587,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     }
     if (p.potential != MDLG_POT_NONE) {
         // Verlet list of radius = the MD cell width (rc + the whole skin);
-        // capacity three times the mean count at the highest density, plus 16
+        // capacity three times the mean count at the highest density, plus 16,
+        // a multiple of 4 (the step kernel's list batch: lists are padded to it)
         c->list_radius = (float)(g.k * p.grid);
         const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(AdjArgs a) {
                 const float sym = (float)wrap_half((wrap_mod(cy - 1, geo.nc[1]) - cy) * geo.k, geo.lg[1]) * geo.g;
                 const float syp = (float)wrap_half((wrap_mod(cy + 1, geo.nc[1]) - cy) * geo.k, geo.lg[1]) * geo.g;
                 for (int t = 0; t < cnt; ++t) {
-                    const uint32_t ent = a.nbr[(int64_t)t * a.n + i];
+                    const uint32_t ent = a.nbr[((int64_t)(t >> 2) * a.n + i) * 4 + (t & 3)];
                     const int32_t j = (int32_t)(ent & 0x0fffffffu);
                     const uint32_t ox = (ent >> 28) & 3u, oy = ent >> 30;
                     const float sx = ox == 0u ? sxm : (ox == 2u ? sxp : 0.0f);

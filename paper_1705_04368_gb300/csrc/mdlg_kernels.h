@@ -158,7 +158,7 @@ struct StepArgs {
     float cell_w;               // k g: narrowest MD cell width
     float rc;
     float round_margin;         // per-step slack added to the displacement bound
-    const uint32_t *nbr;        // Verlet list, column-major (cap x n), or null
+    const uint32_t *nbr;        // Verlet list in batches of four (cap x n), or null
     const int32_t *ncount;      // entries per particle (cap + 1: overflowed)
     int32_t cap;                // list capacity per particle
     float list_skin;            // list radius - rc

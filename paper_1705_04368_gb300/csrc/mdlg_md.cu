@@ -156,12 +156,14 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
 }
 
 // Pairs from the Verlet list built at the last sort: entry t of particle i is
-// nbr[t n + i] = j | (ox + 1) << 28 | (oy + 1) << 30 with (ox, oy) the offset of
-// j's cell from i's cell.  Each list is padded to a multiple of kListBatch with
-// entries i | 3 << 28 | 3 << 30: the particle itself two cell widths away on
-// both axes, always beyond rc (cells are wider than rc), so every load is
-// unconditional and a padding slot adds zero.  Entries are fetched kListBatch
-// at a time so that their loads (and the dependent position loads) overlap.
+// nbr[4 (floor(t/4) n + i) + t mod 4] = j | (ox + 1) << 28 | (oy + 1) << 30 with
+// (ox, oy) the offset of j's cell from i's cell, so that each batch of four
+// entries of a particle is one 16-byte load and a warp's batches are adjacent.
+// Each list is padded to a multiple of kListBatch with entries
+// i | 3 << 28 | 3 << 30: the particle itself two cell widths away on both axes,
+// always beyond rc (cells are wider than rc), so every load is unconditional
+// and a padding slot adds zero.  The position loads of a batch are issued
+// together so that they overlap.
 // For a particle whose neighbouring cells are all full-width and unwrapped
 // (REGULAR) the origin shift is (code - 1) w, with the 2-bit code turned into
 // a float by the exponent trick (2^23 + code, minus 2^23: exact, no
@@ -171,14 +173,13 @@ template <bool STATS, bool REGULAR, bool SF>
 __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
                                             float sxm, float sxp, float sym, float syp,
                                             PairAcc &acc) {
-    const uint32_t *e = a.nbr + i;
+    const uint4 *e = reinterpret_cast<const uint4 *>(a.nbr) + i;
     const int64_t n = a.n;
     const float w = a.cell_w;
-    const int npad = (cnt + kListBatch - 1) & ~(kListBatch - 1);
-    for (int t0 = 0; t0 < npad; t0 += kListBatch) {
-        uint32_t ent[kListBatch];
-#pragma unroll
-        for (int u = 0; u < kListBatch; ++u) ent[u] = __ldg(e + (int64_t)(t0 + u) * n);
+    const int nb = (cnt + kListBatch - 1) / kListBatch;
+    for (int b = 0; b < nb; ++b) {
+        const uint4 e4 = __ldg(e + (int64_t)b * n);
+        const uint32_t ent[kListBatch] = {e4.x, e4.y, e4.z, e4.w};
         float2 q[kListBatch];
 #pragma unroll
         for (int u = 0; u < kListBatch; ++u) q[u] = __ldg(a.cl_in + (ent[u] & 0x0fffffffu));
@@ -516,8 +517,9 @@ __global__ void k_sort_scatter(SortArgs a) {
 // Verlet list of the freshly sorted state: every j != i closer than the list
 // radius, found in the 3 x 3 cell stencil (cells are at least that wide and
 // every particle is inside its cell).  Candidates are fetched four at a time
-// (predicated) so their loads overlap.  Column-major: entry t of particle i at
-// nbr[t n + i].  A particle with more than `cap` entries stores cap + 1 as its
+// (predicated) so their loads overlap.  Entry t of particle i is written to
+// nbr[4 (floor(t/4) n + i) + t mod 4], padded to a multiple of four (see
+// forces_list).  A particle with more than `cap` entries stores cap + 1 as its
 // count and is handled through the cell stencil by the step kernel.
 template <bool B>
 __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
@@ -598,12 +600,17 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                     }
                 }
             }
-            const int keep = cnt < a.cap ? cnt : a.cap;
-            for (int t = 0; t < keep; ++t) a.nbr[(int64_t)t * a.n + i] = s_ent[t * nt + threadIdx.x];
-            // padding to a multiple of the step kernel's batch (cap is a multiple of it)
+            // batches of four entries, padded (cap is a multiple of the batch)
             if (cnt <= a.cap) {
-                const int npad = (cnt + kListBatch - 1) & ~(kListBatch - 1);
-                for (int t = cnt; t < npad; ++t) a.nbr[(int64_t)t * a.n + i] = (uint32_t)i | 0xf0000000u;
+                const uint32_t pad = (uint32_t)i | 0xf0000000u;
+                uint4 *out = reinterpret_cast<uint4 *>(a.nbr) + i;
+                for (int t = 0; t < cnt; t += kListBatch) {
+                    uint32_t b[kListBatch];
+#pragma unroll
+                    for (int u = 0; u < kListBatch; ++u)
+                        b[u] = t + u < cnt ? s_ent[(t + u) * nt + threadIdx.x] : pad;
+                    out[(int64_t)(t / kListBatch) * a.n] = make_uint4(b[0], b[1], b[2], b[3]);
+                }
             }
             a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
         }

@@ -592,7 +592,7 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         c->list_radius = (float)(g.k * p.grid);
         const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
-        if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x cap words of shared memory
+        if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x (cap + 1) words of shared memory
         if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
             return fail(rc);
     }

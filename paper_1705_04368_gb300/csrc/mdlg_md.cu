@@ -517,15 +517,19 @@ __global__ void k_sort_scatter(SortArgs a) {
 // Verlet list of the freshly sorted state: every j != i closer than the list
 // radius, found in the 3 x 3 cell stencil (cells are at least that wide and
 // every particle is inside its cell).  Candidates are fetched four at a time
-// (predicated) so their loads overlap.  Entry t of particle i is written to
-// nbr[4 (floor(t/4) n + i) + t mod 4], padded to a multiple of four (see
-// forces_list).  A particle with more than `cap` entries stores cap + 1 as its
-// count and is handled through the cell stencil by the step kernel.
+// (predicated) so their loads overlap.  Every candidate's entry is written to
+// the next free staging slot and the count advances only on a hit, so the
+// lanes of a warp do not diverge over the test (staging holds cap + 1 slots per
+// thread: entries past the capacity all land in the spare one, and such a list
+// is not used).  Entry t of particle i is
+// written to nbr[4 (floor(t/4) n + i) + t mod 4], padded to a multiple of four
+// (see forces_list).  A particle with more than `cap` entries stores cap + 1 as
+// its count and is handled through the cell stencil by the step kernel.
 template <bool B>
 __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
     // entries are staged in shared memory and written after the search, so
     // that no global store precedes a candidate load (see k_bin_state)
-    extern __shared__ uint32_t s_ent[];          // blockDim.x x cap, column-major
+    extern __shared__ uint32_t s_ent[];          // blockDim.x x (cap + 1), column-major
     const int nt = blockDim.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
@@ -539,6 +543,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
             const int32_t *cs = a.cell_start + sv.cell0;
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
             const float2 p = a.cl_out[i];
+            const int last = a.cap;   // spare staging slot: every entry past the capacity
             // x offsets of the three columns (wrapped at the periodic edges)
             const float sxm = (float)wrap_half((wrap_mod(cx - 1, geo.nc[0]) - cx) * geo.k, geo.lg[0]) * geo.g;
             const float sxp = (float)wrap_half((wrap_mod(cx + 1, geo.nc[0]) - cx) * geo.k, geo.lg[0]) * geo.g;
@@ -566,12 +571,10 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const int ox = (j >= m1) + (j >= m2) - 1;
                             const float odx = ox < 0 ? sxm : (ox > 0 ? sxp : 0.0f);
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
-                                if (cnt < a.cap)
-                                    s_ent[cnt * nt + threadIdx.x] =
-                                        (uint32_t)j | ((uint32_t)(ox + 1) << 28) | ycode;
-                                ++cnt;
-                            }
+                            const bool hit = j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            s_ent[min(cnt, last) * nt + threadIdx.x] =
+                                (uint32_t)j | ((uint32_t)(ox + 1) << 28) | ycode;
+                            cnt += hit;
                         }
                     }
                     continue;
@@ -592,10 +595,9 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                         for (int u = 0; u < 4; ++u) {
                             const int32_t j = b + u;
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            if (j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2) {
-                                if (cnt < a.cap) s_ent[cnt * nt + threadIdx.x] = (uint32_t)j | code;
-                                ++cnt;
-                            }
+                            const bool hit = j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            s_ent[min(cnt, last) * nt + threadIdx.x] = (uint32_t)j | code;
+                            cnt += hit;
                         }
                     }
                 }
@@ -766,8 +768,8 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
     k_sort_scatter<B><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     if (a.nbr) {
-        const int nt = (size_t)kNlistThreads * a.cap * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
-        const size_t smem = sizeof(uint32_t) * (size_t)nt * a.cap;
+        const int nt = (size_t)kNlistThreads * (a.cap + 1) * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
+        const size_t smem = sizeof(uint32_t) * (size_t)nt * (a.cap + 1);
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(k_nlist<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);

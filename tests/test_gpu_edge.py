@@ -1,7 +1,8 @@
 """Degenerate and boundary cases of the MD path against the oracle: one
 particle, one pair, the smallest periodic box (three neighbour cells per axis,
 every neighbour cell a periodic image), a list that overflows its capacity
-(cell-stencil fallback), and the largest velocity window."""
+(cell-stencil fallback), lists exactly at their capacity, and the largest
+velocity window."""
 import numpy as np
 import pytest
 
@@ -68,6 +69,36 @@ def test_dense_lists_overflow_to_cell_stencil(cuda):
     v0 = np.concatenate([np.zeros((g.shape[0], 2)), vo[far][:2500]])
     p = m.Params(n=n, box=L, dx=4.0)
     with m.Simulation(p, x0, v0) as s:
+        _, _, f = s.get_state(want_force=True)
+        st, _, _ = s.stats()
+    f_ref, scale, _, _ = oracle.lj_forces(x0, (L, L))
+    assert np.all(np.abs(f - f_ref).max(axis=1) <= 1e-5 * np.maximum(scale, 1e-3))
+    assert st["status"] == 0
+
+
+def test_lists_at_and_around_capacity(cuda):
+    # rectangular patches of spacings (0.80 + 0.02 k, 0.98 - 0.02 k) give list
+    # lengths (pairs closer than the list radius, the MD cell width) on both
+    # sides of the capacity, including lists exactly full: those are used, the
+    # longer ones overflow to the cell stencil; every force matches the oracle
+    L = 128.0
+    pts = []
+    for k in range(10):
+        sp = np.array([0.80 + 0.02 * k, 0.98 - 0.02 * k])
+        g = np.stack(np.meshgrid(np.arange(9), np.arange(9)), -1).reshape(-1, 2) * sp
+        pts.append(g + np.array([4.0 + 12.0 * k, 20.0]))
+    x0 = np.round(np.concatenate(pts) / Q) * Q
+    n = x0.shape[0]
+    p = m.Params(n=n, box=L, dx=4.0)
+    rl = p.grid * np.ceil((p.rcut + p.skin) / p.grid)
+    mean = n / (L * L) * np.pi * rl * rl
+    cap = int(np.ceil((3.0 * mean + 16.0) / 4.0)) * 4
+    d2 = ((x0[:, None, :] - x0[None, :, :]) ** 2).sum(-1)   # patches are far from the box edges
+    np.fill_diagonal(d2, np.inf)
+    assert np.abs(d2 - rl * rl).min() > 1e-3                 # no pair near the list radius
+    counts = (d2 < rl * rl).sum(1)
+    assert {cap - 1, cap, cap + 1} <= set(counts.tolist()), (cap, sorted(set(counts.tolist())))
+    with m.Simulation(p, x0, np.zeros_like(x0)) as s:
         _, _, f = s.get_state(want_force=True)
         st, _, _ = s.stats()
     f_ref, scale, _, _ = oracle.lj_forces(x0, (L, L))

@@ -67,7 +67,10 @@ __global__ void k_bin_snapshots(LatticeArgs la, int64_t n, const int2 *__restric
 // The pair count is a template parameter, so the loop is unrolled and every
 // pair's parameters are compile-time offsets into the argument block; when
 // every dx is a power of two (ALLPOW2) the division path is not compiled in.
-// Multiplying by 1/dx equals dividing by dx when dx is a power of two.
+// Multiplying by 1/dx equals dividing by dx when dx is a power of two.  The
+// rest velocity, where most decisions of a short coarse step land, is counted
+// per pair in registers and added to the block histogram once per thread; the
+// other bins take one shared atomic per decision.
 template <int NC, bool ALLPOW2>
 __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restrict__ pos,
                                const float2 *__restrict__ vel, unsigned long long *counts) {
@@ -76,6 +79,9 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
     const int center = ga.vmax * w + ga.vmax;
     for (int b = threadIdx.x; b < q1 * NC; b += blockDim.x) sh[b] = 0;
     __syncthreads();
+    uint32_t rest[NC];   // rest-velocity counts kept in registers, added once per thread
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rest[k] = 0u;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t j = base + threadIdx.x;
@@ -105,8 +111,16 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
             const float qy = pow2 ? __fmul_rn(yn, inv) : __fdiv_rn(yn, dx);
             const int32_t vx = ceil_small(qx) - 1 - c0x;
             const int32_t vy = ceil_small(qy) - 1 - c0y;
-            hist_add(sh + k * q1, vel_index(vx, vy, ga.vmax), center, act);
+            const int32_t bin = vel_index(vx, vy, ga.vmax);
+            rest[k] += (act && bin == center) ? 1u : 0u;
+            if (act && bin != center) atomicAdd(&sh[k * q1 + bin], 1u);
         }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        uint32_t r = rest[k];
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((threadIdx.x & 31) == 0 && r) atomicAdd(&sh[k * q1 + center], r);
     }
     __syncthreads();
     for (int k = 0; k < NC; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)k * q1);

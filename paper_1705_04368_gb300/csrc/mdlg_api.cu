@@ -520,24 +520,6 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     // rounding slack of one drift update: a few ulps of the largest offset
     c->round_margin = (float)(4.0 * std::ldexp(1.0, -23) * (2.0 * g.k * p.grid));
 
-    // re-sort interval: half the skin covered at 1.15x the fastest initial speed (if the
-    // bound tracked on the device grows past it earlier, the step kernel uses the
-    // cell stencil for the remaining steps, so a late sort costs time, not accuracy)
-    double vmax0 = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        const double s2 = v0[2 * i] * v0[2 * i] + v0[2 * i + 1] * v0[2 * i + 1];
-        if (s2 > vmax0) vmax0 = s2;
-    }
-    vmax0 = std::sqrt(vmax0);
-    if (p.sort_every > 0) {
-        c->sort_every = p.sort_every;
-    } else {
-        const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
-        const double v = std::fmax(1.15 * vmax0, 1e-12);
-        double k = std::floor(0.5 * skin_eff / (v * p.dt));
-        c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
-    }
-
     int rc = MDLG_OK;
     auto fail = [&](int code) {
         free_all(c);
@@ -661,6 +643,25 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     // every lag starts from the lattice cells at t = 0
     StateBinArgs b = bin_args(c, (1u << p.nlags) - 1u);
     if ((rc = chk(launch_bin_seed(b, s)))) return fail(rc);
+    // re-sort interval (nothing above depends on it, so this host pass over the
+    // velocities overlaps the device work just queued): half the skin covered at
+    // 1.15x the fastest initial speed.  If the bound tracked on the device grows
+    // past it earlier, the step kernel uses the cell stencil for the remaining
+    // steps, so a late sort costs time, not accuracy.
+    if (p.sort_every > 0) {
+        c->sort_every = p.sort_every;
+    } else {
+        double vmax0 = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double s2 = v0[2 * i] * v0[2 * i] + v0[2 * i + 1] * v0[2 * i + 1];
+            if (s2 > vmax0) vmax0 = s2;
+        }
+        vmax0 = std::sqrt(vmax0);
+        const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
+        const double v = std::fmax(1.15 * vmax0, 1e-12);
+        double k = std::floor(0.5 * skin_eff / (v * p.dt));
+        c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
+    }
     if ((rc = chk(cudaStreamSynchronize(s)))) return fail(rc);
     int32_t status = 0;
     if ((rc = read_status(c, &status, nullptr))) return fail(rc);

@@ -447,6 +447,7 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
             params->lattice_u[1] != 0.0)
             return MDLG_EINVAL;
         ntot = 0;
+        int64_t slots = 0;
         for (int32_t k = 0; k < nsys; ++k) {
             mdlg_params q = *params;
             q.n = ns[k];
@@ -454,8 +455,10 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
             q.box[1] = boxes[2 * k + 1];
             MDLG_TRY(validate(&q));
             ntot += ns[k];
+            slots += (ns[k] + kChunk - 1) / kChunk * kChunk;
         }
-        if (ntot >= (1LL << 28)) return MDLG_EINVAL;
+        // Verlet-list entries carry the slot index (padding included) in 28 bits
+        if (ntot >= (1LL << 28) || slots >= (1LL << 28)) return MDLG_EINVAL;
     } else if (nsys < 0) {
         return MDLG_EINVAL;
     } else {

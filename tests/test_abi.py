@@ -142,6 +142,18 @@ def test_batch_rejects_single_system_analyses():
         assert rc == -1 and not h.value, kw
 
 
+def test_batch_rejects_slot_count_past_list_index_range():
+    # list entries hold a slot index in 28 bits; systems are padded to whole
+    # 128-slot chunks, so 2^28 - 64 particles in two systems take 2^28 slots
+    x = np.full((1, 2), 1.0)
+    ns = np.array([1 << 27, (1 << 27) - 64], np.int64)
+    boxes = np.array([[16.0, 16.0], [16.0, 16.0]])
+    h = ctypes.c_void_p()
+    rc = m.lib().mdlg_create_batch(ctypes.byref(_params()), 2, ns.ctypes.data, boxes.ctypes.data,
+                                   x.ctypes.data, x.ctypes.data, None, None, ctypes.byref(h))
+    assert rc == -1 and not h.value
+
+
 def test_get_collision_rejects_null_context():
     assert m.lib().mdlg_get_collision(None, None, None, None) == -1
 

@@ -377,13 +377,18 @@ int sync_stats(mdlg_ctx *c, bool with_force) {
     return MDLG_OK;
 }
 
-int read_status(mdlg_ctx *c, int32_t *status, double *stats) {
+int read_status(mdlg_ctx *c, int32_t *status, double *stats, double *vmax0 = nullptr) {
     Control h{};
     MDLG_TRY(cuda_err(cudaMemcpyAsync(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
                                       c->stream)));
     MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
     if (status) *status = h.status;
     if (stats) memcpy(stats, h.stats, sizeof(h.stats));
+    if (vmax0) {
+        double s2;
+        memcpy(&s2, &h.vmax0_bits, sizeof(s2));
+        *vmax0 = std::sqrt(s2);
+    }
     return MDLG_OK;
 }
 
@@ -646,29 +651,23 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     // every lag starts from the lattice cells at t = 0
     StateBinArgs b = bin_args(c, (1u << p.nlags) - 1u);
     if ((rc = chk(launch_bin_seed(b, s)))) return fail(rc);
-    // re-sort interval (nothing above depends on it, so this host pass over the
-    // velocities overlaps the device work just queued): half the skin covered at
-    // 1.15x the fastest initial speed.  If the bound tracked on the device grows
+    if ((rc = chk(cudaStreamSynchronize(s)))) return fail(rc);
+    int32_t status = 0;
+    double vmax0 = 0.0;   // fastest uploaded speed (reduced by the upload kernel)
+    if ((rc = read_status(c, &status, nullptr, &vmax0))) return fail(rc);
+    if (status) return fail(status);
+    // re-sort interval: half the skin covered at 1.15x the fastest initial speed
+    // (nothing above depends on it).  If the bound tracked on the device grows
     // past it earlier, the step kernel uses the cell stencil for the remaining
     // steps, so a late sort costs time, not accuracy.
     if (p.sort_every > 0) {
         c->sort_every = p.sort_every;
     } else {
-        double vmax0 = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            const double s2 = v0[2 * i] * v0[2 * i] + v0[2 * i + 1] * v0[2 * i + 1];
-            if (s2 > vmax0) vmax0 = s2;
-        }
-        vmax0 = std::sqrt(vmax0);
         const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
         const double v = std::fmax(1.15 * vmax0, 1e-12);
         double k = std::floor(0.5 * skin_eff / (v * p.dt));
         c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
     }
-    if ((rc = chk(cudaStreamSynchronize(s)))) return fail(rc);
-    int32_t status = 0;
-    if ((rc = read_status(c, &status, nullptr))) return fail(rc);
-    if (status) return fail(status);
     *out = c;
     return MDLG_OK;
 }

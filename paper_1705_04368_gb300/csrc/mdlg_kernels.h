@@ -134,6 +134,7 @@ struct Control {
     uint32_t done;             // blocks finished in the running launch
     int32_t status;            // first device-side error (MDLG_E* value) or 0
     double stats[8];           // ke, pe, virial, px, py of the last stats launch
+    unsigned long long vmax0_bits;   // max |v|^2 of the uploaded state (FP64 bits; >= 0)
 };
 
 enum StepMode : int32_t {

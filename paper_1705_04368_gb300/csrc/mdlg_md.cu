@@ -621,9 +621,26 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
 
 // ---- upload / download conversions ----------------------------------------
 
+// Largest |v|^2 of the block's uploaded velocities into ctl->vmax0_bits: the
+// bits of non-negative doubles order like the values, so an integer max is
+// exact and independent of the order of the blocks.  Every thread calls it.
+__device__ void block_max_speed2(double s2, Control *ctl) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 = fmax(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        atomicMax(&ctl->vmax0_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 __global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, uint32_t *cell,
                        float2 *cl, float2 *vel, int32_t *pid, Control *ctl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double s2 = 0.0;   // largest |v|^2 seen by this thread
     const double g = geo.g, inv_g = geo.inv_g;   // g a power of two: x * (1/g) is exact
     const double L0 = (double)geo.lg[0] * g, L1 = (double)geo.lg[1] * g;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -644,7 +661,9 @@ __global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, ui
                             (float)(py - (double)(cy * geo.k) * g));
         vel[i] = make_float2((float)v[2 * i], (float)v[2 * i + 1]);
         pid[i] = (int32_t)i;
+        s2 = fmax(s2, __dadd_rn(__dmul_rn(v[2 * i], v[2 * i]), __dmul_rn(v[2 * i + 1], v[2 * i + 1])));
     }
+    block_max_speed2(s2, ctl);
 }
 
 // Batched upload: slot t of system s holds particle q0 + (t - p0) of the
@@ -652,6 +671,7 @@ __global__ void k_pack(Geom geo, int64_t n, const double *x, const double *v, ui
 __global__ void k_pack_batch(Batch b, int64_t slots, const double *x, const double *v,
                              uint32_t *cell, float2 *cl, float2 *vel, int32_t *pid, Control *ctl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double s2 = 0.0;   // largest |v|^2 seen by this thread
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < slots; t += stride) {
         const SysInfo &si = b.sys[b.chunk_sys[t / kChunk]];
         const Geom &geo = si.geo;
@@ -683,7 +703,9 @@ __global__ void k_pack_batch(Batch b, int64_t slots, const double *x, const doub
                             (float)(py - (double)(cy * geo.k) * g));
         vel[t] = make_float2((float)v[2 * q], (float)v[2 * q + 1]);
         pid[t] = (int32_t)q;
+        s2 = fmax(s2, __dadd_rn(__dmul_rn(v[2 * q], v[2 * q]), __dmul_rn(v[2 * q + 1], v[2 * q + 1])));
     }
+    block_max_speed2(s2, ctl);
 }
 
 template <bool B>

@@ -41,6 +41,7 @@ COLLISION_BYTES_PER_SITE_Q = 12   # read n_i at x and at x + v_i, write Xi_i: 3 
 COLLISION_BYTES_PER_SITE = 12     # dmass + dmom int32
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+SMSP_PER_SM = 4
 
 
 def _peaks():
@@ -53,9 +54,10 @@ def _peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-def _traffic_record(kernel: str):
-    """dram bytes per particle of a kernel from profiles/traffic.txt, if the
-    kernel source has not changed since that capture (else None)."""
+def _traffic_record(kernel: str, key: str = "dram_bytes_per_particle"):
+    """A per-particle counter of a kernel (DRAM bytes, warp instructions) from
+    profiles/traffic.txt, if the kernel source has not changed since that
+    capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         import hashlib
@@ -63,8 +65,8 @@ def _traffic_record(kernel: str):
         sha = hashlib.sha256(src).hexdigest()[:16]
         for ln in open(path):
             kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
-            if kv.get("kernel") == kernel and kv.get("src_sha") == sha:
-                return float(kv["dram_bytes_per_particle"])
+            if kv.get("kernel") == kernel and kv.get("src_sha") == sha and key in kv:
+                return float(kv[key])
     except Exception:
         pass
     return None
@@ -257,6 +259,9 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     achieved_tf = flops / avg_step_s / 1e12
     tpp = _traffic_record("k_step")
+    ipp = _traffic_record("k_step", "warp_inst_per_particle")
+    # instruction issue: one warp instruction per clock per SM sub-partition
+    issue_peak = SM_COUNT * SMSP_PER_SM * sm_max_mhz * 1e6
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
                 "traffic": (tpp * c.n) if tpp is not None else None,
@@ -265,7 +270,15 @@ def run_ours(args, rank, world, local_rank):
                 "avg_launch_us": avg_step_s * 1e6,
                 "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
                          "frac": achieved_tf / fp32_peak,
-                         "flops_per_particle": 18.0 * n_in + 8.0}}
+                         "flops_per_particle": 18.0 * n_in + 8.0},
+                "issue": None if ipp is None else {
+                    "achieved_warp_inst_per_s": ipp * c.n / avg_step_s,
+                    "peak_warp_inst_per_s": issue_peak,
+                    "frac": ipp * c.n / avg_step_s / issue_peak,
+                    "warp_inst_per_particle": ipp,
+                    "what": "ncu warp-instruction count of one launch (profiles/traffic.txt) over "
+                            "the launch time measured here; peak = one issue per clock per SM "
+                            "sub-partition at the maximum SM clock"}}
     kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms if ms else None}
                for k, v in prof.items() if v[1]}
     launches = prof["step"][1] + prof["sort"][1] + prof["bin"][1] + prof["sync"][1]

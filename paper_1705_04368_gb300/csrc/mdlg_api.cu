@@ -43,7 +43,6 @@ struct mdlg_ctx {
     uint32_t *key = nullptr;
     int32_t *slot = nullptr, *count = nullptr, *block_sums = nullptr;
     unsigned long long *entry = nullptr;
-    long long *partials = nullptr;
     Control *ctl = nullptr;
     unsigned long long *counts = nullptr;   // nlags x q1
     uint32_t *site_n = nullptr, *site_counts = nullptr;
@@ -263,7 +262,6 @@ StepArgs step_args(mdlg_ctx *c) {
     a.round_margin = c->round_margin;
     a.potential = c->p.potential == MDLG_POT_LJ_TS ? 1 : (c->p.potential == MDLG_POT_LJ_SF ? 2 : 0);
     a.fc = (float)lj_fc(c->p);
-    a.partials = c->partials;
     a.ctl = c->ctl;
     a.nbr = c->nbr;
     a.ncount = c->ncount;
@@ -552,7 +550,6 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
         (rc = alloc_n(c, &c->count, (size_t)c->ncells)) ||
         (rc = alloc_n(c, &c->block_sums, (size_t)nb)) || (rc = alloc_n(c, &c->entry, N)) ||
-        (rc = alloc_n(c, &c->partials, (size_t)mdlg::step_blocks(c->slots) * 5)) ||
         (rc = alloc_n(c, &c->ctl, 1)) ||
         (rc = alloc_n(c, &c->counts, (size_t)nsb * p.nlags * c->q1)) ||
         (rc = alloc_n(c, &c->vsync, N)) || (rc = alloc_n(c, &c->fsync, N)) ||

@@ -135,6 +135,7 @@ struct Control {
     int32_t status;            // first device-side error (MDLG_E* value) or 0
     double stats[8];           // ke, pe, virial, px, py of the last stats launch
     unsigned long long vmax0_bits;   // max |v|^2 of the uploaded state (FP64 bits; >= 0)
+    long long stats_acc[5];    // fixed-point sums of a running stats launch (zero at rest)
 };
 
 enum StepMode : int32_t {
@@ -165,13 +166,11 @@ struct StepArgs {
     float list_skin;            // list radius - rc
     int32_t potential;          // 0 none, 1 LJ truncated-shifted, 2 LJ shifted-force
     float fc;                   // |F(rc)| (shifted-force subtracts it)
-    int32_t stats;              // 1: FP64 reductions into partials
-    long long *partials;        // gridDim.x x 5 fixed-point block sums
+    int32_t stats;              // 1: FP64 reductions (Control::stats, or per system in a batch)
     Control *ctl;
     Batch batch;
 };
 
-int64_t step_blocks(int64_t n);
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);
 
 struct SortArgs {

@@ -310,11 +310,11 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
             for (int k = 0; k < kStatsN; ++k) {
                 long long t = 0;
                 for (int w = 0; w < kWarps; ++w) t += s_red[w][k];
-                // batched: a block is one chunk of one system; integer sums are
+                // batched: a block is one chunk of one system.  Integer sums are
                 // exact, so the order of these atomics does not matter
-                if (B) atomicAdd((unsigned long long *)&a.batch.stats[sv.sys * kStatsN + k],
-                                 (unsigned long long)t);
-                else a.partials[(size_t)blockIdx.x * kStatsN + k] = t;
+                atomicAdd(B ? (unsigned long long *)&a.batch.stats[sv.sys * kStatsN + k]
+                            : (unsigned long long *)&a.ctl->stats_acc[k],
+                          (unsigned long long)t);
             }
         }
         __threadfence();
@@ -325,16 +325,11 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
     if (!s_last) return;
     // Last block of the launch: every other block has published its results.
     __threadfence();
-    if (STATS && !B) {
-        if (warp == 0) {
-            for (int k = 0; k < kStatsN; ++k) {
-                long long t = 0;
-                for (int b = lane; b < (int)gridDim.x; b += 32)
-                    t += ((volatile long long *)a.partials)[(size_t)b * kStatsN + k];
-                t = warp_sum_ll(t);
-                if (lane == 0) a.ctl->stats[k] = (double)t * kFixInv;
-            }
-        }
+    if (STATS && !B && threadIdx.x < kStatsN) {
+        // the launch's totals, and the accumulators back to zero for the next
+        const long long t =
+            (long long)atomicExch((unsigned long long *)&a.ctl->stats_acc[threadIdx.x], 0ull);
+        a.ctl->stats[threadIdx.x] = (double)t * kFixInv;
     }
     if (threadIdx.x == 0) {
         if (MODE == kModeStep) {
@@ -743,9 +738,6 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 }
 
 }  // namespace
-
-// Blocks of the largest step launch (a batch launches 128-thread blocks).
-int64_t step_blocks(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {

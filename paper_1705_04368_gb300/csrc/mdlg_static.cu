@@ -38,7 +38,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Byte offsets of the sub-arrays inside the scratch array.
 struct Layout {
     size_t cell[2], cl[2], vel[2], pid[2], key, slot, entry, count, cell_start, block_sums,
-        partials, ctl, vsync, fsync, total;
+        ctl, vsync, fsync, total;
 };
 
 constexpr Layout make_layout() {
@@ -56,7 +56,6 @@ constexpr Layout make_layout() {
     L.count = o;      o += align256(sizeof(int32_t) * kMaxCells);
     L.cell_start = o; o += align256(sizeof(int32_t) * (kMaxCells + 1));
     L.block_sums = o; o += align256(sizeof(int32_t) * 64);
-    L.partials = o;   o += align256(sizeof(long long) * 5 * ((kMaxN + 31) / 32));
     L.ctl = o;        o += align256(sizeof(Control));
     L.vsync = o;      o += align256(sizeof(float2) * kMaxN);
     L.fsync = o;      o += align256(sizeof(float2) * kMaxN);
@@ -209,7 +208,6 @@ extern "C" int mdlg_forces_static(const mdlg_params *p, const double *x, const d
     a.potential = p->potential == MDLG_POT_LJ_SF ? 2 : 1;
     a.fc = (float)(24.0 * ep * (2.0 * sr6 * sr6 - sr6) / rcut);
     a.stats = 1;
-    a.partials = static_cast<long long *>(at(L.partials));
     a.ctl = ctl;
     a.nbr = nullptr;
     if (launch_step(a, kModeSync, s) != cudaSuccess) return MDLG_ECUDA;

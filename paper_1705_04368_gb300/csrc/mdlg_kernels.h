@@ -116,7 +116,7 @@ struct CollArgs {
     int32_t *dmom;                // C_y*C_x*2, or null
 };
 
-int hist_grid(int64_t n, int threads);
+int hist_grid(int64_t n, int threads, int per_sm = 8);   // blocks: per_sm per SM at most
 cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t *prev,
                                  const int32_t *cur, unsigned long long *counts, uint32_t *ncell,
                                  uint32_t *field, cudaStream_t s);

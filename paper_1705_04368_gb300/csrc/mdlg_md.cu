@@ -100,12 +100,12 @@ __device__ __forceinline__ void pair_term(const StepArgs &a, float dx, float dy,
 
 // The same term without a branch: evaluated for every list slot and masked, so
 // the lanes of a warp never diverge inside a batch.  Far or empty slots give a
-// tiny finite r^-2, multiplied by a zero mask.
+// tiny finite r^-2, replaced by zero (a select, not a product with a mask).
 template <bool STATS, bool SF>
 __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, float dy,
                                                  PairAcc &acc) {
     const float r2 = fmaf(dx, dx, dy * dy);
-    const float on = r2 < a.rc2 ? 1.0f : 0.0f;
+    const bool on = r2 < a.rc2;
     const float ir2 = __fdividef(1.0f, r2);   // hardware reciprocal, <= 2 ulp
     const float sr2 = a.sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
@@ -115,13 +115,13 @@ __device__ __forceinline__ void pair_term_masked(const StepArgs &a, float dx, fl
         ir = rsqrtf(r2);
         fs -= a.fc * ir;
     }
-    fs *= on;
+    fs = on ? fs : 0.0f;
     acc.fx = fmaf(fs, dx, acc.fx);
     acc.fy = fmaf(fs, dy, acc.fy);
     if (STATS) {
         float e = a.eps4 * sr6 * (sr6 - 1.0f) - a.vshift;
         if (SF) e = fmaf(a.fc, r2 * ir - a.rc, e);       // + (r - rc) F(rc)
-        acc.pe = fmaf(on, e, acc.pe);
+        acc.pe += on ? e : 0.0f;
         acc.vir = fmaf(fs, r2, acc.vir);
     }
 }
@@ -165,14 +165,14 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
 // and a padding slot adds zero.  The position loads of a batch are issued
 // together so that they overlap.
 // For a particle whose neighbouring cells are all full-width and unwrapped
-// (REGULAR) the origin shift is (code - 1) w, with the 2-bit code turned into
-// a float by the exponent trick (2^23 + code, minus 2^23: exact, no
-// conversion instruction); at the periodic edges and next to the wider last
-// cell it is looked up from the four per-particle shifts.
+// (REGULAR) the origin shifts are ((c_x - 1) w, (c_y - 1) w), read from a
+// 16-entry shared-memory table indexed by the entry's four code bits; at the
+// periodic edges and next to the wider last cell they are selected from the
+// four per-particle shifts.
 template <bool STATS, bool REGULAR, bool SF>
 __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
-                                            float sxm, float sxp, float sym, float syp,
-                                            PairAcc &acc) {
+                                            const float2 *tab, float sxm, float sxp, float sym,
+                                            float syp, PairAcc &acc) {
     const uint4 *e = reinterpret_cast<const uint4 *>(a.nbr) + i;
     const int64_t n = a.n;
     const float w = a.cell_w;
@@ -187,10 +187,9 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
         for (int u = 0; u < kListBatch; ++u) {
             float sx, sy;
             if (REGULAR) {
-                const float kx = __int_as_float(0x4B000000u | ((ent[u] >> 28) & 3u)) - 8388608.0f;
-                const float ky = __int_as_float(0x4B000000u | (ent[u] >> 30)) - 8388608.0f;
-                sx = fmaf(kx, w, -w);
-                sy = fmaf(ky, w, -w);
+                const float2 o = tab[ent[u] >> 28];
+                sx = o.x;
+                sy = o.y;
             } else {
                 const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
                 sx = ox == 0u ? sxm : (ox == 2u ? sxp : (ox == 3u ? 2.0f * w : 0.0f));
@@ -210,6 +209,13 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
     const Geom &geo = sv.geo;
     const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
     const bool act = i < a.n && (!B || cw != kGhostCell);
+    // origin shifts ((c_x - 1) w, (c_y - 1) w) of the 16 list offset codes of a
+    // regular neighbourhood (code 3: the padding entries' 2 w)
+    __shared__ float2 s_tab[16];
+    if (threadIdx.x < 16)
+        s_tab[threadIdx.x] = make_float2(fmaf((float)(threadIdx.x & 3u), a.cell_w, -a.cell_w),
+                                         fmaf((float)(threadIdx.x >> 2), a.cell_w, -a.cell_w));
+    __syncthreads();
 
     // Neighbour-cell radius for the displacement bound of the input positions.
     const float D = a.ctl->dbound;
@@ -233,13 +239,13 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
             if (cnt <= a.cap) {
                 // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
                 if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
-                    forces_list<STATS, true, SF>(a, i, p, cnt, 0.f, 0.f, 0.f, 0.f, acc);
+                    forces_list<STATS, true, SF>(a, i, p, cnt, s_tab, 0.f, 0.f, 0.f, 0.f, acc);
                 } else {
                     const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
                     const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
                     const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
                     const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                    forces_list<STATS, false, SF>(a, i, p, cnt, sxm, sxp, sym, syp, acc);
+                    forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
                 }
             } else {
                 int lox, hix, loy, hiy;

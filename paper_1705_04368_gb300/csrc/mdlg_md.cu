@@ -217,14 +217,19 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
                                          fmaf((float)(threadIdx.x >> 2), a.cell_w, -a.cell_w));
     __syncthreads();
 
-    // Neighbour-cell radius for the displacement bound of the input positions.
+    // Neighbour-cell radius for the displacement bound of the input positions
+    // (evaluated only where it is used: the cell-stencil path and the check).
     const float D = a.ctl->dbound;
-    const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
-    // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
-    const int R = (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
-    if (a.potential && threadIdx.x == 0 && blockIdx.x == 0 &&
-        (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1]))
-        set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
+    const auto stencil_radius = [&]() {
+        const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
+        // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
+        return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
+    };
+    if (a.potential && threadIdx.x == 0 && blockIdx.x == 0) {
+        const int R = stencil_radius();
+        if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1])
+            set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
+    }
     // the Verlet list holds every pair that can be closer than rc while 2D <= skin
     const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
 
@@ -248,6 +253,7 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
                     forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
                 }
             } else {
+                const int R = stencil_radius();
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);
                 stencil(R, geo.nc[1], loy, hiy);

@@ -203,7 +203,7 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
 // B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
 // per system); otherwise one system described by a.geo.
 template <int MODE, bool STATS, bool B, bool SF>
-__global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) {
+__device__ __forceinline__ void step_body(const StepArgs &a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
     const Geom &geo = sv.geo;
@@ -351,6 +351,20 @@ __global__ void __launch_bounds__(B ? kChunk : kStepThreads) k_step(StepArgs a) 
         }
         a.ctl->done = 0u;
     }
+}
+
+// One system: 256-thread blocks, the register count left to the compiler.
+template <int MODE, bool STATS, bool SF>
+__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+    step_body<MODE, STATS, false, SF>(a);
+}
+
+// A batch: one 128-slot chunk per block, 16 blocks per SM (32 registers: the
+// per-chunk geometry would otherwise take the count to 40 and the occupancy
+// to 48 warps; 4 % faster for the 256-system batch).
+template <int MODE, bool STATS, bool SF>
+__global__ void __launch_bounds__(kChunk, 16) k_step_batch(StepArgs a) {
+    step_body<MODE, STATS, true, SF>(a);
 }
 
 // ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
@@ -751,15 +765,21 @@ int grid_for(int64_t n, int threads, int per_sm = 8) {
 
 }  // namespace
 
+template <int MODE, bool STATS, bool B, bool SF>
+void launch_step_k(const StepArgs &a, dim3 grid, dim3 block, cudaStream_t s) {
+    if (B) k_step_batch<MODE, STATS, SF><<<grid, block, 0, s>>>(a);
+    else k_step<MODE, STATS, SF><<<grid, block, 0, s>>>(a);
+}
+
 template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
     if (mode == kModeStep) {
-        if (a.stats) k_step<kModeStep, true, B, SF><<<grid, block, 0, s>>>(a);
-        else k_step<kModeStep, false, B, SF><<<grid, block, 0, s>>>(a);
+        if (a.stats) launch_step_k<kModeStep, true, B, SF>(a, grid, block, s);
+        else launch_step_k<kModeStep, false, B, SF>(a, grid, block, s);
     } else if (mode == kModeInit) {
-        k_step<kModeInit, true, B, SF><<<grid, block, 0, s>>>(a);
+        launch_step_k<kModeInit, true, B, SF>(a, grid, block, s);
     } else {
-        k_step<kModeSync, true, B, SF><<<grid, block, 0, s>>>(a);
+        launch_step_k<kModeSync, true, B, SF>(a, grid, block, s);
     }
 }
 

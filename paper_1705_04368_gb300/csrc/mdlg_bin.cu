@@ -111,9 +111,15 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
             const float qy = pow2 ? __fmul_rn(yn, inv) : __fdiv_rn(yn, dx);
             const int32_t vx = ceil_small(qx) - 1 - c0x;
             const int32_t vy = ceil_small(qy) - 1 - c0y;
-            const int32_t bin = vel_index(vx, vy, ga.vmax);
-            rest[k] += (act && bin == center) ? 1u : 0u;
-            if (act && bin != center) atomicAdd(&sh[k * q1 + bin], 1u);
+            const bool at_rest = (vx | vy) == 0;
+            rest[k] += (act && at_rest) ? 1u : 0u;
+            if (act && !at_rest) {
+                // window index by unsigned range checks; the overflow bin past it
+                const uint32_t ux = (uint32_t)(vx + ga.vmax), uy = (uint32_t)(vy + ga.vmax);
+                const uint32_t bin = max(ux, uy) <= (uint32_t)(2 * ga.vmax) ? uy * (uint32_t)w + ux
+                                                                            : (uint32_t)(w * w);
+                atomicAdd(&sh[k * q1 + bin], 1u);
+            }
         }
     }
 #pragma unroll

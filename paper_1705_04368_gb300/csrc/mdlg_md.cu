@@ -589,12 +589,12 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int32_t j = b + u;
-                            const int ox = (j >= m1) + (j >= m2) - 1;
-                            const float odx = ox < 0 ? sxm : (ox > 0 ? sxp : 0.0f);
+                            const bool g1 = j >= m1, g2 = j >= m2;   // in cell cx, cx + 1
+                            const float odx = g2 ? sxp : (g1 ? 0.0f : sxm);
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
                             const bool hit = j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] =
-                                (uint32_t)j | ((uint32_t)(ox + 1) << 28) | ycode;
+                                ((uint32_t)j | ycode) + (g1 ? (1u << 28) : 0u) + (g2 ? (1u << 28) : 0u);
                             cnt += hit;
                         }
                     }

@@ -334,11 +334,13 @@ __device__ __forceinline__ int32_t wrap_into(int32_t v, int32_t c) {
 template <int V>
 __host__ __device__ constexpr int coll_ts() {
     constexpr int q = (2 * V + 1) * (2 * V + 1);
-    return 12288 / q > 64 ? 64 : 12288 / q;     // TS x Q int32 <= 48 KB
+    // 48 sites: 45 registers and five blocks per SM for V <= 3 (64 sites: 56
+    // registers, four blocks, 9 % slower); TS x Q int32 <= 48 KB
+    return 12288 / q > 48 ? 48 : 12288 / q;
 }
 
 template <int V>
-__global__ void __launch_bounds__(256, V <= 3 ? 4 : 1) k_collision(CollArgs ca) {
+__global__ void __launch_bounds__(256, V <= 3 ? 5 : 1) k_collision(CollArgs ca) {
     constexpr int w = 2 * V + 1, q = w * w, q1 = q + 1;
     constexpr int TS = coll_ts<V>();
     constexpr int NV = ((TS * q1 + 6) / 4 + 255) / 256;     // 16-byte vectors per thread

@@ -334,9 +334,10 @@ __device__ __forceinline__ int32_t wrap_into(int32_t v, int32_t c) {
 template <int V>
 __host__ __device__ constexpr int coll_ts() {
     constexpr int q = (2 * V + 1) * (2 * V + 1);
-    // 48 sites: 45 registers and five blocks per SM for V <= 3 (64 sites: 56
-    // registers, four blocks, 9 % slower); TS x Q int32 <= 48 KB
-    return 12288 / q > 48 ? 48 : 12288 / q;
+    // 56 sites: 45 registers and five blocks per SM for V <= 3 (64 sites: 56
+    // registers, four blocks, 12 % slower; 48 or 40 sites 2-3 % slower); TS x Q
+    // int32 <= 48 KB
+    return 12288 / q > 56 ? 56 : 12288 / q;
 }
 
 template <int V>

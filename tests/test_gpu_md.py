@@ -94,6 +94,28 @@ def test_late_resort_uses_wider_stencil(cuda):
     assert st["status"] == 0
 
 
+def test_resort_interval_from_fastest_initial_speed(cuda):
+    # sort_every = 0: the library re-sorts every floor(skin_eff / (2 x 1.15 vmax0 dt))
+    # steps, vmax0 the fastest initial speed (reduced on the device by the upload
+    # kernel); counted here from the re-sort launches of 100 steps (7 per re-sort)
+    n, L = 4096, mi.box_for(4096, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=78)
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=(5,))
+    k = math.ceil((p.rcut + p.skin) / p.grid - 1e-12)
+    skin_eff = k * p.grid - p.rcut
+    vmax0 = math.sqrt(float((v0 * v0).sum(axis=1).max()))
+    every = int(max(1.0, min(math.floor(0.5 * skin_eff / (1.15 * vmax0 * p.dt)), 1000.0)))
+    assert 2 <= every <= 50
+    K = 100
+    with m.Simulation(p, x0, v0) as s:
+        s.profile(True)
+        s.step(K)
+        prof = s.profile(False)
+        st, _, _ = s.stats()
+    assert prof["sort"][1] == 7 * ((K - 1) // every)
+    assert st["status"] == 0
+
+
 def test_fp64_reductions_at_start(cuda):
     n, L = 8192, mi.box_for(8192, 0.3, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=11)

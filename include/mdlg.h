@@ -162,7 +162,10 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
  *            params->site_mode and params->msd must be 0 and
  *            params->lattice_u {0, 0}.
  *   nsys   : systems, 1..65535.
- *   n      : host, nsys particle counts (the total below 2^28).
+ *   n      : host, nsys particle counts; each system is padded to a multiple
+ *            of 128 slots, and the total of the padded counts must stay
+ *            below 2^28 (the Verlet list indexes slots in 28 bits), else
+ *            MDLG_EINVAL.
  *   box    : host, nsys x 2 box sides, each a multiple of params->dx.
  *   x0, v0 : host, (sum n) x 2 FP64 positions and velocities, system after
  *            system in the order of n.

@@ -44,7 +44,8 @@ extern "C" {
 #define MDLG_ECUDA      -3   /* a CUDA runtime call failed                     */
 #define MDLG_EOVERFLOW  -4   /* a counter or index range was exceeded          */
 #define MDLG_ENONFINITE -5   /* a non-finite position or velocity was found    */
-#define MDLG_ETIMEOUT   -6   /* a bounded device wait gave up                  */
+#define MDLG_ETIMEOUT   -6   /* reserved: no entry point waits on the device with a
+                                bound today, so none returns it                  */
 #define MDLG_ENOTIMPL   -7   /* the entry point is declared but not built yet  */
 
 /* ---- limits ------------------------------------------------------------- */
@@ -404,8 +405,9 @@ int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t nco
  * (pack, neighbour-cell sort, the step kernel's force/reduction mode with a
  * zero time step), with every intermediate array in one statically sized
  * device array of the library instead of allocated scratch.
- *   params : as for mdlg_create; only n, box, potential (must be
- *            MDLG_POT_LJ_TS), eps, sigma, mass, rcut, grid and skin are used.
+ *   params : as for mdlg_create; only n, box, potential (MDLG_POT_LJ_TS or
+ *            MDLG_POT_LJ_SF; anything else is MDLG_EINVAL), eps, sigma, mass,
+ *            rcut, grid and skin are used.
  *   x, v   : device, n x 2 FP64 positions in (0, L] and velocities (inputs).
  *   f      : device, n x 2 FP64 forces F_i (output, original particle order).
  *   obs    : device, 5 FP64 (output): kinetic energy, potential energy,

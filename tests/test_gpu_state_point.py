@@ -21,7 +21,8 @@ import pytest
 
 import mdlg_inputs as mi
 import paper_1705_04368_gb300 as m
-from paper_1705_04368_gb300 import analysis as an
+import oracle
+from oracle import closed_form as cf
 
 pytestmark = pytest.mark.gpu
 
@@ -65,11 +66,11 @@ def test_msd_follows_exponential_vacf_with_tau_one_half(rest):
     t = np.array(C.lags) * C.dt
     msd = np.array([0.5 * (a + b) for a, b in st["msd"]])
     taus = np.linspace(0.1, 1.5, 1401)
-    err = [np.sum((np.log([an.msd_exponential(T, tau, ti) for ti in t]) - np.log(msd)) ** 2)
+    err = [np.sum((np.log([cf.msd_exponential_vacf(T, tau, ti) for ti in t]) - np.log(msd)) ** 2)
            for tau in taus]
     tau = float(taus[int(np.argmin(err))])
     assert 0.45 < tau < 0.55, tau
-    model = np.array([an.msd_exponential(T, 0.5, ti) for ti in t])
+    model = np.array([cf.msd_exponential_vacf(T, 0.5, ti) for ti in t])
     assert np.all(np.abs(msd / model - 1.0) < 0.03), msd / model
 
 
@@ -77,7 +78,7 @@ def test_fi_matches_closed_form_at_measured_width(rest):
     _, st, counts, fi = rest
     for li, lag in enumerate(C.lags):
         msd = 0.5 * (st["msd"][li][0] + st["msd"][li][1])
-        th = an.feq(C.vmax, math.sqrt(msd) / C.dx)
+        th = cf.feq_window(C.vmax, math.sqrt(msd) / C.dx)
         assert np.abs(fi[li] - th).max() < 0.01, (lag, np.abs(fi[li] - th).max())
         assert int(counts[li].sum()) == C.n * st["intervals"][li]
 
@@ -95,8 +96,8 @@ def test_moving_lattice_equilibrium(rest):
     assert abs(u - U_LATTICE) <= 0.5 * quantum / (U * C.dt) * U_LATTICE * 1.0001
     msd = 0.5 * (st["msd"][li][0] + st["msd"][li][1])
     a = math.sqrt(msd) / C.dx
-    th = an.feq(C.vmax, a, (u, 0.0))
+    th = cf.feq_window(C.vmax, a, (u, 0.0))
     assert np.abs(fi[li] - th).max() < 0.01
-    mom = an.moments(fi[li], C.vmax)
-    assert mom["mean"][0] == pytest.approx(u, abs=3e-3)
-    assert abs(mom["mean"][1]) < 3e-3
+    mean = (fi[li][:-1, None] * oracle.velocity_table(C.vmax)).sum(axis=0)
+    assert mean[0] == pytest.approx(u, abs=3e-3)
+    assert abs(mean[1]) < 3e-3

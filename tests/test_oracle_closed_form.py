@@ -87,13 +87,25 @@ def test_window_and_overflow():
 
 def test_d2q9_match_near_one_sixth():
     # Sec. V (Eq. wif0eqn): each D2Q9 weight is met by f_i^eq/rho at a^2 close
-    # to 1/6, and the three solutions nearly coincide.
+    # to 1/6, and the three solutions nearly coincide.  The roots are solved
+    # twice: from the closed form, and from the wedge integral of Eq. fgen
+    # evaluated by quadrature (independent of the erf algebra); both must give
+    # 0.1771 (rest), 0.1836 (axis) and 0.1801 (diagonal) to 1e-4.
     def feq(a2, v):
         return cf.feq_over_rho(v, math.sqrt(a2))
+
+    def feq_quad(a2, v):
+        a = math.sqrt(a2)
+        return _quad_axis(v[0], 0.0, a) * _quad_axis(v[1], 0.0, a)
+
+    cases = (((0, 0), 4 / 9, 0.1771), ((1, 0), 1 / 9, 0.1836), ((1, 1), 1 / 36, 0.1801))
     roots = []
-    for v, w in (((0, 0), 4 / 9), ((1, 0), 1 / 9), ((1, 1), 1 / 36)):
-        roots.append(optimize.brentq(lambda a2: feq(a2, v) - w, 0.05, 0.5, xtol=1e-14))
-    assert all(0.16 < r < 0.19 for r in roots), roots
+    for v, w, expect in cases:
+        r = optimize.brentq(lambda a2: feq(a2, v) - w, 0.05, 0.5, xtol=1e-14)
+        rq = optimize.brentq(lambda a2: feq_quad(a2, v) - w, 0.05, 0.5, xtol=1e-12)
+        assert r == pytest.approx(expect, abs=1e-4), (v, r)
+        assert rq == pytest.approx(r, abs=1e-9), (v, rq, r)
+        roots.append(r)
     assert max(roots) - min(roots) < 0.01, roots
 
 

@@ -35,11 +35,14 @@ import mdlg_inputs as mi  # noqa: E402
 MD_STEPS_PER_STEP = 200
 METRIC = "MD+MDLG particle-steps/s on 1 GB300 (% FP32/HBM roofline); batched & adjoint vs plain"
 UNIT = "particle-steps/s"
-STEP_BYTES_PER_PARTICLE = 36      # read cell 4 + cl 8 + v 8, write cl 8 + v 8
+# algorithmic bytes of one particle-step of the fused force + velocity-Verlet
+# kernel: positions read and written (12 B each: two 16-bit cell ids + two
+# binary32 offsets) and velocities read and written (8 B each); the layout here
+# reads a 32-bit cell word and does not write it back (36 B moved)
+STEP_BYTES_PER_PARTICLE = 40
 IDEALGAS_BYTES_PER_PARTICLE = 16  # x, y, vx, vy binary32
 COLLISION_BYTES_PER_SITE_Q = 12   # read n_i at x and at x + v_i, write Xi_i: 3 x 4 B per velocity
 COLLISION_BYTES_PER_SITE = 12     # dmass + dmom int32
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SMSP_PER_SM = 4
 
@@ -162,16 +165,83 @@ def _params(c, m):
                     stats_every=100)
 
 
-def _oracle_sample(c, x0, v0, md_steps=3):
-    """FP64 oracle (as it stands, one host thread) on the full system for a few MD steps."""
+def _cpu_info():
+    """Host core count and CPU model (the oracle baselines run on these cores)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def run_oracle_timing(threads: int):
+    """The FP64 oracle, as it stands, on the three workloads of the measurement
+    plan; one JSON line.  threads = 1: the serial build; 0: the threaded build on
+    every host core.  c1: N = 1024 LJ gas, 2000 steps with a binning every 50;
+    c3: 3 velocity-Verlet steps of the production gas plus one binning (per
+    particle-step); c2: one snapshot of the 2^22-particle ideal gas, 9 pairs."""
     import oracle
+    used = 1 if threads == 1 else oracle.use_threads(threads)
+    out = {"threads": used, **_cpu_info()}
+    c = mi.SMALL_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
     t0 = time.perf_counter()
     ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
-    ref.run(md_steps)
     cnt = np.zeros(50, np.uint64)
-    oracle.mdlg_bin(x0, ref.x, c.dx, (int(c.box / c.dx),) * 2, 3, counts=cnt)
-    dt_s = time.perf_counter() - t0
-    return c.n * md_steps / dt_s, dt_s
+    cells = (int(c.box / c.dx),) * 2
+    prev = ref.x.copy()
+    for _ in range(c.steps // c.lags[0]):
+        ref.run(c.lags[0])
+        oracle.mdlg_bin(prev, ref.x, c.dx, cells, c.vmax, counts=cnt)
+        prev = ref.x.copy()
+    s1 = time.perf_counter() - t0
+    out["c1"] = {"workload": c.name, "md_steps": c.steps, "seconds": s1,
+                 "particle_steps_per_s": c.n * c.steps / s1}
+    c = mi.PRODUCTION_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
+    k = 3
+    t0 = time.perf_counter()
+    ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
+    ref.run(k)
+    oracle.mdlg_bin(x0, ref.x, c.dx, (int(c.box / c.dx),) * 2, 3, counts=np.zeros(50, np.uint64))
+    s3 = time.perf_counter() - t0
+    out["c3"] = {"workload": c.name, "md_steps": k, "seconds": s3,
+                 "particle_steps_per_s": c.n * k / s3}
+    pos, vel = mi.idealgas_state(mi.IDEALGAS_N, mi.IDEALGAS_BOX, 1.0, seed=7)
+    combos = list(mi.IDEALGAS_COMBOS)
+    t0 = time.perf_counter()
+    oracle.stream_bin_f32(pos, vel, [x[0] for x in combos], [x[1] for x in combos], 3)
+    s2 = time.perf_counter() - t0
+    out["c2"] = {"workload": "idealgas_n4194304_L2048_9combos", "seconds": s2,
+                 "particles_per_s": mi.IDEALGAS_N / s2}
+    print(json.dumps(out), flush=True)
+
+
+def _oracle_timings():
+    """run_oracle_timing in child processes (one loads the serial build, one the
+    threaded build): single thread, then every host core."""
+    res = {}
+    for name, th in (("one_thread", 1), ("all_cores", 0)):
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-timing", str(th)],
+                           capture_output=True, text=True, timeout=900)
+        if r.returncode != 0:
+            res[name] = {"error": r.stderr.strip().splitlines()[-1:] or [f"rc {r.returncode}"]}
+            continue
+        res[name] = json.loads(r.stdout.strip().splitlines()[-1])
+    return res
 
 
 def run_reference(args, rank, world):
@@ -180,6 +250,7 @@ def run_reference(args, rank, world):
     c = _workload()
     x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
     import oracle
+    cores = oracle.use_threads(0)
     ref = oracle.VV(x0, v0, (c.box, c.box), c.dt, cells=True)
     times = []
     for k in range(args.warmup + args.steps):
@@ -195,10 +266,11 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(c, 1),
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(times)} bench steps of one FP64 velocity-Verlet "
                                        f"step each (not 200) of the full {c.n}-particle "
-                                       f"system, linked-cell oracle, one host thread"},
+                                       f"system, linked-cell oracle, {cores} host threads",
+                             **_cpu_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -247,41 +319,42 @@ def run_ours(args, rank, world, local_rank):
     md_steps = args.steps * MD_STEPS_PER_STEP
     value = job_rate(world, c.n * md_steps, ms / 1e3)
 
-    # dominant kernel: fused force + velocity-Verlet step
+    # roofline denominators: HBM from MEASURED_PEAKS.json, FP32 from the project's
+    # FMA probe (the copy probe is reported beside the HBM figure as a cross-check)
     hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+    probes = _probe_peaks(m, torch, dev, stream)
+    sms = probes["sms"]
+    fp32_nominal = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    fp32_peak = probes["fp32_tflops"]
+    probes["fp32_tflops_nominal"] = fp32_nominal
+    probes["hbm_gbs_measured_peaks"] = hbm_gbs
+    # dominant kernel: fused force + velocity-Verlet step
     step_ms, step_launches = prof["step"]
     avg_step_s = step_ms / 1e3 / max(step_launches, 1)
-    step_bytes = STEP_BYTES_PER_PARTICLE * c.n
-    achieved_gbs = step_bytes / avg_step_s / 1e9
     rho_eff = c.n / (c.box * c.box)
-    n_in = rho_eff * math.pi * c.rc ** 2
-    flops = c.n * (18.0 * n_in + 8.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
-    achieved_tf = flops / avg_step_s / 1e12
-    tpp = _traffic_record("k_step")
-    ipp = _traffic_record("k_step", "warp_inst_per_particle")
+    roofline = _step_roofline(c.n, rho_eff, c.rc, avg_step_s, hbm_gbs, fp32_peak, peak_kind)
+    tpp = _traffic_record("k_step_tile")
+    ipp = _traffic_record("k_step_tile", "warp_inst_per_particle")
+    roofline["traffic"] = (tpp * c.n) if tpp is not None else None
     # instruction issue: one warp instruction per clock per SM sub-partition
-    issue_peak = SM_COUNT * SMSP_PER_SM * sm_max_mhz * 1e6
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
-                "traffic": (tpp * c.n) if tpp is not None else None,
-                "kernel": "k_step (force + velocity-Verlet)",
-                "algorithmic_bytes_per_launch": step_bytes,
-                "avg_launch_us": avg_step_s * 1e6,
-                "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
-                         "frac": achieved_tf / fp32_peak,
-                         "flops_per_particle": 18.0 * n_in + 8.0},
-                "issue": None if ipp is None else {
-                    "achieved_warp_inst_per_s": ipp * c.n / avg_step_s,
-                    "peak_warp_inst_per_s": issue_peak,
-                    "frac": ipp * c.n / avg_step_s / issue_peak,
-                    "warp_inst_per_particle": ipp,
-                    "what": "ncu warp-instruction count of one launch (profiles/traffic.txt) over "
-                            "the launch time measured here; peak = one issue per clock per SM "
-                            "sub-partition at the maximum SM clock"}}
+    issue_peak = sms * SMSP_PER_SM * sm_max_mhz * 1e6
+    roofline["issue"] = None if ipp is None else {
+        "achieved_warp_inst_per_s": ipp * c.n / avg_step_s,
+        "peak_warp_inst_per_s": issue_peak,
+        "frac": ipp * c.n / avg_step_s / issue_peak,
+        "warp_inst_per_particle": ipp,
+        "what": "ncu warp-instruction count of one launch (profiles/traffic.txt) over the launch "
+                "time measured here; peak = one issue per clock per SM sub-partition at the "
+                "maximum SM clock"}
     kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms if ms else None}
                for k, v in prof.items() if v[1]}
     launches = prof["step"][1] + prof["sort"][1] + prof["bin"][1] + prof["sync"][1]
+
+    # the dense production case (rho = 0.6, T = 0.8) with its own roofline
+    dense = _production_leg(m, torch, stream, local_rank, mi.PRODUCTION_LJ_DENSE, rank_seed(rank),
+                            hbm_gbs, fp32_peak, peak_kind) if rank == 0 else None
+    # the small case (N = 1024), absolute time only
+    small = _small_leg(m, torch, stream, local_rank) if rank == 0 else None
 
     # ideal-gas single pass (binning throughput), rotating buffers > 2x L2
     ig = _idealgas(m, torch, dev, stream, hbm_gbs)
@@ -308,18 +381,146 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": _config(c, world), "roofline": roofline,
             "gpu_launches": launches, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "idealgas": ig, "batched": batched, "adjoint": adjoint, "analyses": analyses,
+            "dense": dense, "small": small, "peaks": probes,
             "status": st["status"],
             "tuned": {"grid": params.grid, "skin": params.skin,
                       "cell_width": params.grid * math.ceil((params.rcut + params.skin) / params.grid - 1e-12),
                       "cached": tune_report["cached"]}}
     if rank == 0:
         if world == 1:
-            v, secs = _oracle_sample(c, x0, v0)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"3 FP64 velocity-Verlet steps of the full "
-                                              f"{c.n}-particle system plus one MDLG binning, "
-                                              f"{secs:.1f} s on one host thread"}
+            ot = _oracle_timings()
+            line["oracle_timings"] = ot
+            allc = ot.get("all_cores", {})
+            one = ot.get("one_thread", {})
+            if "c3" in allc:
+                line["cpu_baseline"] = {
+                    "value": allc["c3"]["particle_steps_per_s"], "unit": UNIT,
+                    "cores": allc["threads"], "kind": "oracle",
+                    "sample": f"3 FP64 velocity-Verlet steps of the full {c.n}-particle system "
+                              f"plus one MDLG binning, {allc['c3']['seconds']:.1f} s on "
+                              f"{allc['threads']} host threads (threaded build of the oracle)",
+                    "nproc": allc.get("nproc"), "cpu_model": allc.get("model"),
+                    "one_thread": one.get("c3")}
         print(json.dumps(line), flush=True)
+
+
+def _probe_peaks(m, torch, dev, stream):
+    """FP32 multiply-add rate and HBM copy bandwidth measured with the library's
+    probe kernels (CUDA events on the library's stream): the FMA loop on every SM
+    (8 blocks of 256 threads per SM, 8 independent chains per thread), the copy
+    over two 512 MiB buffers (4x L2 each), best of several launches."""
+    import ctypes
+    lib = m.lib()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 1 << 18
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    fl = ctypes.c_double()
+    h = stream.cuda_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def best_of(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    def fma():
+        assert lib.mdlg_probe_fma(blocks, threads, iters, out.data_ptr(), ctypes.byref(fl), h) == 0
+
+    t_fma = best_of(fma, 3)
+    nbytes = 512 << 20
+    src = torch.empty(nbytes // 4, dtype=torch.int32, device=dev)
+    dst = torch.empty_like(src)
+
+    def copy():
+        assert lib.mdlg_probe_copy(src.data_ptr(), dst.data_ptr(), nbytes, h) == 0
+
+    t_copy = best_of(copy, 10)
+    del src, dst, out
+    return {"sms": sms, "fp32_tflops": fl.value / t_fma / 1e12,
+            "hbm_copy_gbs": 2 * nbytes / t_copy / 1e9,
+            "what": "mdlg_probe_fma: 8 blocks x 256 threads per SM, 8 independent binary32 FMA "
+                    "chains per thread; mdlg_probe_copy: 512 MiB copied with 16-byte words "
+                    "(read + write bytes); best of 3 / 10 launches"}
+
+
+def _step_roofline(n, rho_eff, rc, avg_step_s, hbm_gbs, fp32_peak, peak_kind):
+    """The fused force + velocity-Verlet kernel against HBM (40 B per particle-step)
+    and against the FP32 peak (18 n_in + 8 flops per particle-step, n_in = rho pi rc^2),
+    with the FP32 fraction the HBM roofline allows at this density."""
+    step_bytes = STEP_BYTES_PER_PARTICLE * n
+    achieved_gbs = step_bytes / avg_step_s / 1e9
+    n_in = rho_eff * math.pi * rc ** 2
+    fpp = 18.0 * n_in + 8.0
+    achieved_tf = n * fpp / avg_step_s / 1e12
+    intensity = fpp / STEP_BYTES_PER_PARTICLE
+    cap = min(1.0, intensity * hbm_gbs / 1e3 / fp32_peak)
+    return {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
+            "kernel": "k_step_tile (force + velocity-Verlet)",
+            "algorithmic_bytes_per_launch": step_bytes, "avg_launch_us": avg_step_s * 1e6,
+            "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
+                     "frac": achieved_tf / fp32_peak, "flops_per_particle": fpp,
+                     "intensity_flop_per_byte": intensity,
+                     "cap_frac_at_hbm_peak": cap,
+                     "frac_of_cap": achieved_tf / fp32_peak / cap}}
+
+
+def _production_leg(m, torch, stream, local_rank, c, seed, hbm_gbs, fp32_peak, peak_kind,
+                    steps=2):
+    """Another production configuration (tuned geometry, 200 MD steps per bench
+    step, binning and statistics as in the headline leg), timed with CUDA events."""
+    from paper_1705_04368_gb300 import tune
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=seed)
+    params, rep = tune.tune(_params(c, m), x0, v0, c.temperature)
+    with m.Simulation(params, x0, v0, stream=stream, device=local_rank) as s:
+        s.step(MD_STEPS_PER_STEP)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.profile(True)
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(MD_STEPS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = s.profile(False)
+        st, _, _ = s.stats()
+    ms = e0.elapsed_time(e1)
+    step_ms, nst = prof["step"]
+    rho_eff = c.n / (c.box * c.box)
+    return {"workload": c.name, "n": c.n, "box": c.box, "rho_eff": round(rho_eff, 5),
+            "temperature": c.temperature, "status": st["status"],
+            "particle_steps_per_s": c.n * steps * MD_STEPS_PER_STEP / (ms / 1e3),
+            "ms_per_step": ms / steps,
+            "tuned": {"grid": params.grid, "skin": params.skin, "cached": rep["cached"]},
+            "kernels": {k: {"ms": v[0], "launches": v[1], "share": v[0] / ms}
+                        for k, v in prof.items() if v[1]},
+            "roofline": _step_roofline(c.n, rho_eff, c.rc, step_ms / 1e3 / max(nst, 1), hbm_gbs,
+                                       fp32_peak, peak_kind)}
+
+
+def _small_leg(m, torch, stream, local_rank):
+    """The small LJ gas (N = 1024, L = 64, dx = 4, lag 50): 2000 MD steps and the
+    statistics read-back, wall time (the size is launch-bound; CUDA graphs on)."""
+    c = mi.SMALL_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
+    p = m.Params(n=c.n, box=c.box, dx=c.dx, dt=c.dt, lag_steps=c.lags, use_graphs=True)
+    with m.Simulation(p, x0, v0, stream=stream, device=local_rank) as s:
+        s.step(c.steps)           # captures the schedule's graph
+        s.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(c.steps)
+        st, _, _ = s.stats()
+        sec = time.perf_counter() - t0
+    return {"workload": c.name, "md_steps": c.steps, "seconds": sec,
+            "particle_steps_per_s": c.n * c.steps / sec, "status": st["status"]}
 
 
 def _idealgas(m, torch, dev, stream, hbm_gbs):
@@ -357,9 +558,12 @@ def _batched(m, torch, stream, local_rank, md_steps=700):
     dx = 4, lag 50, re-sort every 7 steps): particle-steps/s advanced as one batch
     versus one context per system.  Both arms replay CUDA graphs of their 700-step
     schedule (captured during an untimed first pass)."""
+    from paper_1705_04368_gb300 import tune
     ns, boxes, seeds = mi.batch_recipe()
     x0, v0 = mi.batch_states(ns, boxes, seeds)
     params = m.Params(n=0, box=64.0, dx=4.0, lag_steps=(50,), sort_every=7, use_graphs=True)
+    # neighbour-cell geometry tuned for the whole batch (untimed)
+    params, trep = tune.tune_batch(params, ns, boxes, x0, v0, 1.0)
     total = int(ns.sum())
     with m.BatchSimulation(params, ns, boxes, x0, v0, stream=stream, device=local_rank) as bt:
         bt.step(md_steps)          # captures the graph
@@ -374,7 +578,7 @@ def _batched(m, torch, stream, local_rank, md_steps=700):
     sims, off = [], 0
     for n, b in zip(ns, boxes):
         p = m.Params(n=int(n), box=float(b[0]), dx=4.0, lag_steps=(50,), sort_every=7,
-                     use_graphs=True)
+                     use_graphs=True, grid=params.grid, skin=params.skin)
         sims.append(m.Simulation(p, x0[off:off + n], v0[off:off + n], stream=stream,
                                  device=local_rank))
         off += int(n)
@@ -392,7 +596,9 @@ def _batched(m, torch, stream, local_rank, md_steps=700):
             "particles": total, "md_steps": md_steps, "cuda_graphs": True,
             "batched_particle_steps_per_s": total * md_steps / t_batch,
             "one_context_each_particle_steps_per_s": total * md_steps / t_alone,
-            "speedup": t_alone / t_batch, "status": st["status"]}
+            "speedup": t_alone / t_batch, "status": st["status"],
+            "tuned": {"grid": params.grid, "skin": params.skin, "cached": trep["cached"],
+                      "candidates": trep.get("candidates")}}
 
 
 def _adjoint(m, torch, stream, local_rank, reps=3):
@@ -647,7 +853,13 @@ def main():
                          "lattice at dx = 100, dt_LG = 34.16; one JSON line")
     ap.add_argument("--ncu-idealgas", type=int, default=0, metavar="LAUNCHES",
                     help="profiling target: LAUNCHES ideal-gas passes, exit")
+    ap.add_argument("--oracle-timing", type=int, default=None, metavar="THREADS",
+                    help="time the FP64 oracle on the measurement plan's CPU samples (1: serial "
+                         "build, 0: threaded build on every core); one JSON line, exit")
     args = ap.parse_args()
+    if args.oracle_timing is not None:
+        run_oracle_timing(args.oracle_timing)
+        return
     if args.ncu_idealgas:
         run_ncu_idealgas(args.ncu_idealgas)
         return

@@ -432,6 +432,26 @@ int mdlg_idealgas_bin(int64_t n, const float *pos, const float *vel, int32_t nco
 int mdlg_forces_static(const mdlg_params *params, const double *x, const double *v, double *f,
                        double *obs, int32_t *status, void *stream);
 
+/* ---- measurement probes --------------------------------------------------
+ * The paper has no counterpart: these two kernels measure the denominators of
+ * the roofline fractions reported beside the method's kernels.  The caller
+ * times them (CUDA events on `stream`).
+ *
+ * mdlg_probe_fma -- `blocks` blocks of `threads` threads (a multiple of 32,
+ *   at most 256); every thread runs 8 independent binary32 fused multiply-add
+ *   chains of `iters` steps and stores their sum in out[block * threads + thread]
+ *   (device, blocks x threads floats, caller-owned).  *flops (host, may be
+ *   NULL) receives the floating-point operations launched, 2 per multiply-add.
+ *   Errors: MDLG_EINVAL, MDLG_ECUDA.
+ *
+ * mdlg_probe_copy -- copies `bytes` (a multiple of 16) from src to dst (device,
+ *   both 16-byte aligned, caller-owned, not overlapping) with 16-byte loads
+ *   and stores.  Errors: MDLG_EINVAL, MDLG_ECUDA.
+ */
+int mdlg_probe_fma(int32_t blocks, int32_t threads, int64_t iters, float *out, double *flops,
+                   void *stream);
+int mdlg_probe_copy(const void *src, void *dst, int64_t bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

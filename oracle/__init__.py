@@ -52,20 +52,44 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mdlg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_threaded = False
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle C file into a shared library with gcc (FP64, no fast-math)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle C file into a shared library with gcc (FP64, no fast-math).
+
+    openmp: the same source built with -fopenmp (the threaded timing build of the
+    benchmark's CPU baseline); the default build is serial."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    path = _LIB_OMP_PATH if openmp else _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+               "-fPIC", "-shared", *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
+
+
+def use_threads(threads: int) -> int:
+    """Switch this process to the threaded build with `threads` host threads (0: all
+    cores); returns the thread count in use.  Call before the first oracle call."""
+    global _threaded
+    with _lock:
+        if _lib is not None and not _threaded:
+            raise RuntimeError("oracle.use_threads must come before the first oracle call")
+        _threaded = True
+    lib = _load()
+    lib.oracle_set_threads(int(threads) if threads > 0 else (os.cpu_count() or 1))
+    return int(lib.oracle_threads())
+
+
+def threads() -> int:
+    """Host threads the loaded oracle build uses (1 for the serial build)."""
+    return int(_load().oracle_threads())
 
 
 def _load():
@@ -73,7 +97,7 @@ def _load():
     with _lock:
         if _lib is None:
             # ORACLE_LIB: an alternative build of the same source (the sanitizer test)
-            lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build(openmp=_threaded))
             P = ctypes.c_void_p
             I64 = ctypes.c_int64
             D = ctypes.c_double
@@ -91,6 +115,10 @@ def _load():
             lib.oracle_kinetic.argtypes = [I64, P, D, P]
             lib.oracle_set_shifted_force.argtypes = [ctypes.c_int]
             lib.oracle_set_shifted_force.restype = None
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
+            lib.oracle_threads.argtypes = []
+            lib.oracle_threads.restype = ctypes.c_int
             for name in ("oracle_lj_forces_direct", "oracle_lj_forces_cells",
                          "oracle_lj_forces_sample", "oracle_vv", "oracle_free_stream",
                          "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic",

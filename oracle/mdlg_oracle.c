@@ -27,6 +27,34 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/*
+ * Threads.  The default build is serial.  Built with -fopenmp (the timing
+ * build of the benchmark's CPU baseline only), the per-particle loops below
+ * run on several host threads: every particle's own sums keep their serial
+ * order, only the global energy / virial sums and the histogram totals are
+ * combined across threads.
+ */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Periodic helpers                                                          */
@@ -222,6 +250,7 @@ void oracle_lj_forces_cells(int64_t n, const double *x, const double *L,
     double rc2 = rc * rc;
     double pe = 0.0, vir = 0.0;
     g_rc = rc;
+#pragma omp parallel for schedule(static) reduction(+ : pe, vir)
     for (int64_t i = 0; i < n; ++i) {
         double fx = 0.0, fy = 0.0, fs = 0.0;
         for (int oy = -1; oy <= 1; ++oy)
@@ -267,6 +296,7 @@ void oracle_vv(int64_t n, double *x, double *v, double *f, int have_force,
         else oracle_lj_forces_direct(n, x, L, eps, sigma, rc, f, NULL, tmp);
     }
     for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i)
             for (int a = 0; a < 2; ++a) {
                 v[2 * i + a] += 0.5 * dt * f[2 * i + a] / mass;
@@ -274,6 +304,7 @@ void oracle_vv(int64_t n, double *x, double *v, double *f, int have_force,
             }
         if (use_cells) oracle_lj_forces_cells(n, x, L, eps, sigma, rc, f, NULL, tmp);
         else oracle_lj_forces_direct(n, x, L, eps, sigma, rc, f, NULL, tmp);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i)
             for (int a = 0; a < 2; ++a)
                 v[2 * i + a] += 0.5 * dt * f[2 * i + a] / mass;
@@ -357,6 +388,10 @@ void oracle_mdlg_bin_shifted(int64_t n, const double *xprev, const double *xcur,
     const double zero[2] = {0.0, 0.0};
     if (!s_prev) s_prev = zero;
     if (!s_cur) s_cur = zero;
+    int64_t vs0 = 0, vs1 = 0;
+    /* threaded only when no per-site output is requested (the totals are
+     * integers: combining them across threads changes nothing) */
+#pragma omp parallel for schedule(static) reduction(+ : counts[:Q + 1], vs0, vs1) if (!ncell && !field)
     for (int64_t j = 0; j < n; ++j) {
         int64_t c0x = lattice_cell(xprev[2 * j] + s_prev[0], dx);
         int64_t c0y = lattice_cell(xprev[2 * j + 1] + s_prev[1], dx);
@@ -373,13 +408,15 @@ void oracle_mdlg_bin_shifted(int64_t n, const double *xprev, const double *xcur,
             i = Q;
         } else {
             i = (vy + vmax) * W + (vx + vmax);
-            if (vsum) { vsum[0] += vx; vsum[1] += vy; }
+            vs0 += vx;
+            vs1 += vy;
         }
         int64_t site = c1y * C[0] + c1x;
         counts[i] += 1;
         if (ncell) ncell[site] += 1;
         if (field) field[site * (Q + 1) + i] += 1;
     }
+    if (vsum) { vsum[0] += vs0; vsum[1] += vs1; }
 }
 
 /*
@@ -402,6 +439,8 @@ void oracle_stream_bin_f32(int64_t n, const float *pos, const float *vel,
     int64_t W = 2 * vmax + 1, Q = W * W;
     for (int k = 0; k < ncombo; ++k) {
         volatile float dx = dxs[k], dt = dts[k];
+        uint64_t *ck = counts + k * (Q + 1);
+#pragma omp parallel for schedule(static) reduction(+ : ck[:Q + 1])
         for (int64_t j = 0; j < n; ++j) {
             int64_t c[2][2];
             for (int a = 0; a < 2; ++a) {
@@ -417,7 +456,7 @@ void oracle_stream_bin_f32(int64_t n, const float *pos, const float *vel,
             int64_t vx = c[0][1] - c[0][0], vy = c[1][1] - c[1][0];
             int64_t i = (vx < -vmax || vx > vmax || vy < -vmax || vy > vmax)
                             ? Q : (vy + vmax) * W + (vx + vmax);
-            counts[k * (Q + 1) + i] += 1;
+            ck[i] += 1;
         }
     }
 }

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmdlg.so")
-SOURCES = ("mdlg_api.cu", "mdlg_md.cu", "mdlg_bin.cu", "mdlg_static.cu", "mdlg_adjoint.cu")
+SOURCES = ("mdlg_api.cu", "mdlg_md.cu", "mdlg_bin.cu", "mdlg_static.cu", "mdlg_adjoint.cu",
+           "mdlg_probe.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--ptxas-options=-v"]

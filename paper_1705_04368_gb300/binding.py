@@ -102,6 +102,9 @@ _SIGNATURES = {
     "mdlg_idealgas_bin": (ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P, _P,
                                          ctypes.c_int32, _P, _P]),
     "mdlg_forces_static": (ctypes.c_int, [ctypes.POINTER(_Params), _P, _P, _P, _P, _P, _P]),
+    "mdlg_probe_fma": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
+                                      ctypes.POINTER(ctypes.c_double), _P]),
+    "mdlg_probe_copy": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
 }
 
 

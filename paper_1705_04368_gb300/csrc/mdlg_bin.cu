@@ -6,6 +6,8 @@
 // over particles with a block-private shared-memory histogram of the Q+1
 // velocity bins, flushed once per block with 64-bit global atomics; optional
 // per-site outputs (N(x,t), n_i(x,t)) are 32-bit global atomics.
+#include <cmath>
+
 #include "mdlg_kernels.h"
 
 namespace mdlg {
@@ -132,6 +134,99 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
     for (int k = 0; k < NC; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)k * q1);
 }
 
+// Non-interacting gas, every dx a power of two.  The pairs arrive ordered so
+// that pairs sharing (dt, U) are adjacent: x' = fl(x + fl(v' dt)) is formed
+// once per group, and the cell at every dx of the group is the cell at the
+// smallest dx shifted right.  This is exact: dx_min = dx / 2^s and x / dx_min
+// are exact in binary32, and with c = ceil(x / dx_min) - 1 (so c < x / dx_min
+// <= c + 1) the cell ceil(x / dx) - 1 is floor(c / 2^s) (the multiples of 2^s
+// are integers).  The decisions therefore equal the division form above bit
+// for bit.  PPT particles per thread per loop trip (2: one 16-byte load of
+// positions and one of velocities).
+template <int NC, int PPT>
+__global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t n,
+                                                       const float2 *__restrict__ pos,
+                                                       const float2 *__restrict__ vel,
+                                                       unsigned long long *counts) {
+    extern __shared__ uint32_t sh[];
+    const int w = 2 * ga.vmax + 1, q1 = w * w + 1;
+    const int center = ga.vmax * w + ga.vmax;
+    const uint32_t wmax = (uint32_t)(2 * ga.vmax);
+    for (int b = threadIdx.x; b < q1 * NC; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    uint32_t rest[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rest[k] = 0u;
+    const float inv = ga.inv_min;
+    const int64_t ng = (n + PPT - 1) / PPT;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ng; base += stride) {
+        const int64_t gi = base + threadIdx.x;
+        const int64_t j0 = gi * PPT;
+        float2 p[PPT], v[PPT];
+        bool act[PPT];
+        if (PPT == 2 && j0 + 1 < n) {
+            const float4 pp = reinterpret_cast<const float4 *>(pos)[gi];
+            const float4 vv = reinterpret_cast<const float4 *>(vel)[gi];
+            p[0] = make_float2(pp.x, pp.y);
+            p[PPT - 1] = make_float2(pp.z, pp.w);
+            v[0] = make_float2(vv.x, vv.y);
+            v[PPT - 1] = make_float2(vv.z, vv.w);
+            act[0] = act[PPT - 1] = true;
+        } else {
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+                act[u] = gi < ng && j0 + u < n;
+                p[u] = act[u] ? pos[j0 + u] : make_float2(1.f, 1.f);
+                v[u] = act[u] ? vel[j0 + u] : make_float2(0.f, 0.f);
+            }
+        }
+        int32_t bx[PPT], by[PPT], cx[PPT], cy[PPT];
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            bx[u] = ceil_small(__fmul_rn(p[u].x, inv)) - 1;
+            by[u] = ceil_small(__fmul_rn(p[u].y, inv)) - 1;
+            cx[u] = cy[u] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k == 0 || ga.first[k]) {
+                const float dt = ga.dt[k];
+#pragma unroll
+                for (int u = 0; u < PPT; ++u) {
+                    const float vx_ = ga.boost ? __fadd_rn(v[u].x, ga.ux[k]) : v[u].x;
+                    const float vy_ = ga.boost ? __fadd_rn(v[u].y, ga.uy[k]) : v[u].y;
+                    const float xn = __fadd_rn(p[u].x, __fmul_rn(vx_, dt));
+                    const float yn = __fadd_rn(p[u].y, __fmul_rn(vy_, dt));
+                    cx[u] = ceil_small(__fmul_rn(xn, inv)) - 1;
+                    cy[u] = ceil_small(__fmul_rn(yn, inv)) - 1;
+                }
+            }
+            const int sft = ga.shift[k];
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+                const int32_t dvx = (cx[u] >> sft) - (bx[u] >> sft);
+                const int32_t dvy = (cy[u] >> sft) - (by[u] >> sft);
+                const bool at_rest = (dvx | dvy) == 0;
+                rest[k] += (act[u] && at_rest) ? 1u : 0u;
+                if (act[u] && !at_rest) {
+                    const uint32_t ux = (uint32_t)(dvx + ga.vmax), uy = (uint32_t)(dvy + ga.vmax);
+                    const uint32_t bin = max(ux, uy) <= wmax ? uy * (uint32_t)w + ux : (uint32_t)(w * w);
+                    atomicAdd(&sh[k * q1 + bin], 1u);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        uint32_t r = rest[k];
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((threadIdx.x & 31) == 0 && r) atomicAdd(&sh[k * q1 + center], r);
+    }
+    __syncthreads();
+    for (int k = 0; k < NC; ++k) flush_hist(sh + k * q1, q1, counts + (size_t)ga.out[k] * q1);
+}
+
 // Sum v over the block into out (added to, FP64); every thread calls it.
 __device__ void block_sum_add(float v, float *red, double *out) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -237,6 +332,114 @@ __global__ void k_bin_state(StateBinArgs sa) {
                 block_sum_add(m2[l][1], red, sa.msd_acc + 2 * l + 1);
             }
     }
+}
+
+// Binning of the state on the lattice at rest without displacement sums: the
+// same decisions as k_bin_state, four consecutive particles per thread and
+// loop trip with 16-byte loads (cell words, offsets, each lag's stored cells)
+// and stores, every load of a trip issued before its first store.  K is the
+// number of lags binned by the launch (the set bits of the mask, in order), so
+// only their stored cells are loaded and kept in registers.  The rest velocity
+// is counted in registers per lag and added to the block histogram once per
+// thread.
+template <int K>
+__global__ void __launch_bounds__(256) k_bin_state_v(StateBinArgs sa) {
+    extern __shared__ uint32_t sh[];   // K x (Q + 1): the k-th binned lag at k (Q + 1)
+    const Geom &geo = sa.geo;
+    const int w = 2 * geo.vmax + 1, q1 = w * w + 1;
+    const int center = geo.vmax * w + geo.vmax;
+    for (int b = threadIdx.x; b < q1 * K; b += blockDim.x) sh[b] = 0;
+    int lag[K];
+    {
+        uint32_t m = sa.mask;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            lag[k] = __ffs(m) - 1;
+            m &= m - 1u;
+        }
+    }
+    const bool sites = sa.site_n != nullptr && lag[0] == 0;
+    __syncthreads();
+    uint32_t rest[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) rest[k] = 0u;
+    const int64_t n = sa.n;
+    const int64_t ng = (n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ng; base += stride) {
+        const int64_t gi = base + threadIdx.x;
+        const int64_t j0 = 4 * gi;
+        const bool full = j0 + 3 < n;
+        uint32_t c[4], bef[K][4];
+        float2 p[4];
+        if (full) {
+            const uint4 cw = reinterpret_cast<const uint4 *>(sa.cell)[gi];
+            const float4 pa = reinterpret_cast<const float4 *>(sa.cl)[2 * gi];
+            const float4 pb = reinterpret_cast<const float4 *>(sa.cl)[2 * gi + 1];
+            c[0] = cw.x; c[1] = cw.y; c[2] = cw.z; c[3] = cw.w;
+            p[0] = make_float2(pa.x, pa.y);
+            p[1] = make_float2(pa.z, pa.w);
+            p[2] = make_float2(pb.x, pb.y);
+            p[3] = make_float2(pb.z, pb.w);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const uint4 b4 = reinterpret_cast<const uint4 *>(sa.lprev[lag[k]])[gi];
+                bef[k][0] = b4.x; bef[k][1] = b4.y; bef[k][2] = b4.z; bef[k][3] = b4.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool a = gi < ng && j0 + u < n;
+                c[u] = a ? sa.cell[j0 + u] : 0u;
+                p[u] = a ? sa.cl[j0 + u] : make_float2(1.f, 1.f);
+#pragma unroll
+                for (int k = 0; k < K; ++k) bef[k][u] = a ? sa.lprev[lag[k]][j0 + u] : 0u;
+            }
+        }
+        uint32_t now[4];
+        int32_t lx[4], ly[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int32_t bx = base_cell((int32_t)(c[u] & 0xffffu) * geo.k, p[u].x, geo.inv_g, geo.lg[0]);
+            const int32_t by = base_cell((int32_t)(c[u] >> 16) * geo.k, p[u].y, geo.inv_g, geo.lg[1]);
+            lx[u] = lattice_of_base(bx, geo.ratio, sa.ratio_shift);
+            ly[u] = lattice_of_base(by, geo.ratio, sa.ratio_shift);
+            now[u] = pack_cell(lx[u], ly[u]);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (full) {
+                reinterpret_cast<uint4 *>(sa.lprev[lag[k]])[gi] = make_uint4(now[0], now[1], now[2], now[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (gi < ng && j0 + u < n) sa.lprev[lag[k]][j0 + u] = now[u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool a = full || (gi < ng && j0 + u < n);
+                const int32_t vx = lattice_disp(lx[u] - (int32_t)(bef[k][u] & 0xffffu), geo.lat[0]);
+                const int32_t vy = lattice_disp(ly[u] - (int32_t)(bef[k][u] >> 16), geo.lat[1]);
+                const int32_t bin = vel_index(vx, vy, geo.vmax);
+                if (k == 0 && sites && a) {
+                    const int64_t site = (int64_t)ly[u] * geo.lat[0] + lx[u];
+                    atomicAdd(&sa.site_n[site], 1u);
+                    atomicAdd(&sa.site_counts[site * q1 + bin], 1u);
+                }
+                rest[k] += (a && bin == center) ? 1u : 0u;
+                if (a && bin != center) atomicAdd(&sh[k * q1 + bin], 1u);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        uint32_t r = rest[k];
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((threadIdx.x & 31) == 0 && r) atomicAdd(&sh[k * q1 + center], r);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) flush_hist(sh + k * q1, q1, sa.counts[lag[k]]);
 }
 
 // Batched systems: one chunk (one system) per block iteration, so the block's
@@ -489,29 +692,77 @@ cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t
     return cudaGetLastError();
 }
 
-template <int NC, bool ALLPOW2>
+template <int NC>
 cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *pos,
-                               const float *vel, unsigned long long *counts, cudaStream_t s) {
+                               const float *vel, unsigned long long *counts, bool allpow2,
+                               cudaStream_t s) {
     const int threads = 256;
     const int q1 = (2 * ga.vmax + 1) * (2 * ga.vmax + 1) + 1;
     const size_t smem = (size_t)q1 * NC * sizeof(uint32_t);
+    const float2 *p2 = reinterpret_cast<const float2 *>(pos);
+    const float2 *v2 = reinterpret_cast<const float2 *>(vel);
+    void (*kern)(IdealGasArgs, int64_t, const float2 *, const float2 *, unsigned long long *);
+    int64_t units = n;
+    if (allpow2) {
+        // two particles per thread when both arrays allow 16-byte loads
+        const bool vec = ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(vel)) & 15) == 0;
+        kern = vec ? k_idealgas_pow2<NC, 2> : k_idealgas_pow2<NC, 1>;
+        units = vec ? (n + 1) / 2 : n;
+    } else {
+        kern = k_idealgas_bin<NC, false>;
+    }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_idealgas_bin<NC, ALLPOW2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_idealgas_bin<NC, ALLPOW2><<<hist_grid(n, threads), threads, smem, s>>>(
-        ga, n, reinterpret_cast<const float2 *>(pos), reinterpret_cast<const float2 *>(vel), counts);
+    kern<<<hist_grid(units, threads), threads, smem, s>>>(ga, n, p2, v2, counts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_idealgas_bin(const IdealGasArgs &ga, int64_t n, const float *pos,
+cudaError_t launch_idealgas_bin(const IdealGasArgs &ga_in, int64_t n, const float *pos,
                                 const float *vel, unsigned long long *counts, cudaStream_t s) {
+    IdealGasArgs ga = ga_in;
     bool allpow2 = true;
     for (int k = 0; k < ga.ncombo; ++k) allpow2 = allpow2 && ga.pow2[k];
+    for (int k = 0; k < ga.ncombo; ++k) ga.out[k] = k;
+    if (allpow2) {
+        // order the pairs by (dt, U), then by dx; record each pair's output row
+        int ord[16];
+        for (int k = 0; k < ga.ncombo; ++k) ord[k] = k;
+        auto key_less = [&](int a, int b) {
+            if (ga.dt[a] != ga.dt[b]) return ga.dt[a] < ga.dt[b];
+            if (ga.boost && ga.ux[a] != ga.ux[b]) return ga.ux[a] < ga.ux[b];
+            if (ga.boost && ga.uy[a] != ga.uy[b]) return ga.uy[a] < ga.uy[b];
+            if (ga.dx[a] != ga.dx[b]) return ga.dx[a] < ga.dx[b];
+            return a < b;
+        };
+        for (int i = 1; i < ga.ncombo; ++i)   // insertion sort of at most 16 pairs
+            for (int j = i; j > 0 && key_less(ord[j], ord[j - 1]); --j) {
+                const int t = ord[j]; ord[j] = ord[j - 1]; ord[j - 1] = t;
+            }
+        float dxmin = ga.dx[0];
+        for (int k = 1; k < ga.ncombo; ++k) dxmin = fminf(dxmin, ga.dx[k]);
+        IdealGasArgs o = ga;
+        for (int k = 0; k < ga.ncombo; ++k) {
+            const int a = ord[k];
+            o.dx[k] = ga.dx[a];
+            o.dt[k] = ga.dt[a];
+            o.inv_dx[k] = ga.inv_dx[a];
+            o.pow2[k] = 1;
+            o.ux[k] = ga.ux[a];
+            o.uy[k] = ga.uy[a];
+            o.out[k] = a;
+            int sft = 0;   // dx_k / dx_min = 2^sft, both powers of two
+            while (sft < 62 && std::ldexp((double)dxmin, sft) < (double)o.dx[k]) ++sft;
+            o.shift[k] = sft;
+            o.first[k] = k == 0 || o.dt[k] != o.dt[k - 1] ||
+                         (ga.boost && (o.ux[k] != o.ux[k - 1] || o.uy[k] != o.uy[k - 1]));
+        }
+        o.inv_min = (float)(1.0 / (double)dxmin);
+        ga = o;
+    }
     switch (ga.ncombo) {
-#define MDLG_IG_CASE(K) case K: return allpow2 ? launch_idealgas_nc<K, true>(ga, n, pos, vel, counts, s) \
-                                               : launch_idealgas_nc<K, false>(ga, n, pos, vel, counts, s);
+#define MDLG_IG_CASE(K) case K: return launch_idealgas_nc<K>(ga, n, pos, vel, counts, allpow2, s);
         MDLG_IG_CASE(1) MDLG_IG_CASE(2) MDLG_IG_CASE(3) MDLG_IG_CASE(4) MDLG_IG_CASE(5)
         MDLG_IG_CASE(6) MDLG_IG_CASE(7) MDLG_IG_CASE(8) MDLG_IG_CASE(9) MDLG_IG_CASE(10)
         MDLG_IG_CASE(11) MDLG_IG_CASE(12) MDLG_IG_CASE(13) MDLG_IG_CASE(14) MDLG_IG_CASE(15)
@@ -535,6 +786,28 @@ cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
     }
     const int threads = 256;
     const bool msd = sa.msd_acc != nullptr, move = sa.shift.on != 0;
+    if (!msd && !move) {
+        const int K = __builtin_popcount(sa.mask);
+        void (*kv)(StateBinArgs) = nullptr;
+        switch (K) {
+            case 1: kv = k_bin_state_v<1>; break;
+            case 2: kv = k_bin_state_v<2>; break;
+            case 3: kv = k_bin_state_v<3>; break;
+            case 4: kv = k_bin_state_v<4>; break;
+            case 5: kv = k_bin_state_v<5>; break;
+            case 6: kv = k_bin_state_v<6>; break;
+            case 7: kv = k_bin_state_v<7>; break;
+            case 8: kv = k_bin_state_v<8>; break;
+            default: return cudaSuccess;
+        }
+        const size_t smv = (size_t)q1 * K * sizeof(uint32_t);
+        if (smv > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
+            if (e != cudaSuccess) return e;
+        }
+        kv<<<hist_grid((sa.n + 3) / 4, threads), threads, smv, s>>>(sa);
+        return cudaGetLastError();
+    }
     void (*kern)(StateBinArgs) = msd ? (move ? k_bin_state<true, true> : k_bin_state<true, false>)
                                      : (move ? k_bin_state<false, true> : k_bin_state<false, false>);
     if (smem > 48 * 1024) {

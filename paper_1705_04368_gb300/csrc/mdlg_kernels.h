@@ -78,6 +78,12 @@ struct IdealGasArgs {
     int32_t pow2[16];
     int32_t boost;             // 1: velocities boosted by (ux[k], uy[k]) per pair
     float ux[16], uy[16];
+    // every dx a power of two: the pairs are ordered so that pairs with the same
+    // (dt, U) are adjacent, and each decision is a shift of the cell at dx_min
+    int32_t out[16];           // counts row of pair k (the caller's order)
+    int32_t shift[16];         // log2(dx_k / dx_min)
+    int32_t first[16];         // 1: pair k is the first of its (dt, U) group
+    float inv_min;             // 1 / dx_min (a power of two)
 };
 
 // Lattice displacement S = (K + b) g per axis of a moving lattice, K in [0, lg),
@@ -138,6 +144,43 @@ struct Control {
     long long stats_acc[5];    // fixed-point sums of a running stats launch (zero at rest)
 };
 
+// ---- tiles of the sorted state (single systems) ------------------------------
+// A tile is up to kTileT consecutive slots of one MD-cell row.  Its neighbour
+// window is the slots of the cells [cxa - 1, cxb + 1] of the rows above, at and
+// below (cxa, cxb: the first and last cell column of the tile's particles),
+// stored as up to three segments per row: the wrapped left cell, the main
+// range and the wrapped right cell (or the whole row when the range would
+// cover it).  Each segment is staged from an even slot so that its copy starts
+// on a 16-byte boundary; the window index of slot j of segment s is
+// off[s] + (src[s] & 1) + (j - src[s]).  List entries of a tiled context are
+// 16 bits: window index | (o_x + 1) << 12 | (o_y + 1) << 14, four per 8-byte
+// word, word b of slot i at b n + i.
+constexpr int kTileT = 128;       // slots per tile, one thread each
+constexpr int kTileSegs = 9;      // three rows x (wrapped left cell, main range, wrapped right cell)
+constexpr int kTileWinCap = 640;  // window elements a block stages in shared memory
+constexpr int kTileNbMax = 8;     // list words per particle staged in shared memory
+
+struct TileDesc {
+    int32_t t0, cnt;              // first slot, particles
+    int32_t nb;                   // list words per particle to stage (max over the tile)
+    int32_t wlen;                 // window elements, alignment padding included
+    int32_t whole;                // bit r: window row r is its whole cell row
+    int32_t cxa, cxb;             // first and last cell column of the tile's particles
+    int32_t row;                  // the tile's cell row
+    int32_t src[kTileSegs];       // first slot of each segment
+    int32_t len[kTileSegs];       // its slots (0: absent)
+    int32_t off[kTileSegs];       // its first window element (even)
+    int32_t pad_[5];
+};
+
+struct TileArgs {
+    TileDesc *desc;               // max_tiles descriptors (null: no tiles)
+    int32_t *ntiles;              // tiles in use (device)
+    int32_t *row_tiles;           // nc_y + 1: tiles per cell row, then their exclusive prefix
+    int64_t max_tiles;
+    uint2 *list;                  // 16-bit entries, four per word
+};
+
 enum StepMode : int32_t {
     kModeStep = 0,   // F(x_n); v_{n+1/2} = v_{n-1/2} + F dt/m; x_{n+1} = x_n + v dt
     kModeInit = 1,   // F(x_0); v_{-1/2} = v_0 - F dt/(2m)        (positions kept)
@@ -169,6 +212,7 @@ struct StepArgs {
     int32_t stats;              // 1: FP64 reductions (Control::stats, or per system in a batch)
     Control *ctl;
     Batch batch;
+    TileArgs tile;              // tiled list (desc non-null): the staged-window step kernel
 };
 
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);
@@ -206,10 +250,14 @@ struct SortArgs {
     int32_t cap;
     float rl2;               // list radius squared
     Batch batch;
+    TileArgs tile;           // desc non-null: build tiles and the tiled 16-bit list instead
 };
 
 int64_t sort_scratch_blocks(int64_t ncells);
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
+// Verlet list (batches of four 32-bit entries) of an already sorted state.
+cudaError_t launch_nlist(const SortArgs &a, cudaStream_t s);
+int64_t max_tiles(int64_t n, int32_t rows);
 
 // Upload conversion: FP64 positions -> (cell, cl) in original order (unsorted).
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,

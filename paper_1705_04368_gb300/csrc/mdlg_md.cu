@@ -200,68 +200,14 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     }
 }
 
-// B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
-// per system); otherwise one system described by a.geo.
-template <int MODE, bool STATS, bool B, bool SF>
-__device__ __forceinline__ void step_body(const StepArgs &a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
-    const Geom &geo = sv.geo;
-    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
-    const bool act = i < a.n && (!B || cw != kGhostCell);
-    // origin shifts ((c_x - 1) w, (c_y - 1) w) of the 16 list offset codes of a
-    // regular neighbourhood (code 3: the padding entries' 2 w)
-    __shared__ float2 s_tab[16];
-    if (threadIdx.x < 16)
-        s_tab[threadIdx.x] = make_float2(fmaf((float)(threadIdx.x & 3u), a.cell_w, -a.cell_w),
-                                         fmaf((float)(threadIdx.x >> 2), a.cell_w, -a.cell_w));
-    __syncthreads();
-
-    // Neighbour-cell radius for the displacement bound of the input positions
-    // (evaluated only where it is used: the cell-stencil path and the check).
-    const float D = a.ctl->dbound;
-    const auto stencil_radius = [&]() {
-        const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
-        // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
-        return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
-    };
-    if (a.potential && threadIdx.x == 0 && blockIdx.x == 0) {
-        const int R = stencil_radius();
-        if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1])
-            set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
-    }
-    // the Verlet list holds every pair that can be closer than rc while 2D <= skin
-    const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
-
-    PairAcc acc = {0.f, 0.f, 0.f, 0.f};
-    float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-    if (act) {
-        p = a.cl_in[i];
-        v = a.v_in[i];
-        if (a.potential) {
-            const int32_t cx = cell_x(cw), cy = cell_y(cw);
-            const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
-            if (cnt <= a.cap) {
-                // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
-                if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
-                    forces_list<STATS, true, SF>(a, i, p, cnt, s_tab, 0.f, 0.f, 0.f, 0.f, acc);
-                } else {
-                    const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                    const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                    const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                    const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                    forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
-                }
-            } else {
-                const int R = stencil_radius();
-                int lox, hix, loy, hiy;
-                stencil(R, geo.nc[0], lox, hix);
-                stencil(R, geo.nc[1], loy, hiy);
-                forces_cells<STATS, SF>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
-                                    hiy, acc);
-            }
-        }
-    }
+// Integration, statistics and the launch-wide reductions of one step launch
+// (everything after the forces), shared by the list and the tiled kernels.
+// THREADS is the block size; every thread of every block of the launch calls
+// it exactly once.
+template <int MODE, bool STATS, bool B, int THREADS>
+__device__ __forceinline__ void step_finish(const StepArgs &a, const SysView &sv, int64_t i,
+                                            bool act, float2 p, float2 v, const PairAcc &acc,
+                                            float D) {
     const float fx = acc.fx, fy = acc.fy;
 
     float2 vn = v;   // velocity at the integer step (statistics)
@@ -286,7 +232,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
         }
     }
 
-    constexpr int kWarps = (B ? kChunk : kStepThreads) / 32;
+    constexpr int kWarps = THREADS / 32;
     __shared__ long long s_red[kWarps][kStatsN];
     __shared__ float s_max[kWarps];
     __shared__ int s_last;
@@ -351,6 +297,71 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
         }
         a.ctl->done = 0u;
     }
+}
+
+// B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
+// per system); otherwise one system described by a.geo.
+template <int MODE, bool STATS, bool B, bool SF>
+__device__ __forceinline__ void step_body(const StepArgs &a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
+    const Geom &geo = sv.geo;
+    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
+    const bool act = i < a.n && (!B || cw != kGhostCell);
+    // origin shifts ((c_x - 1) w, (c_y - 1) w) of the 16 list offset codes of a
+    // regular neighbourhood (code 3: the padding entries' 2 w)
+    __shared__ float2 s_tab[16];
+    if (threadIdx.x < 16)
+        s_tab[threadIdx.x] = make_float2(fmaf((float)(threadIdx.x & 3u), a.cell_w, -a.cell_w),
+                                         fmaf((float)(threadIdx.x >> 2), a.cell_w, -a.cell_w));
+    __syncthreads();
+
+    // Neighbour-cell radius for the displacement bound of the input positions
+    // (evaluated only where it is used: the cell-stencil path and the check).
+    const float D = a.ctl->dbound;
+    const auto stencil_radius = [&]() {
+        const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
+        // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
+        return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
+    };
+    if (a.potential && threadIdx.x == 0 && blockIdx.x == 0) {
+        const int R = stencil_radius();
+        if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1])
+            set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
+    }
+    // the Verlet list holds every pair that can be closer than rc while 2D <= skin
+    const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
+
+    PairAcc acc = {0.f, 0.f, 0.f, 0.f};
+    float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+    if (act) {
+        p = a.cl_in[i];
+        v = a.v_in[i];
+        if (a.potential) {
+            const int32_t cx = cell_x(cw), cy = cell_y(cw);
+            const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
+            if (cnt <= a.cap) {
+                // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
+                if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
+                    forces_list<STATS, true, SF>(a, i, p, cnt, s_tab, 0.f, 0.f, 0.f, 0.f, acc);
+                } else {
+                    const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                    const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                    const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                    const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                    forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
+                }
+            } else {
+                const int R = stencil_radius();
+                int lox, hix, loy, hiy;
+                stencil(R, geo.nc[0], lox, hix);
+                stencil(R, geo.nc[1], loy, hiy);
+                forces_cells<STATS, SF>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
+                                    hiy, acc);
+            }
+        }
+    }
+    step_finish<MODE, STATS, B, (B ? kChunk : kStepThreads)>(a, sv, i, act, p, v, acc, D);
 }
 
 // One system: 256-thread blocks, the register count left to the compiler.
@@ -640,6 +651,410 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
     }
 }
 
+// ---- tiles: shared-memory windows of the sorted state ------------------------
+//
+// After each sort the slots of every MD-cell row are cut into tiles of up to
+// kTileT slots (TileDesc).  The list build and the step kernel each run one
+// block per tile: the block's neighbour window (the tile's cells widened by
+// one cell, in the rows above, at and below) is staged in shared memory, and
+// list entries are window indices, so no list entry and no neighbour position
+// is fetched from global memory one particle at a time.
+
+constexpr int kTileDescWords = (int)(sizeof(TileDesc) / sizeof(int32_t));
+constexpr uint32_t kTileWaitPolls = 1u << 20;   // bounded wait for the staged copies
+constexpr int kErrTimeout = -6;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One bulk copy (TMA engine) of `bytes` (a multiple of 16) from global memory
+// to shared memory, both 16-byte aligned, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Wait for the barrier's phase `parity` to complete, polling at most `limit`
+// times; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t k = 0; k < limit; ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Elements staged for a segment: from its even first slot, rounded up to even.
+__device__ __forceinline__ int32_t seg_staged(int32_t src, int32_t len) {
+    return len > 0 ? (((src & 1) + len + 1) & ~1) : 0;
+}
+
+// Exclusive prefix of the tiles of cell rows before r (the scan of row_tiles).
+__device__ __forceinline__ int32_t tile_prefix(const SortArgs &a, int64_t r) {
+    return a.tile.row_tiles[r] + a.block_sums[r / kScanChunk];
+}
+
+// Tiles of every cell row, and a zero past the last row so that the scan also
+// yields the total.
+__global__ void k_tile_count(SortArgs a) {
+    const int32_t ncx = a.geo.nc[0], ncy = a.geo.nc[1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= ncy; r += stride) {
+        int32_t t = 0;
+        if (r < ncy) {
+            const int32_t pop = a.cell_start[(r + 1) * ncx] - a.cell_start[r * ncx];
+            t = (pop + kTileT - 1) / kTileT;
+        }
+        a.tile.row_tiles[r] = t;
+    }
+}
+
+// One thread per tile: its slots, cell columns and window segments.
+__global__ void k_tile_desc(SortArgs a) {
+    const int32_t ncx = a.geo.nc[0], ncy = a.geo.nc[1];
+    const int32_t *cs = a.cell_start;
+    const int32_t total = tile_prefix(a, ncy);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.tile.ntiles = total;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        // the row: the last r whose prefix is <= t
+        int32_t lo = 0, hi = ncy - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (tile_prefix(a, mid) <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t r = lo, k = (int32_t)t - tile_prefix(a, r);
+        const int32_t rs = cs[(int64_t)r * ncx], pop = cs[(int64_t)(r + 1) * ncx] - rs;
+        TileDesc d;
+        d.t0 = rs + k * kTileT;
+        d.cnt = min(kTileT, pop - k * kTileT);
+        d.nb = 0;
+        d.row = r;
+        d.cxa = cell_x(a.cell_out[d.t0]);
+        d.cxb = cell_x(a.cell_out[d.t0 + d.cnt - 1]);
+        const bool whole = d.cxb - d.cxa + 3 > ncx;
+        d.whole = whole ? 7 : 0;
+        int32_t off = 0;
+        for (int oy = 0; oy < 3; ++oy) {
+            const int64_t rb = (int64_t)wrap_mod(r + oy - 1, ncy) * ncx;
+            int32_t s3[3], l3[3];
+            if (whole) {
+                s3[0] = s3[2] = 0;
+                l3[0] = l3[2] = 0;
+                s3[1] = cs[rb];
+                l3[1] = cs[rb + ncx] - s3[1];
+            } else {
+                const int32_t clo = d.cxa > 0 ? d.cxa - 1 : 0;
+                const int32_t chi = d.cxb + 1 < ncx ? d.cxb + 1 : ncx - 1;
+                s3[0] = d.cxa == 0 ? cs[rb + ncx - 1] : 0;
+                l3[0] = d.cxa == 0 ? cs[rb + ncx] - s3[0] : 0;
+                s3[1] = cs[rb + clo];
+                l3[1] = cs[rb + chi + 1] - s3[1];
+                s3[2] = d.cxb == ncx - 1 ? cs[rb] : 0;
+                l3[2] = d.cxb == ncx - 1 ? cs[rb + 1] - s3[2] : 0;
+            }
+            for (int q = 0; q < 3; ++q) {
+                const int sg = 3 * oy + q;
+                d.src[sg] = s3[q];
+                d.len[sg] = l3[q];
+                d.off[sg] = off;
+                off += seg_staged(s3[q], l3[q]);
+            }
+        }
+        d.wlen = off;
+        for (int q = 0; q < 5; ++q) d.pad_[q] = 0;
+        a.tile.desc[t] = d;
+    }
+}
+
+// Window element of slot j of segment sg.
+__device__ __forceinline__ int32_t win_index(const TileDesc &d, int sg, int32_t j) {
+    return d.off[sg] + (d.src[sg] & 1) + (j - d.src[sg]);
+}
+
+// Slot of window element w (tiles whose window is not staged).
+__device__ __forceinline__ int32_t win_slot(const TileDesc &d, int32_t w) {
+    int32_t slot = 0;
+#pragma unroll
+    for (int sg = 0; sg < kTileSegs; ++sg) {
+        const int32_t st = seg_staged(d.src[sg], d.len[sg]);
+        if (w >= d.off[sg] && w < d.off[sg] + st) slot = (d.src[sg] & ~1) + (w - d.off[sg]);
+    }
+    return slot;
+}
+
+// Segment and cell column of the neighbouring column cx + ox - 1 in window row oy.
+__device__ __forceinline__ void win_cell(const TileDesc &d, int oy, int32_t vc, int32_t ncx,
+                                         int &sg, int32_t &c) {
+    if (!(d.whole & 1) && vc < 0) {
+        sg = 3 * oy;
+        c = ncx - 1;
+    } else if (!(d.whole & 1) && vc >= ncx) {
+        sg = 3 * oy + 2;
+        c = 0;
+    } else {
+        sg = 3 * oy + 1;
+        c = wrap_mod(vc, ncx);
+    }
+}
+
+// Verlet list of one tile per block, in the tiled format: candidates are read
+// from the staged window (or, for a window larger than the buffer, from
+// global memory through the same indices), and every entry is the window
+// index of the neighbour with its cell-offset code.  Entries are staged per
+// thread in shared memory (cap + 1 slots, the last one catching everything
+// past the capacity) and written as words of four, padded with the particle's
+// own window index at code 15 (two cell widths away on both axes).  The
+// tile's largest word count goes to its descriptor.
+__global__ void __launch_bounds__(kTileT) k_nlist_tile(SortArgs a) {
+    extern __shared__ uint16_t s_ent16[];        // kTileT x (cap + 1), column-major
+    __shared__ __align__(16) float2 win[kTileWinCap];
+    __shared__ __align__(16) TileDesc d;
+    __shared__ int s_nb;
+    const int tid = threadIdx.x;
+    const Geom &geo = a.geo;
+    const int32_t ncx = geo.nc[0], ncy = geo.nc[1];
+    const int32_t total = *a.tile.ntiles;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        if (tid < kTileDescWords)
+            reinterpret_cast<int32_t *>(&d)[tid] = reinterpret_cast<const int32_t *>(a.tile.desc + tile)[tid];
+        if (tid == 0) s_nb = 0;
+        __syncthreads();
+        const bool staged = d.wlen <= kTileWinCap;
+        if (staged) {
+            for (int sg = 0; sg < kTileSegs; ++sg) {
+                const int32_t st = seg_staged(d.src[sg], d.len[sg]);
+                const float2 *src = a.cl_out + (d.src[sg] & ~1);
+                for (int e = tid; e < st; e += kTileT) win[d.off[sg] + e] = src[e];
+            }
+        }
+        __syncthreads();
+        if (tid < d.cnt) {
+            const int64_t i = d.t0 + tid;
+            const uint32_t cw = a.cell_out[i];
+            const int32_t cx = cell_x(cw), cy = cell_y(cw);
+            const float2 p = a.cl_out[i];
+            const int last = a.cap;
+            const float sxm = (float)wrap_half((wrap_mod(cx - 1, ncx) - cx) * geo.k, geo.lg[0]) * geo.g;
+            const float sxp = (float)wrap_half((wrap_mod(cx + 1, ncx) - cx) * geo.k, geo.lg[0]) * geo.g;
+            int cnt = 0;
+            for (int oy = 0; oy < 3; ++oy) {
+                const int32_t ry = wrap_mod(cy + oy - 1, ncy);
+                const int64_t rb = (int64_t)ry * ncx;
+                const float ody = (float)wrap_half((ry - cy) * geo.k, geo.lg[1]) * geo.g;
+                for (int ox = 0; ox < 3; ++ox) {
+                    int sg;
+                    int32_t c;
+                    win_cell(d, oy, cx + ox - 1, ncx, sg, c);
+                    const int32_t j0 = a.cell_start[rb + c], j1 = a.cell_start[rb + c + 1];
+                    const int32_t w0 = win_index(d, sg, j0);
+                    const float2 *src = staged ? win + w0 : a.cl_out + j0;
+                    const float odx = ox == 0 ? sxm : (ox == 2 ? sxp : 0.0f);
+                    const uint32_t code = ((uint32_t)ox << 12) | ((uint32_t)oy << 14);
+                    const int32_t m = j1 - j0;
+                    for (int32_t b = 0; b < m; b += 4) {
+                        float2 q[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            q[u] = (b + u < m) ? src[b + u] : make_float2(1.0e18f, 1.0e18f);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
+                            const bool hit = b + u < m && j0 + b + u != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            s_ent16[min(cnt, last) * kTileT + tid] = (uint16_t)((uint32_t)(w0 + b + u) | code);
+                            cnt += hit;
+                        }
+                    }
+                }
+            }
+            if (cnt <= a.cap) {
+                const uint32_t pad = (uint32_t)win_index(d, 4, (int32_t)i) | 0xf000u;
+                for (int t = 0; t < cnt; t += kListBatch) {
+                    uint32_t e[kListBatch];
+#pragma unroll
+                    for (int u = 0; u < kListBatch; ++u)
+                        e[u] = t + u < cnt ? (uint32_t)s_ent16[(t + u) * kTileT + tid] : pad;
+                    a.tile.list[(int64_t)(t / kListBatch) * a.n + i] =
+                        make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+                }
+                atomicMax(&s_nb, (cnt + kListBatch - 1) / kListBatch);
+            }
+            a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
+        }
+        __syncthreads();
+        if (tid == 0) a.tile.desc[tile].nb = s_nb;
+        __syncthreads();   // the next tile reuses the shared arrays
+    }
+}
+
+// Pairs of one particle from the tiled list: every entry is a window index
+// (neighbour position from the staged window, or from global memory through
+// the segment map when the window was not staged) and a cell-offset code
+// (origin shifts as in forces_list).
+template <bool STATS, bool REGULAR, bool SF, bool STAGED>
+__device__ __forceinline__ void forces_tile(const StepArgs &a, const TileDesc &d, int tid, int64_t i,
+                                            float2 p, int cnt, const uint2 (*s_list)[kTileT + 2],
+                                            int nbs, const float2 *win, const float2 *tab, float sxm,
+                                            float sxp, float sym, float syp, PairAcc &acc) {
+    const float w = a.cell_w;
+    const int nb = (cnt + kListBatch - 1) / kListBatch;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t e0 = (int64_t)b * a.n + d.t0;
+        const uint2 wd = (STAGED && b < nbs) ? s_list[b][(int)(e0 & 1) + tid]
+                                             : a.tile.list[(int64_t)b * a.n + i];
+        const uint32_t ent[kListBatch] = {wd.x & 0xffffu, wd.x >> 16, wd.y & 0xffffu, wd.y >> 16};
+        float2 q[kListBatch];
+#pragma unroll
+        for (int u = 0; u < kListBatch; ++u) {
+            const int32_t wi = (int32_t)(ent[u] & 0x0fffu);
+            q[u] = STAGED ? win[wi] : __ldg(a.cl_in + win_slot(d, wi));
+        }
+#pragma unroll
+        for (int u = 0; u < kListBatch; ++u) {
+            float sx, sy;
+            if (REGULAR) {
+                const float2 o = tab[ent[u] >> 12];
+                sx = o.x;
+                sy = o.y;
+            } else {
+                const uint32_t ox = (ent[u] >> 12) & 3u, oy = ent[u] >> 14;
+                sx = ox == 0u ? sxm : (ox == 2u ? sxp : (ox == 3u ? 2.0f * w : 0.0f));
+                sy = oy == 0u ? sym : (oy == 2u ? syp : (oy == 3u ? 2.0f * w : 0.0f));
+            }
+            pair_term_masked<STATS, SF>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
+        }
+    }
+}
+
+// Step kernel of a tiled context: one block per tile.  Thread 0 issues bulk
+// copies (TMA engine) of the tile's window and of its first list words into
+// shared memory, all completing on one barrier, while every thread loads its
+// own particle; the pair loop then reads only shared memory.  Blocks past the
+// tile count take part in the launch-wide reductions only.
+template <int MODE, bool STATS, bool SF>
+__global__ void __launch_bounds__(kTileT) k_step_tile(StepArgs a) {
+    __shared__ __align__(16) float2 s_win[kTileWinCap];
+    __shared__ __align__(16) uint2 s_list[kTileNbMax][kTileT + 2];
+    __shared__ __align__(16) TileDesc d;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ float2 s_tab[16];
+    const int tid = threadIdx.x;
+    const Geom &geo = a.geo;
+    const int32_t total = *a.tile.ntiles;
+    const bool live = (int64_t)blockIdx.x < total;
+    if (live && tid < kTileDescWords)
+        reinterpret_cast<int32_t *>(&d)[tid] = reinterpret_cast<const int32_t *>(a.tile.desc + blockIdx.x)[tid];
+    if (tid < 16)
+        s_tab[tid] = make_float2(fmaf((float)(tid & 3), a.cell_w, -a.cell_w),
+                                 fmaf((float)(tid >> 2), a.cell_w, -a.cell_w));
+    const float D = a.ctl->dbound;
+    const auto stencil_radius = [&]() {
+        const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
+        return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
+    };
+    if (a.potential && tid == 0 && blockIdx.x == 0) {
+        const int R = stencil_radius();
+        if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1]) set_status(a.ctl, kErrOverflow);
+    }
+    const bool list_ok = a.tile.list != nullptr && 2.0f * D <= a.list_skin;
+    __syncthreads();
+
+    const int64_t i = live ? (int64_t)d.t0 + tid : 0;
+    const bool act = live && tid < d.cnt;
+    const bool staged = live && a.potential && list_ok && d.wlen <= kTileWinCap;
+    const int nbs = staged ? min(d.nb, kTileNbMax) : 0;
+    if (staged && tid == 0) {
+        mbar_init(&s_bar, 1);
+        uint32_t bytes = 0;
+        for (int sg = 0; sg < kTileSegs; ++sg) bytes += 8u * (uint32_t)seg_staged(d.src[sg], d.len[sg]);
+        for (int b = 0; b < nbs; ++b) {
+            const int64_t e0 = (int64_t)b * a.n + d.t0;
+            bytes += 8u * (uint32_t)((((int)(e0 & 1)) + d.cnt + 1) & ~1);
+        }
+        mbar_expect_tx(&s_bar, bytes);
+        for (int sg = 0; sg < kTileSegs; ++sg) {
+            const int32_t st = seg_staged(d.src[sg], d.len[sg]);
+            if (st > 0) bulk_g2s(s_win + d.off[sg], a.cl_in + (d.src[sg] & ~1), 8u * (uint32_t)st, &s_bar);
+        }
+        for (int b = 0; b < nbs; ++b) {
+            const int64_t e0 = (int64_t)b * a.n + d.t0;
+            const int a0 = (int)(e0 & 1);
+            bulk_g2s(&s_list[b][0], a.tile.list + (e0 - a0), 8u * (uint32_t)((a0 + d.cnt + 1) & ~1), &s_bar);
+        }
+    }
+    PairAcc acc = {0.f, 0.f, 0.f, 0.f};
+    float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+    uint32_t cw = 0u;
+    int cnt = a.cap + 1;
+    if (act) {
+        cw = a.cell[i];
+        p = a.cl_in[i];
+        v = a.v_in[i];
+        if (list_ok) cnt = a.ncount[i];
+    }
+    __syncthreads();   // the barrier's initialisation is visible to every thread
+    if (staged && !mbar_wait(&s_bar, 0, kTileWaitPolls)) {
+        set_status(a.ctl, kErrTimeout);
+        mbar_wait(&s_bar, 0, kTileWaitPolls);   // let the copies land before the block exits
+    }
+    if (act && a.potential) {
+        const int32_t cx = cell_x(cw), cy = cell_y(cw);
+        if (cnt <= a.cap) {
+            const bool regular = cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1];
+            if (staged && regular) {
+                forces_tile<STATS, true, SF, true>(a, d, tid, i, p, cnt, s_list, nbs, s_win, s_tab,
+                                                   0.f, 0.f, 0.f, 0.f, acc);
+            } else {
+                const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
+                const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
+                if (staged)
+                    forces_tile<STATS, false, SF, true>(a, d, tid, i, p, cnt, s_list, nbs, s_win, s_tab,
+                                                        sxm, sxp, sym, syp, acc);
+                else
+                    forces_tile<STATS, false, SF, false>(a, d, tid, i, p, cnt, s_list, 0, s_win, s_tab,
+                                                         sxm, sxp, sym, syp, acc);
+            }
+        } else {
+            const int R = stencil_radius();
+            int lox, hix, loy, hiy;
+            stencil(R, geo.nc[0], lox, hix);
+            stencil(R, geo.nc[1], loy, hiy);
+            forces_cells<STATS, SF>(a, geo, a.cell_start, i, cx, cy, p, lox, hix, loy, hiy, acc);
+        }
+    }
+    SysView sv;
+    sv.geo = geo;
+    sv.cell0 = 0;
+    sv.ncells = geo.nc[0] * geo.nc[1];
+    sv.sys = 0;
+    step_finish<MODE, STATS, false, kTileT>(a, sv, i, act, p, v, acc, D);
+}
+
 // ---- upload / download conversions ----------------------------------------
 
 // Largest |v|^2 of the block's uploaded velocities into ctl->vmax0_bits: the
@@ -783,7 +1198,27 @@ void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStrea
     }
 }
 
+template <bool SF>
+void launch_step_tile_t(const StepArgs &a, int mode, dim3 grid, cudaStream_t s) {
+    const dim3 block(kTileT);
+    if (mode == kModeStep) {
+        if (a.stats) k_step_tile<kModeStep, true, SF><<<grid, block, 0, s>>>(a);
+        else k_step_tile<kModeStep, false, SF><<<grid, block, 0, s>>>(a);
+    } else if (mode == kModeInit) {
+        k_step_tile<kModeInit, true, SF><<<grid, block, 0, s>>>(a);
+    } else {
+        k_step_tile<kModeSync, true, SF><<<grid, block, 0, s>>>(a);
+    }
+}
+
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
+    if (!a.batch.sys && a.tile.desc) {
+        // one block per possible tile; blocks past the tile count only join the reductions
+        const dim3 grid((unsigned)a.tile.max_tiles);
+        if (a.potential == 2) launch_step_tile_t<true>(a, mode, grid, s);
+        else launch_step_tile_t<false>(a, mode, grid, s);
+        return cudaGetLastError();
+    }
     const int threads = a.batch.sys ? kChunk : kStepThreads;
     const int64_t blocks = (a.n + threads - 1) / threads;
     if (blocks < 1) return cudaSuccess;
@@ -813,6 +1248,23 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_sort_place<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
     k_sort_scatter<B><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    if (!B && a.tile.desc) {
+        // tiles of the new order (the cell scan's block sums are free again
+        // and hold the row scan's), then the tiled list
+        const int32_t rows = a.geo.nc[1];
+        k_tile_count<<<grid_for(rows + 1, t), t, 0, s>>>(a);
+        const int64_t nbr = sort_scratch_blocks(rows + 1);
+        k_scan_local<<<(unsigned)nbr, kScanThreads, 0, s>>>(a.tile.row_tiles, rows + 1, a.block_sums);
+        k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nbr);
+        k_tile_desc<<<grid_for(a.tile.max_tiles, t), t, 0, s>>>(a);
+        const size_t smem = sizeof(uint16_t) * (size_t)kTileT * (a.cap + 1);
+        if (smem > 32 * 1024) {
+            e = cudaFuncSetAttribute(k_nlist_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_nlist_tile<<<grid_for(a.tile.max_tiles, kTileT, 16), kTileT, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.nbr) {
         const int nt = (size_t)kNlistThreads * (a.cap + 1) * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
         const size_t smem = sizeof(uint32_t) * (size_t)nt * (a.cap + 1);
@@ -825,6 +1277,20 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     }
     return cudaGetLastError();
 }
+
+cudaError_t launch_nlist(const SortArgs &a, cudaStream_t s) {
+    const int nt = (size_t)kNlistThreads * (a.cap + 1) * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
+    const size_t smem = sizeof(uint32_t) * (size_t)nt * (a.cap + 1);
+    void (*kern)(SortArgs) = a.batch.sys ? k_nlist<true> : k_nlist<false>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid_for(a.n, nt, 32), nt, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int64_t max_tiles(int64_t n, int32_t rows) { return n / kTileT + rows + 1; }
 
 // In a batch, a.ncells counts every system's cells plus its ghost cell.
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s) {

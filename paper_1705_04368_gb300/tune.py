@@ -78,26 +78,35 @@ def time_candidate(params: Params, x0, v0, steps: int, warmup: int, stream=None)
 
 def tune(params: Params, x0, v0, temperature: float,
          candidates: Iterable[tuple] = DEFAULT_CANDIDATES, steps: int = 140, warmup: int = 14,
-         timer: Optional[Callable] = None, path: Optional[str] = None, refresh: bool = False):
+         timer: Optional[Callable] = None, path: Optional[str] = None, refresh: bool = False,
+         key: Optional[str] = None, extents: Optional[Iterable[float]] = None,
+         keep_sort_every: bool = False):
     """Best (grid, skin) for this workload; returns (params with them set, report).
 
     ``timer(params, x0, v0, steps, warmup) -> seconds per step`` defaults to a
     CUDA-event measurement; candidates whose grid does not divide the lattice
-    spacing and box, or that fail to build, are skipped.
+    spacing and every box extent (``extents``, default the params' box), or that
+    fail to build, are skipped.  ``key`` overrides the cache key;
+    ``keep_sort_every`` keeps the caller's re-sort interval instead of letting
+    the library derive one per candidate.
     """
     path = path or cache_path()
-    key = workload_key(params, temperature)
+    key = key or workload_key(params, temperature)
     cache = _load(path)
     if key in cache and not refresh:
         g, sk = cache[key]["grid"], cache[key]["skin"]
         return replace(params, grid=g, skin=sk), {"key": key, "cached": True, **cache[key]}
     timer = timer or time_candidate
+    if extents is None:
+        extents = (params.box, params.box) if np.isscalar(params.box) else params.box
+    extents = [float(v) for v in extents]
     results = []
     for g, sk in candidates:
-        box = (params.box, params.box) if np.isscalar(params.box) else params.box
-        if any(abs(v / g - round(v / g)) > 1e-9 for v in (params.dx, *box)):
+        if any(abs(v / g - round(v / g)) > 1e-9 for v in (params.dx, *extents)):
             continue
-        cand = replace(params, grid=float(g), skin=float(sk), sort_every=0)
+        cand = replace(params, grid=float(g), skin=float(sk))
+        if not keep_sort_every:
+            cand = replace(cand, sort_every=0)
         try:
             sec = float(timer(cand, x0, v0, steps, warmup))
         except Exception as exc:       # a candidate that cannot be built is skipped
@@ -114,3 +123,40 @@ def tune(params: Params, x0, v0, temperature: float,
     _store(path, cache)
     return replace(params, grid=best["grid"], skin=best["skin"]), {"key": key, "cached": False,
                                                                    **entry}
+
+
+def time_batch_candidate(params: Params, ns, boxes, x0, v0, steps: int, warmup: int,
+                         stream=None) -> float:
+    """Seconds per MD step of a replica batch under one candidate geometry."""
+    import torch
+    from .binding import BatchSimulation
+    s = stream if stream is not None else torch.cuda.Stream()
+    with BatchSimulation(params, ns, boxes, x0, v0, stream=s) as bt:
+        bt.step(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        bt.step(steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+
+def tune_batch(params: Params, ns, boxes, x0, v0, temperature: float,
+               candidates: Iterable[tuple] = DEFAULT_CANDIDATES, steps: int = 140,
+               warmup: int = 14, path: Optional[str] = None, refresh: bool = False):
+    """Best (grid, skin) for a batch of replicas (every system shares the geometry);
+    returns (params, report).  The caller's re-sort interval is kept (0: the library
+    derives one per candidate)."""
+    ns = np.asarray(ns)
+    boxes = np.asarray(boxes, dtype=np.float64)
+    rho = float(ns.sum() / np.prod(boxes, axis=1).sum())
+    key = (f"batch nsys={len(ns)} n={_sig(float(ns.sum()))} rho={_sig(rho)} "
+           f"T={_sig(temperature)} dt={params.dt:g} rc={params.rcut:g} "
+           f"sort_every={params.sort_every}")
+
+    def timer(cand, x0_, v0_, steps_, warmup_):
+        return time_batch_candidate(cand, ns, boxes, x0_, v0_, steps_, warmup_)
+
+    return tune(params, x0, v0, temperature, candidates, steps, warmup, timer=timer, path=path,
+                refresh=refresh, key=key, extents=boxes.ravel(), keep_sort_every=True)

@@ -169,3 +169,16 @@ def test_checkpoint_entry_points_validate():
 
 def test_adjoint_rejects_null_context():
     assert m.lib().mdlg_adjoint(None, 10, 10, 1.0, None, None, None, None, None, None, None) == -1
+
+
+def test_probes_validate_arguments_before_launching():
+    L = m.lib()
+    buf = ctypes.c_void_p(16)
+    assert L.mdlg_probe_fma(0, 256, 10, buf, None, None) == -1
+    assert L.mdlg_probe_fma(4, 48, 10, buf, None, None) == -1      # not a multiple of 32
+    assert L.mdlg_probe_fma(4, 512, 10, buf, None, None) == -1     # above 256
+    assert L.mdlg_probe_fma(4, 256, 0, buf, None, None) == -1
+    assert L.mdlg_probe_fma(4, 256, 10, None, None, None) == -1
+    assert L.mdlg_probe_copy(buf, buf, 24, None) == -1             # not a multiple of 16
+    assert L.mdlg_probe_copy(ctypes.c_void_p(8), buf, 32, None) == -1   # misaligned
+    assert L.mdlg_probe_copy(buf, buf, 0, None) == 0

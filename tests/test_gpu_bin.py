@@ -140,3 +140,32 @@ def test_idealgas_largest_window_and_pair_count(cuda):
     assert np.array_equal(got, ref)
     assert np.all(got.sum(axis=1) == 200_003)
 
+
+
+@pytest.mark.parametrize("boost", [False, True])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_idealgas_pow2_groups_bit_exact(cuda, boost, offset):
+    # Every dx a power of two (0.5 ... 8), pairs given out of (dt, dx) order, dt
+    # values shared by non-adjacent pairs, an odd particle count; with drifts,
+    # pairs that share dt but not U.  offset = 1 starts both arrays 8 bytes into
+    # a buffer (no 16-byte loads).
+    import torch
+    n = 100_003
+    pos, vel = mi.idealgas_state(n + offset, 512.0, 1.0, seed=31)
+    combos = [(2.0, 1.0), (0.5, 0.25), (8.0, 1.0), (1.0, 0.25), (2.0, 0.25), (4.0, 1.5),
+              (1.0, 1.0), (0.5, 1.5), (2.0, 1.0)]
+    us = None
+    if boost:
+        us = np.array([[0.4, 0.0], [0.0, 0.0], [0.4, 0.0], [-0.3, 0.2], [0.0, 0.0], [1.1, -0.9],
+                       [0.4, 0.0], [0.0, 0.0], [0.0, 0.5]], np.float32)
+    pb = torch.from_numpy(pos).to(cuda)
+    vb = torch.from_numpy(vel).to(cuda)
+    p, v = pb[offset:], vb[offset:]
+    counts = torch.zeros((len(combos), 50), dtype=torch.int64, device=cuda)
+    m.idealgas_bin(p, v, combos, 3, counts, us=us)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().view(np.uint64)
+    ref = oracle.stream_bin_f32(pos[offset:], vel[offset:], [c[0] for c in combos],
+                                [c[1] for c in combos], 3, us=us)
+    assert np.array_equal(got, ref)
+    assert np.all(got.sum(axis=1) == n)

@@ -42,3 +42,28 @@ def test_tuner_skips_grids_that_do_not_divide(tmp_path):
                           path=str(tmp_path / "t.json"))
     assert seen == [0.5] and best.grid == 0.5
     assert "rho=1" in rep["key"] and "n=1e+02" in rep["key"]
+
+
+def test_batch_tuning_keeps_sort_interval_and_checks_every_box(tmp_path):
+    # the batch variant: candidates must divide every system's box, the caller's
+    # re-sort interval is kept, and the cache key describes the ensemble
+    ns = np.array([1000, 3000])
+    boxes = np.array([[60.0, 60.0], [100.0, 100.0]])
+    p = m.Params(n=0, box=64.0, dx=4.0, sort_every=7)
+    seen = []
+
+    def fake(cand, ns_, boxes_, x0, v0, steps, warmup):
+        seen.append((cand.grid, cand.skin, cand.sort_every))
+        return 1.0 + cand.skin
+
+    orig = tune.time_batch_candidate
+    tune.time_batch_candidate = fake
+    try:
+        best, rep = tune.tune_batch(p, ns, boxes, None, None, 1.0,
+                                    candidates=((0.5, 0.5), (0.3, 0.25), (0.25, 0.75)),
+                                    path=str(tmp_path / "b.json"))
+    finally:
+        tune.time_batch_candidate = orig
+    assert [s[0] for s in seen] == [0.5, 0.25] and all(s[2] == 7 for s in seen)
+    assert (best.grid, best.skin, best.sort_every) == (0.5, 0.5, 7)
+    assert rep["key"].startswith("batch nsys=2 n=4e+03")

@@ -60,8 +60,11 @@ struct mdlg_ctx {
     float list_radius = 0.f;
     // tiles of the sorted state (single systems with a potential)
     TileDesc *tdesc = nullptr;
+    TileLane *tlanes = nullptr;
     int32_t *ntiles = nullptr, *row_tiles = nullptr;
     int64_t max_tiles = 0;
+    int32_t list_stage = 0;       // tiled-list entries a step-kernel stage holds
+    size_t nbr_bytes = 0;
     bool want_tiles = false;      // sorts build the tiled list
     bool list_tiles = false;      // the current list is the tiled one
     // host-side schedule
@@ -245,7 +248,9 @@ TileArgs tile_args(mdlg_ctx *c) {
     t.ntiles = c->ntiles;
     t.row_tiles = c->row_tiles;
     t.max_tiles = c->max_tiles;
-    t.list = reinterpret_cast<uint2 *>(c->nbr);
+    t.list = reinterpret_cast<uint16_t *>(c->nbr);
+    t.lanes = c->tlanes;
+    t.list_stage = c->list_stage;
     return t;
 }
 
@@ -580,7 +585,7 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     for (int b = 0; b < 2; ++b) {
         // two spare offsets: staged window copies round their end up to 16 bytes
         if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N + 2)) ||
-            (rc = alloc_n(c, &c->vel[b], N)) || (rc = alloc_n(c, &c->pid[b], N)))
+            (rc = alloc_n(c, &c->vel[b], N + 2)) || (rc = alloc_n(c, &c->pid[b], N)))
             return fail(rc);
         for (int l = 0; l < p.nlags; ++l) {
             if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
@@ -623,14 +628,32 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
         if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x (cap + 1) words of shared memory
-        if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
+        // one buffer holds either list format: cap 32-bit entries per slot, or
+        // (one system) cap 16-bit entries per tile slot plus 16 bytes of slack
+        // for the staged copies' rounding
+        c->nbr_bytes = sizeof(uint32_t) * (size_t)c->cap * N;
+        if (nsys == 0) {
+            c->max_tiles = max_tiles(c->slots, g.nc[1]);
+            const size_t tb = sizeof(uint16_t) * (size_t)c->max_tiles * kTileT * c->cap + 16;
+            if (tb > c->nbr_bytes) c->nbr_bytes = tb;
+        }
+        c->nbr_bytes = (c->nbr_bytes + 15) & ~(size_t)15;
+        if ((rc = alloc_n(c, &c->nbr, c->nbr_bytes / sizeof(uint32_t))) || (rc = alloc_n(c, &c->ncount, N)))
             return fail(rc);
         if (nsys == 0) {
-            // one system: tiles with staged windows and the 16-bit list
-            c->max_tiles = max_tiles(c->slots, g.nc[1]);
-            if ((rc = alloc_n(c, &c->tdesc, (size_t)c->max_tiles)) || (rc = alloc_n(c, &c->ntiles, 1)) ||
+            // one system: tiles with staged windows, lane tables and the 16-bit list
+            if ((rc = alloc_n(c, &c->tdesc, (size_t)c->max_tiles)) ||
+                (rc = alloc_n(c, &c->tlanes, (size_t)c->max_tiles * kTileLanes)) ||
+                (rc = alloc_n(c, &c->ntiles, 1)) ||
                 (rc = alloc_n(c, &c->row_tiles, (size_t)g.nc[1] + 1)))
                 return fail(rc);
+            // entries a stage holds: a tile's mean plus six standard deviations
+            // (counts are near Poisson), at most the tile's capacity
+            const double et = kTileT * mean;
+            int64_t ls = (int64_t)std::ceil(et + 6.0 * std::sqrt(et) + 64.0);
+            ls = (ls + 7) / 8 * 8;
+            if (ls > (int64_t)kTileT * c->cap) ls = (int64_t)kTileT * c->cap;
+            c->list_stage = (int32_t)ls;
             c->want_tiles = true;
         }
     }
@@ -1411,11 +1434,12 @@ std::vector<Region> ckpt_regions(mdlg_ctx *c) {
     }
     r.push_back({c->cell_start, ((size_t)c->ncells + 1) * sizeof(int32_t)});
     if (c->nbr) {
-        r.push_back({c->nbr, (size_t)c->cap * N * sizeof(uint32_t)});
+        r.push_back({c->nbr, c->nbr_bytes});
         r.push_back({c->ncount, N * sizeof(int32_t)});
     }
     if (c->list_tiles) {
         r.push_back({c->tdesc, (size_t)c->max_tiles * sizeof(TileDesc)});
+        r.push_back({c->tlanes, (size_t)c->max_tiles * kTileLanes * sizeof(TileLane)});
         r.push_back({c->ntiles, sizeof(int32_t)});
     }
     r.push_back({c->ctl, sizeof(Control)});

@@ -152,19 +152,36 @@ struct Control {
 // range and the wrapped right cell (or the whole row when the range would
 // cover it).  Each segment is staged from an even slot so that its copy starts
 // on a 16-byte boundary; the window index of slot j of segment s is
-// off[s] + (src[s] & 1) + (j - src[s]).  List entries of a tiled context are
-// 16 bits: window index | (o_x + 1) << 12 | (o_y + 1) << 14, four per 8-byte
-// word, word b of slot i at b n + i.
-constexpr int kTileT = 128;       // slots per tile, one thread each
-constexpr int kTileSegs = 9;      // three rows x (wrapped left cell, main range, wrapped right cell)
-constexpr int kTileWinCap = 640;  // window elements a block stages in shared memory
-constexpr int kTileNbMax = 8;     // list words per particle staged in shared memory
+// off[s] + (src[s] & 1) + (j - src[s]).
+//
+// The tiled Verlet list holds, per tile, the entries of its particles one
+// after another (no padding), 16 bits each: window index | x-shift code << 10
+// | y-shift code << 13.  A shift code names the neighbour cell's origin minus
+// the particle's cell origin along one axis (kShift* below; the wrapped codes
+// cross the periodic boundary next to the last, possibly wider, cell).  The
+// particles of a tile are ranked by entry count, and step-kernel lane l
+// (0 <= l < kTileT / 2) takes ranks l and kTileT - 1 - l, so that every lane
+// has about the same number of entries: the tile's lane table gives each
+// lane its two slots, their counts and the offset of its entries.
+constexpr int kTileT = 128;        // slots per tile
+constexpr int kTileLanes = kTileT / 2;
+constexpr int kTileSegs = 9;       // three rows x (wrapped left cell, main range, wrapped right cell)
+constexpr int kTileWinCap = 512;   // window elements a stage holds (entry indices have 10 bits)
+constexpr int kTileWinMax = 1024;  // larger windows: the tile's particles use the cell stencil
+constexpr uint16_t kTileOverflow = 0xffffu;   // lane-table count of a particle past the capacity
+enum ShiftCode : int32_t {
+    kShiftMinus = 0,       // origin - w
+    kShiftZero = 1,        // same column / row
+    kShiftPlus = 2,        // origin + w
+    kShiftWrapMinus = 3,   // across the boundary to the last cell: -(its width)
+    kShiftWrapPlus = 4,    // from the last cell across the boundary: +(its width)
+};
 
 struct TileDesc {
     int32_t t0, cnt;              // first slot, particles
-    int32_t nb;                   // list words per particle to stage (max over the tile)
+    int32_t ne;                   // list entries of the tile
     int32_t wlen;                 // window elements, alignment padding included
-    int32_t whole;                // bit r: window row r is its whole cell row
+    int32_t whole;                // 1: every window row is its whole cell row
     int32_t cxa, cxb;             // first and last cell column of the tile's particles
     int32_t row;                  // the tile's cell row
     int32_t src[kTileSegs];       // first slot of each segment
@@ -173,12 +190,24 @@ struct TileDesc {
     int32_t pad_[5];
 };
 
+// One step-kernel lane of a tile: slots (offsets from t0; 0xff: none) of the
+// particles of ranks l and kTileT - 1 - l, their entry counts (kTileOverflow:
+// list past the capacity, use the cell stencil) and the first entry of the
+// lane in the tile's list.
+struct TileLane {
+    uint8_t a, b;
+    uint16_t ca, cb;
+    uint16_t off;
+};
+
 struct TileArgs {
     TileDesc *desc;               // max_tiles descriptors (null: no tiles)
     int32_t *ntiles;              // tiles in use (device)
     int32_t *row_tiles;           // nc_y + 1: tiles per cell row, then their exclusive prefix
     int64_t max_tiles;
-    uint2 *list;                  // 16-bit entries, four per word
+    uint16_t *list;               // entries: tile t's at t * kTileT * cap
+    TileLane *lanes;              // max_tiles x kTileLanes
+    int32_t list_stage;           // entries a stage holds (the rest are read from global memory)
 };
 
 enum StepMode : int32_t {

@@ -200,6 +200,30 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     }
 }
 
+// The velocity-Verlet update of one particle for the launch mode, with its
+// integer-step velocity vn (statistics) and squared half-step speed (MODE step).
+template <int MODE>
+__device__ __forceinline__ void integrate_one(const StepArgs &a, int64_t i, float2 p, float2 v,
+                                              float fx, float fy, float2 &vn, float &vmax2) {
+    if (MODE == kModeStep) {
+        vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
+        const float2 vh = make_float2(fmaf(fx, a.dt_m, v.x), fmaf(fy, a.dt_m, v.y));
+        const float2 pn = make_float2(fmaf(vh.x, a.dt, p.x), fmaf(vh.y, a.dt, p.y));
+        a.v_out[i] = vh;
+        a.cl_out[i] = pn;
+        vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
+        if (!(vmax2 < 3.0e38f) || !(fabsf(pn.x) < 3.0e38f) || !(fabsf(pn.y) < 3.0e38f))
+            set_status(a.ctl, kErrNonFinite);
+    } else if (MODE == kModeInit) {
+        vn = v;
+        a.v_out[i] = make_float2(fmaf(-fx, a.half_dt_m, v.x), fmaf(-fy, a.half_dt_m, v.y));
+    } else {
+        vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
+        a.v_sync[i] = vn;
+        if (a.f_sync) a.f_sync[i] = make_float2(fx, fy);
+    }
+}
+
 // Integration, statistics and the launch-wide reductions of one step launch
 // (everything after the forces), shared by the list and the tiled kernels.
 // THREADS is the block size; every thread of every block of the launch calls
@@ -208,29 +232,9 @@ template <int MODE, bool STATS, bool B, int THREADS>
 __device__ __forceinline__ void step_finish(const StepArgs &a, const SysView &sv, int64_t i,
                                             bool act, float2 p, float2 v, const PairAcc &acc,
                                             float D) {
-    const float fx = acc.fx, fy = acc.fy;
-
     float2 vn = v;   // velocity at the integer step (statistics)
     float vmax2 = 0.f;
-    if (act) {
-        if (MODE == kModeStep) {
-            vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
-            const float2 vh = make_float2(fmaf(fx, a.dt_m, v.x), fmaf(fy, a.dt_m, v.y));
-            const float2 pn = make_float2(fmaf(vh.x, a.dt, p.x), fmaf(vh.y, a.dt, p.y));
-            a.v_out[i] = vh;
-            a.cl_out[i] = pn;
-            vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
-            if (!(vmax2 < 3.0e38f) || !(fabsf(pn.x) < 3.0e38f) || !(fabsf(pn.y) < 3.0e38f))
-                set_status(a.ctl, kErrNonFinite);
-        } else if (MODE == kModeInit) {
-            vn = v;
-            a.v_out[i] = make_float2(fmaf(-fx, a.half_dt_m, v.x), fmaf(-fy, a.half_dt_m, v.y));
-        } else {
-            vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
-            a.v_sync[i] = vn;
-            if (a.f_sync) a.f_sync[i] = make_float2(fx, fy);
-        }
-    }
+    if (act) integrate_one<MODE>(a, i, p, v, acc.fx, acc.fy, vn, vmax2);
 
     constexpr int kWarps = THREADS / 32;
     __shared__ long long s_red[kWarps][kStatsN];
@@ -654,15 +658,18 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
 // ---- tiles: shared-memory windows of the sorted state ------------------------
 //
 // After each sort the slots of every MD-cell row are cut into tiles of up to
-// kTileT slots (TileDesc).  The list build and the step kernel each run one
-// block per tile: the block's neighbour window (the tile's cells widened by
-// one cell, in the rows above, at and below) is staged in shared memory, and
-// list entries are window indices, so no list entry and no neighbour position
-// is fetched from global memory one particle at a time.
+// kTileT slots (TileDesc).  The list build runs one block per tile and writes
+// the tile's entries as window indices, grouped by step-kernel lane.  The step
+// kernel is persistent: each block walks its share of the tiles, and while it
+// computes one tile the next tile's window, own positions and velocities, lane
+// table and entries are being copied into the other half of its shared memory
+// by the TMA engine, so the pair loop only ever reads shared memory.
 
 constexpr int kTileDescWords = (int)(sizeof(TileDesc) / sizeof(int32_t));
 constexpr uint32_t kTileWaitPolls = 1u << 20;   // bounded wait for the staged copies
 constexpr int kErrTimeout = -6;
+constexpr int kStepTileThreads = kTileLanes;    // lane l takes ranks l and kTileT - 1 - l
+constexpr uint8_t kNoSlot = 0xff;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -751,12 +758,12 @@ __global__ void k_tile_desc(SortArgs a) {
         TileDesc d;
         d.t0 = rs + k * kTileT;
         d.cnt = min(kTileT, pop - k * kTileT);
-        d.nb = 0;
+        d.ne = 0;
         d.row = r;
         d.cxa = cell_x(a.cell_out[d.t0]);
         d.cxb = cell_x(a.cell_out[d.t0 + d.cnt - 1]);
         const bool whole = d.cxb - d.cxa + 3 > ncx;
-        d.whole = whole ? 7 : 0;
+        d.whole = whole ? 1 : 0;
         int32_t off = 0;
         for (int oy = 0; oy < 3; ++oy) {
             const int64_t rb = (int64_t)wrap_mod(r + oy - 1, ncy) * ncx;
@@ -806,13 +813,14 @@ __device__ __forceinline__ int32_t win_slot(const TileDesc &d, int32_t w) {
     return slot;
 }
 
-// Segment and cell column of the neighbouring column cx + ox - 1 in window row oy.
+// Segment and cell column of the neighbouring column vc = cx + ox - 1 in
+// window row oy.
 __device__ __forceinline__ void win_cell(const TileDesc &d, int oy, int32_t vc, int32_t ncx,
                                          int &sg, int32_t &c) {
-    if (!(d.whole & 1) && vc < 0) {
+    if (!d.whole && vc < 0) {
         sg = 3 * oy;
         c = ncx - 1;
-    } else if (!(d.whole & 1) && vc >= ncx) {
+    } else if (!d.whole && vc >= ncx) {
         sg = 3 * oy + 2;
         c = 0;
     } else {
@@ -821,30 +829,41 @@ __device__ __forceinline__ void win_cell(const TileDesc &d, int oy, int32_t vc, 
     }
 }
 
-// Verlet list of one tile per block, in the tiled format: candidates are read
-// from the staged window (or, for a window larger than the buffer, from
-// global memory through the same indices), and every entry is the window
-// index of the neighbour with its cell-offset code.  Entries are staged per
-// thread in shared memory (cap + 1 slots, the last one catching everything
-// past the capacity) and written as words of four, padded with the particle's
-// own window index at code 15 (two cell widths away on both axes).  The
-// tile's largest word count goes to its descriptor.
+// Shift code (ShiftCode) of the neighbouring column or row c + o - 1,
+// o in {0, 1, 2}, of a particle in column or row c of nc.
+__device__ __forceinline__ uint32_t shift_code(int o, int32_t c, int32_t nc) {
+    return o == 1 ? (uint32_t)kShiftZero
+                  : (o == 0 ? (uint32_t)(c == 0 ? kShiftWrapMinus : kShiftMinus)
+                            : (uint32_t)(c == nc - 1 ? kShiftWrapPlus : kShiftPlus));
+}
+
+// Verlet list of one tile per block in the tiled format.  Candidates come from
+// the staged window; every entry is the neighbour's window index with its
+// shift codes, staged per thread in shared memory (cap + 1 slots, the last one
+// catching everything past the capacity).  The tile's particles are then
+// ranked by entry count (ties by slot), lane l gets ranks l and kTileT-1-l,
+// and the entries are written lane after lane, each lane's first particle
+// first.  A window beyond kTileWinMax elements cannot be indexed: the tile's
+// particles then take the cell stencil (lane counts kTileOverflow).
 __global__ void __launch_bounds__(kTileT) k_nlist_tile(SortArgs a) {
     extern __shared__ uint16_t s_ent16[];        // kTileT x (cap + 1), column-major
-    __shared__ __align__(16) float2 win[kTileWinCap];
+    __shared__ __align__(16) float2 win[kTileWinMax];
     __shared__ __align__(16) TileDesc d;
-    __shared__ int s_nb;
+    __shared__ int32_t s_cnt[kTileT];            // entries; -1: no particle, -2: overflowed
+    __shared__ uint8_t s_rank_slot[kTileT];
+    __shared__ int32_t s_dst[kTileT];
+    __shared__ int32_t s_wsum[2];
     const int tid = threadIdx.x;
     const Geom &geo = a.geo;
     const int32_t ncx = geo.nc[0], ncy = geo.nc[1];
     const int32_t total = *a.tile.ntiles;
+    const int64_t region = (int64_t)kTileT * a.cap;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
         if (tid < kTileDescWords)
             reinterpret_cast<int32_t *>(&d)[tid] = reinterpret_cast<const int32_t *>(a.tile.desc + tile)[tid];
-        if (tid == 0) s_nb = 0;
         __syncthreads();
-        const bool staged = d.wlen <= kTileWinCap;
-        if (staged) {
+        const bool listable = d.wlen <= kTileWinMax;
+        if (listable) {
             for (int sg = 0; sg < kTileSegs; ++sg) {
                 const int32_t st = seg_staged(d.src[sg], d.len[sg]);
                 const float2 *src = a.cl_out + (d.src[sg] & ~1);
@@ -852,6 +871,7 @@ __global__ void __launch_bounds__(kTileT) k_nlist_tile(SortArgs a) {
             }
         }
         __syncthreads();
+        int cnt = -1;
         if (tid < d.cnt) {
             const int64_t i = d.t0 + tid;
             const uint32_t cw = a.cell_out[i];
@@ -860,21 +880,37 @@ __global__ void __launch_bounds__(kTileT) k_nlist_tile(SortArgs a) {
             const int last = a.cap;
             const float sxm = (float)wrap_half((wrap_mod(cx - 1, ncx) - cx) * geo.k, geo.lg[0]) * geo.g;
             const float sxp = (float)wrap_half((wrap_mod(cx + 1, ncx) - cx) * geo.k, geo.lg[0]) * geo.g;
-            int cnt = 0;
+            // the three neighbouring columns lie in one contiguous run of the
+            // window row's main segment unless a wrapped cell is involved
+            const bool run = !d.whole && cx >= 1 && cx + 1 < ncx;
+            cnt = 0;
+            // every row's cell boundaries are loaded before any candidate is
+            // tested: the run's four boundaries, or (wrapped or whole rows) the
+            // start of each of the three cells
+            int32_t bnd[3][4];
+#pragma unroll
             for (int oy = 0; oy < 3; ++oy) {
+                const int64_t rb = (int64_t)wrap_mod(cy + oy - 1, ncy) * ncx;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    bnd[oy][q] = !listable ? 0
+                                 : run ? __ldg(a.cell_start + rb + cx - 1 + q)
+                                       : (q < 3 ? __ldg(a.cell_start + rb + wrap_mod(cx + q - 1, ncx)) : 0);
+            }
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy) {
+                if (!listable) break;
                 const int32_t ry = wrap_mod(cy + oy - 1, ncy);
-                const int64_t rb = (int64_t)ry * ncx;
                 const float ody = (float)wrap_half((ry - cy) * geo.k, geo.lg[1]) * geo.g;
-                for (int ox = 0; ox < 3; ++ox) {
-                    int sg;
-                    int32_t c;
-                    win_cell(d, oy, cx + ox - 1, ncx, sg, c);
-                    const int32_t j0 = a.cell_start[rb + c], j1 = a.cell_start[rb + c + 1];
-                    const int32_t w0 = win_index(d, sg, j0);
-                    const float2 *src = staged ? win + w0 : a.cl_out + j0;
-                    const float odx = ox == 0 ? sxm : (ox == 2 ? sxp : 0.0f);
-                    const uint32_t code = ((uint32_t)ox << 12) | ((uint32_t)oy << 14);
-                    const int32_t m = j1 - j0;
+                const uint32_t ycode = shift_code(oy, cy, ncy) << 13;
+                if (run) {
+                    // cells cx-1, cx, cx+1: window indices [w0, w0 + m), inner
+                    // boundaries at the starts of cells cx and cx+1
+                    const int32_t j0 = bnd[oy][0], m = bnd[oy][3] - j0;
+                    const int32_t g1 = bnd[oy][1] - j0, g2 = bnd[oy][2] - j0;
+                    const int32_t w0 = win_index(d, 3 * oy + 1, j0);
+                    const int32_t islot = (int32_t)(i - j0);   // the particle itself, if in this run
+                    const float2 *src = win + w0;
                     for (int32_t b = 0; b < m; b += 4) {
                         float2 q[4];
 #pragma unroll
@@ -882,94 +918,260 @@ __global__ void __launch_bounds__(kTileT) k_nlist_tile(SortArgs a) {
                             q[u] = (b + u < m) ? src[b + u] : make_float2(1.0e18f, 1.0e18f);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
+                            const int32_t k = b + u;
+                            const bool in1 = k >= g1, in2 = k >= g2;
+                            const float odx = in2 ? sxp : (in1 ? 0.0f : sxm);
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            const bool hit = b + u < m && j0 + b + u != i && fmaf(dx, dx, dy * dy) < a.rl2;
-                            s_ent16[min(cnt, last) * kTileT + tid] = (uint16_t)((uint32_t)(w0 + b + u) | code);
+                            const bool hit = k < m && k != islot && fmaf(dx, dx, dy * dy) < a.rl2;
+                            const uint32_t xcode = in2 ? (uint32_t)kShiftPlus
+                                                       : (in1 ? (uint32_t)kShiftZero : (uint32_t)kShiftMinus);
+                            s_ent16[min(cnt, last) * kTileT + tid] =
+                                (uint16_t)((uint32_t)(w0 + k) | (xcode << 10) | ycode);
                             cnt += hit;
                         }
                     }
+                    continue;
                 }
-            }
-            if (cnt <= a.cap) {
-                const uint32_t pad = (uint32_t)win_index(d, 4, (int32_t)i) | 0xf000u;
-                for (int t = 0; t < cnt; t += kListBatch) {
-                    uint32_t e[kListBatch];
+                const int64_t rb = (int64_t)ry * ncx;
 #pragma unroll
-                    for (int u = 0; u < kListBatch; ++u)
-                        e[u] = t + u < cnt ? (uint32_t)s_ent16[(t + u) * kTileT + tid] : pad;
-                    a.tile.list[(int64_t)(t / kListBatch) * a.n + i] =
-                        make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+                for (int ox = 0; ox < 3; ++ox) {
+                    int sg;
+                    int32_t c;
+                    win_cell(d, oy, cx + ox - 1, ncx, sg, c);
+                    const int32_t j0 = bnd[oy][ox], j1 = __ldg(a.cell_start + rb + c + 1);
+                    const int32_t w0 = win_index(d, sg, j0);
+                    const float odx = ox == 0 ? sxm : (ox == 2 ? sxp : 0.0f);
+                    const uint32_t code = (shift_code(ox, cx, ncx) << 10) | ycode;
+                    for (int32_t k = 0; k < j1 - j0; ++k) {
+                        const float2 q = win[w0 + k];
+                        const float dx = (p.x - q.x) - odx, dy = (p.y - q.y) - ody;
+                        const bool hit = j0 + k != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                        s_ent16[min(cnt, last) * kTileT + tid] = (uint16_t)((uint32_t)(w0 + k) | code);
+                        cnt += hit;
+                    }
                 }
-                atomicMax(&s_nb, (cnt + kListBatch - 1) / kListBatch);
             }
-            a.ncount[i] = cnt <= a.cap ? cnt : a.cap + 1;
+            const bool ovf = !listable || cnt > a.cap;
+            a.ncount[i] = ovf ? a.cap + 1 : cnt;
+            cnt = ovf ? -2 : cnt;
+        }
+        s_cnt[tid] = cnt;
+        __syncthreads();
+        // rank by entry count, most first (overflowed particles count as none)
+        if (cnt != -1) {
+            const int key = cnt < 0 ? 0 : cnt;
+            int rank = 0;
+            for (int j = 0; j < d.cnt; ++j) {
+                const int kj = s_cnt[j] < 0 ? 0 : s_cnt[j];
+                rank += (kj > key) || (kj == key && j < tid);
+            }
+            s_rank_slot[rank] = (uint8_t)tid;
         }
         __syncthreads();
-        if (tid == 0) a.tile.desc[tile].nb = s_nb;
+        // lane table: lane l takes ranks l and kTileT-1-l; its entries at the
+        // exclusive prefix of the lane sums
+        int lsum = 0;
+        uint8_t sa = kNoSlot, sb = kNoSlot;
+        uint16_t ca = 0, cb = 0;
+        if (tid < kTileLanes) {
+            const int rb = kTileT - 1 - tid;
+            if (tid < d.cnt) {
+                sa = s_rank_slot[tid];
+                const int c = s_cnt[sa];
+                ca = c == -2 ? kTileOverflow : (uint16_t)c;
+                lsum += c > 0 ? c : 0;
+            }
+            if (rb < d.cnt) {
+                sb = s_rank_slot[rb];
+                const int c = s_cnt[sb];
+                cb = c == -2 ? kTileOverflow : (uint16_t)c;
+                lsum += c > 0 ? c : 0;
+            }
+        }
+        // exclusive scan over the kTileLanes lanes (two warps)
+        const int lane = tid & 31, warp = tid >> 5;
+        int inc = lsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31 && warp < 2) s_wsum[warp] = inc;
+        __syncthreads();
+        if (tid < kTileLanes) {
+            const int off = inc - lsum + (warp == 1 ? s_wsum[0] : 0);
+            if (sa != kNoSlot) s_dst[sa] = off;
+            if (sb != kNoSlot) s_dst[sb] = off + (ca == kTileOverflow ? 0 : ca);
+            TileLane ln;
+            ln.a = sa;
+            ln.b = sb;
+            ln.ca = ca;
+            ln.cb = cb;
+            ln.off = (uint16_t)off;
+            a.tile.lanes[tile * kTileLanes + tid] = ln;
+            if (tid == kTileLanes - 1) a.tile.desc[tile].ne = off + lsum;
+        }
+        __syncthreads();
+        if (cnt > 0) {
+            uint16_t *dst = a.tile.list + tile * region + s_dst[tid];
+            for (int k = 0; k < cnt; ++k) dst[k] = s_ent16[k * kTileT + tid];
+        }
         __syncthreads();   // the next tile reuses the shared arrays
     }
 }
 
-// Pairs of one particle from the tiled list: every entry is a window index
-// (neighbour position from the staged window, or from global memory through
-// the segment map when the window was not staged) and a cell-offset code
-// (origin shifts as in forces_list).
-template <bool STATS, bool REGULAR, bool SF, bool STAGED>
-__device__ __forceinline__ void forces_tile(const StepArgs &a, const TileDesc &d, int tid, int64_t i,
-                                            float2 p, int cnt, const uint2 (*s_list)[kTileT + 2],
-                                            int nbs, const float2 *win, const float2 *tab, float sxm,
-                                            float sxp, float sym, float syp, PairAcc &acc) {
-    const float w = a.cell_w;
-    const int nb = (cnt + kListBatch - 1) / kListBatch;
-    for (int b = 0; b < nb; ++b) {
-        const int64_t e0 = (int64_t)b * a.n + d.t0;
-        const uint2 wd = (STAGED && b < nbs) ? s_list[b][(int)(e0 & 1) + tid]
-                                             : a.tile.list[(int64_t)b * a.n + i];
-        const uint32_t ent[kListBatch] = {wd.x & 0xffffu, wd.x >> 16, wd.y & 0xffffu, wd.y >> 16};
-        float2 q[kListBatch];
+// Per-block reductions of a persistent step launch (every thread once):
+// the largest squared speed and the exact statistics sums of the block's
+// particles go to the control block; the last block publishes the launch's
+// totals and the new displacement bound.
+template <int MODE, bool STATS>
+__device__ __forceinline__ void tile_finish(const StepArgs &a, float vmax2, const long long *lsum,
+                                            float D) {
+    constexpr int kWarps = kStepTileThreads / 32;
+    __shared__ long long s_red[kWarps][kStatsN];
+    __shared__ float s_max[kWarps];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MODE == kModeStep) {
+        const float m = warp_max(vmax2);
+        if (lane == 0) s_max[warp] = m;
+    }
+    if (STATS) {
 #pragma unroll
-        for (int u = 0; u < kListBatch; ++u) {
-            const int32_t wi = (int32_t)(ent[u] & 0x0fffu);
-            q[u] = STAGED ? win[wi] : __ldg(a.cl_in + win_slot(d, wi));
+        for (int k = 0; k < kStatsN; ++k) {
+            const long long r = warp_sum_ll(lsum[k]);
+            if (lane == 0) s_red[warp][k] = r;
         }
-#pragma unroll
-        for (int u = 0; u < kListBatch; ++u) {
-            float sx, sy;
-            if (REGULAR) {
-                const float2 o = tab[ent[u] >> 12];
-                sx = o.x;
-                sy = o.y;
-            } else {
-                const uint32_t ox = (ent[u] >> 12) & 3u, oy = ent[u] >> 14;
-                sx = ox == 0u ? sxm : (ox == 2u ? sxp : (ox == 3u ? 2.0f * w : 0.0f));
-                sy = oy == 0u ? sym : (oy == 2u ? syp : (oy == 3u ? 2.0f * w : 0.0f));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (MODE == kModeStep) {
+            float m = 0.f;
+            for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_max[w]);
+            atomicMax(&a.ctl->vmax2_bits, __float_as_uint(m));
+        }
+        if (STATS) {
+            for (int k = 0; k < kStatsN; ++k) {
+                long long t = 0;
+                for (int w = 0; w < kWarps; ++w) t += s_red[w][k];
+                atomicAdd((unsigned long long *)&a.ctl->stats_acc[k], (unsigned long long)t);
             }
-            pair_term_masked<STATS, SF>(a, (p.x - q[u].x) - sx, (p.y - q[u].y) - sy, acc);
+        }
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctl->done, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (STATS && threadIdx.x < kStatsN) {
+        const long long t =
+            (long long)atomicExch((unsigned long long *)&a.ctl->stats_acc[threadIdx.x], 0ull);
+        a.ctl->stats[threadIdx.x] = (double)t * kFixInv;
+    }
+    if (threadIdx.x == 0) {
+        if (MODE == kModeStep) {
+            const uint32_t bits = atomicExch(&a.ctl->vmax2_bits, 0u);
+            const float vmax = sqrtf(__uint_as_float(bits));
+            a.ctl->dbound = D + vmax * a.dt * 1.000001f + a.round_margin;
+        }
+        a.ctl->done = 0u;
+    }
+}
+
+// Shared-memory layout of one stage of the persistent step kernel.
+struct TileStage {
+    static constexpr int kWin = 0;                                        // float2[kTileWinCap]
+    static constexpr int kCl = kWin + 8 * kTileWinCap;                    // float2[kTileT + 2]
+    static constexpr int kV = kCl + 8 * (kTileT + 2);                     // float2[kTileT + 2]
+    static constexpr int kLanes = kV + 8 * (kTileT + 2);                  // TileLane[kTileLanes]
+    static constexpr int kList = kLanes + (int)sizeof(TileLane) * kTileLanes;   // uint16[list_stage]
+    static __host__ __device__ int bytes(int list_stage) {
+        return kList + ((2 * list_stage + 15) & ~15);
+    }
+};
+
+// Issue the copies of tile `tile` into stage buffer `st` (one thread).  The
+// window and the entries are staged only when the list is in use; own
+// positions, velocities and the lane table always.
+__device__ __forceinline__ void tile_issue(const StepArgs &a, const TileDesc &d, int64_t tile,
+                                           unsigned char *st, uint64_t *bar, bool use_list) {
+    const int32_t a0 = d.t0 & 1;
+    const uint32_t own = 8u * (uint32_t)((a0 + d.cnt + 1) & ~1);
+    const bool win = use_list && d.wlen <= kTileWinCap;
+    const int32_t nst = use_list ? min(d.ne, a.tile.list_stage) : 0;
+    const uint32_t lbytes = (uint32_t)((2 * nst + 15) & ~15);
+    uint32_t bytes = 2u * own + (uint32_t)sizeof(TileLane) * kTileLanes + lbytes;
+    if (win)
+        for (int sg = 0; sg < kTileSegs; ++sg) bytes += 8u * (uint32_t)seg_staged(d.src[sg], d.len[sg]);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(st + TileStage::kCl, a.cl_in + (d.t0 - a0), own, bar);
+    bulk_g2s(st + TileStage::kV, a.v_in + (d.t0 - a0), own, bar);
+    bulk_g2s(st + TileStage::kLanes, a.tile.lanes + tile * kTileLanes,
+             (uint32_t)sizeof(TileLane) * kTileLanes, bar);
+    if (lbytes) bulk_g2s(st + TileStage::kList, a.tile.list + tile * (int64_t)kTileT * a.cap, lbytes, bar);
+    if (win) {
+        for (int sg = 0; sg < kTileSegs; ++sg) {
+            const int32_t ns = seg_staged(d.src[sg], d.len[sg]);
+            if (ns > 0)
+                bulk_g2s(st + TileStage::kWin + 8 * d.off[sg], a.cl_in + (d.src[sg] & ~1), 8u * (uint32_t)ns, bar);
         }
     }
 }
 
-// Step kernel of a tiled context: one block per tile.  Thread 0 issues bulk
-// copies (TMA engine) of the tile's window and of its first list words into
-// shared memory, all completing on one barrier, while every thread loads its
-// own particle; the pair loop then reads only shared memory.  Blocks past the
-// tile count take part in the launch-wide reductions only.
+// Pairs of one particle from its entries [e0, e0 + c) of the tile's list.
+template <bool STATS, bool SF, bool WIN>
+__device__ __forceinline__ void forces_tile(const StepArgs &a, const TileDesc &d, int64_t tile,
+                                            const unsigned char *st, const float2 *tab, float2 p,
+                                            int e0, int c, PairAcc &acc) {
+    const uint16_t *sl = reinterpret_cast<const uint16_t *>(st + TileStage::kList);
+    const float2 *win = reinterpret_cast<const float2 *>(st + TileStage::kWin);
+    const uint16_t *gl = a.tile.list + tile * (int64_t)kTileT * a.cap;
+    const int nst = min(d.ne, a.tile.list_stage);
+    const int e1 = e0 + c;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+        const uint32_t ent = e < nst ? sl[e] : gl[e];
+        const int32_t wi = (int32_t)(ent & 0x3ffu);
+        const float2 q = WIN ? win[wi] : __ldg(a.cl_in + win_slot(d, wi));
+        const float2 sh = tab[ent >> 10];
+        pair_term_masked<STATS, SF>(a, (p.x - q.x) - sh.x, (p.y - q.y) - sh.y, acc);
+    }
+}
+
+// Step kernel of a tiled context, persistent: block b computes tiles b,
+// b + gridDim.x, ...  While it computes one, the copies of its next tile are
+// in flight into the other stage buffer; the descriptor after that is loaded
+// into registers one tile ahead.  Lane l of the block handles the particles
+// of ranks l and kTileT-1-l of the tile.  Statistics and the speed bound are
+// accumulated over all of a block's particles and reduced once.
 template <int MODE, bool STATS, bool SF>
-__global__ void __launch_bounds__(kTileT) k_step_tile(StepArgs a) {
-    __shared__ __align__(16) float2 s_win[kTileWinCap];
-    __shared__ __align__(16) uint2 s_list[kTileNbMax][kTileT + 2];
-    __shared__ __align__(16) TileDesc d;
-    __shared__ __align__(8) uint64_t s_bar;
-    __shared__ float2 s_tab[16];
+__global__ void __launch_bounds__(kStepTileThreads) k_step_tile(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(16) TileDesc s_desc[2];
+    __shared__ float2 s_tab[64];
     const int tid = threadIdx.x;
     const Geom &geo = a.geo;
+    const int stage_bytes = TileStage::bytes(a.tile.list_stage);
     const int32_t total = *a.tile.ntiles;
-    const bool live = (int64_t)blockIdx.x < total;
-    if (live && tid < kTileDescWords)
-        reinterpret_cast<int32_t *>(&d)[tid] = reinterpret_cast<const int32_t *>(a.tile.desc + blockIdx.x)[tid];
-    if (tid < 16)
-        s_tab[tid] = make_float2(fmaf((float)(tid & 3), a.cell_w, -a.cell_w),
-                                 fmaf((float)(tid >> 2), a.cell_w, -a.cell_w));
+    const int64_t G = gridDim.x;
+    {
+        // origin shift of every (x code, y code) pair (ShiftCode)
+        const float w = a.cell_w;
+        const float wlx = (float)(geo.lg[0] - (geo.nc[0] - 1) * geo.k) * geo.g;
+        const float wly = (float)(geo.lg[1] - (geo.nc[1] - 1) * geo.k) * geo.g;
+        const int xc = tid & 7, yc = tid >> 3;
+        const auto shift_of = [&](int code, float wl) {
+            return code == kShiftMinus ? -w : code == kShiftPlus ? w
+                 : code == kShiftWrapMinus ? -wl : code == kShiftWrapPlus ? wl : 0.f;
+        };
+        s_tab[tid] = make_float2(shift_of(xc, wlx), shift_of(yc, wly));
+    }
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+    }
     const float D = a.ctl->dbound;
     const auto stencil_radius = [&]() {
         const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
@@ -979,80 +1181,84 @@ __global__ void __launch_bounds__(kTileT) k_step_tile(StepArgs a) {
         const int R = stencil_radius();
         if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1]) set_status(a.ctl, kErrOverflow);
     }
-    const bool list_ok = a.tile.list != nullptr && 2.0f * D <= a.list_skin;
-    __syncthreads();
+    const bool use_list = a.potential && a.tile.list != nullptr && 2.0f * D <= a.list_skin;
+    int lox = 0, hix = 0, loy = 0, hiy = 0;
+    if (a.potential && !use_list) {
+        const int R = stencil_radius();
+        stencil(R, geo.nc[0], lox, hix);
+        stencil(R, geo.nc[1], loy, hiy);
+    }
+    int64_t t = blockIdx.x;
+    if (t < total && tid < kTileDescWords)
+        reinterpret_cast<int32_t *>(&s_desc[0])[tid] = reinterpret_cast<const int32_t *>(a.tile.desc + t)[tid];
+    __syncthreads();   // barriers initialised, first descriptor in place
+    if (t < total && tid == 0) tile_issue(a, s_desc[0], t, s_dyn, &s_bar[0], use_list);
+    // the descriptor after the next one travels one tile ahead in registers
+    int32_t dnext = (t + G < total && tid < kTileDescWords)
+                        ? reinterpret_cast<const int32_t *>(a.tile.desc + t + G)[tid] : 0;
 
-    const int64_t i = live ? (int64_t)d.t0 + tid : 0;
-    const bool act = live && tid < d.cnt;
-    const bool staged = live && a.potential && list_ok && d.wlen <= kTileWinCap;
-    const int nbs = staged ? min(d.nb, kTileNbMax) : 0;
-    if (staged && tid == 0) {
-        mbar_init(&s_bar, 1);
-        uint32_t bytes = 0;
-        for (int sg = 0; sg < kTileSegs; ++sg) bytes += 8u * (uint32_t)seg_staged(d.src[sg], d.len[sg]);
-        for (int b = 0; b < nbs; ++b) {
-            const int64_t e0 = (int64_t)b * a.n + d.t0;
-            bytes += 8u * (uint32_t)((((int)(e0 & 1)) + d.cnt + 1) & ~1);
+    float vmax2 = 0.f;
+    long long lsum[kStatsN] = {0, 0, 0, 0, 0};
+    bool timed_out = false;
+    for (int k = 0; t < total; ++k, t += G) {
+        const int s = k & 1;
+        unsigned char *st = s_dyn + s * stage_bytes;
+        const int64_t tn = t + G;
+        if (tn < total) {
+            if (tid < kTileDescWords) reinterpret_cast<int32_t *>(&s_desc[s ^ 1])[tid] = dnext;
+            __syncthreads();
+            if (tid == 0)
+                tile_issue(a, s_desc[s ^ 1], tn, s_dyn + (s ^ 1) * stage_bytes, &s_bar[s ^ 1], use_list);
+            dnext = (tn + G < total && tid < kTileDescWords)
+                        ? reinterpret_cast<const int32_t *>(a.tile.desc + tn + G)[tid] : 0;
         }
-        mbar_expect_tx(&s_bar, bytes);
-        for (int sg = 0; sg < kTileSegs; ++sg) {
-            const int32_t st = seg_staged(d.src[sg], d.len[sg]);
-            if (st > 0) bulk_g2s(s_win + d.off[sg], a.cl_in + (d.src[sg] & ~1), 8u * (uint32_t)st, &s_bar);
-        }
-        for (int b = 0; b < nbs; ++b) {
-            const int64_t e0 = (int64_t)b * a.n + d.t0;
-            const int a0 = (int)(e0 & 1);
-            bulk_g2s(&s_list[b][0], a.tile.list + (e0 - a0), 8u * (uint32_t)((a0 + d.cnt + 1) & ~1), &s_bar);
-        }
-    }
-    PairAcc acc = {0.f, 0.f, 0.f, 0.f};
-    float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-    uint32_t cw = 0u;
-    int cnt = a.cap + 1;
-    if (act) {
-        cw = a.cell[i];
-        p = a.cl_in[i];
-        v = a.v_in[i];
-        if (list_ok) cnt = a.ncount[i];
-    }
-    __syncthreads();   // the barrier's initialisation is visible to every thread
-    if (staged && !mbar_wait(&s_bar, 0, kTileWaitPolls)) {
-        set_status(a.ctl, kErrTimeout);
-        mbar_wait(&s_bar, 0, kTileWaitPolls);   // let the copies land before the block exits
-    }
-    if (act && a.potential) {
-        const int32_t cx = cell_x(cw), cy = cell_y(cw);
-        if (cnt <= a.cap) {
-            const bool regular = cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1];
-            if (staged && regular) {
-                forces_tile<STATS, true, SF, true>(a, d, tid, i, p, cnt, s_list, nbs, s_win, s_tab,
-                                                   0.f, 0.f, 0.f, 0.f, acc);
-            } else {
-                const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
-                const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                if (staged)
-                    forces_tile<STATS, false, SF, true>(a, d, tid, i, p, cnt, s_list, nbs, s_win, s_tab,
-                                                        sxm, sxp, sym, syp, acc);
-                else
-                    forces_tile<STATS, false, SF, false>(a, d, tid, i, p, cnt, s_list, 0, s_win, s_tab,
-                                                         sxm, sxp, sym, syp, acc);
+        if (!mbar_wait(&s_bar[s], (uint32_t)((k >> 1) & 1), kTileWaitPolls)) timed_out = true;
+        const TileDesc &d = s_desc[s];
+        const bool win = d.wlen <= kTileWinCap;
+        const TileLane ln = reinterpret_cast<const TileLane *>(st + TileStage::kLanes)[tid];
+        const float2 *scl = reinterpret_cast<const float2 *>(st + TileStage::kCl) + (d.t0 & 1);
+        const float2 *sv = reinterpret_cast<const float2 *>(st + TileStage::kV) + (d.t0 & 1);
+        int e0 = ln.off;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const uint8_t slot = h == 0 ? ln.a : ln.b;
+            const uint16_t c = h == 0 ? ln.ca : ln.cb;
+            if (slot == kNoSlot) continue;
+            const int64_t i = (int64_t)d.t0 + slot;
+            const float2 p = scl[slot], v = sv[slot];
+            PairAcc acc = {0.f, 0.f, 0.f, 0.f};
+            if (a.potential) {
+                if (use_list && c != kTileOverflow) {
+                    if (win) forces_tile<STATS, SF, true>(a, d, t, st, s_tab, p, e0, c, acc);
+                    else forces_tile<STATS, SF, false>(a, d, t, st, s_tab, p, e0, c, acc);
+                    e0 += c;
+                } else {
+                    int lx = lox, hx = hix, ly = loy, hy = hiy;
+                    if (use_list) {   // this particle's list overflowed: the current bound's stencil
+                        const int R = stencil_radius();
+                        stencil(R, geo.nc[0], lx, hx);
+                        stencil(R, geo.nc[1], ly, hy);
+                    }
+                    const uint32_t cw = a.cell[i];
+                    forces_cells<STATS, SF>(a, geo, a.cell_start, i, cell_x(cw), cell_y(cw), p, lx, hx,
+                                            ly, hy, acc);
+                }
             }
-        } else {
-            const int R = stencil_radius();
-            int lox, hix, loy, hiy;
-            stencil(R, geo.nc[0], lox, hix);
-            stencil(R, geo.nc[1], loy, hiy);
-            forces_cells<STATS, SF>(a, geo, a.cell_start, i, cx, cy, p, lox, hix, loy, hiy, acc);
+            float2 vn = v;
+            float m2 = 0.f;
+            integrate_one<MODE>(a, i, p, v, acc.fx, acc.fy, vn, m2);
+            vmax2 = fmaxf(vmax2, m2);
+            if (STATS) {
+                const float tt[kStatsN] = {0.5f * a.mass * fmaf(vn.x, vn.x, vn.y * vn.y), 0.5f * acc.pe,
+                                           0.5f * acc.vir, a.mass * vn.x, a.mass * vn.y};
+#pragma unroll
+                for (int q = 0; q < kStatsN; ++q) lsum[q] += __float2ll_rn(tt[q] * kFixScale);
+            }
         }
+        __syncthreads();   // this stage and its descriptor are free for the tile after next
     }
-    SysView sv;
-    sv.geo = geo;
-    sv.cell0 = 0;
-    sv.ncells = geo.nc[0] * geo.nc[1];
-    sv.sys = 0;
-    step_finish<MODE, STATS, false, kTileT>(a, sv, i, act, p, v, acc, D);
+    if (timed_out) set_status(a.ctl, kErrTimeout);
+    tile_finish<MODE, STATS>(a, vmax2, lsum, D);
 }
 
 // ---- upload / download conversions ----------------------------------------
@@ -1198,27 +1404,38 @@ void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStrea
     }
 }
 
-template <bool SF>
-void launch_step_tile_t(const StepArgs &a, int mode, dim3 grid, cudaStream_t s) {
-    const dim3 block(kTileT);
-    if (mode == kModeStep) {
-        if (a.stats) k_step_tile<kModeStep, true, SF><<<grid, block, 0, s>>>(a);
-        else k_step_tile<kModeStep, false, SF><<<grid, block, 0, s>>>(a);
-    } else if (mode == kModeInit) {
-        k_step_tile<kModeInit, true, SF><<<grid, block, 0, s>>>(a);
-    } else {
-        k_step_tile<kModeSync, true, SF><<<grid, block, 0, s>>>(a);
+// Persistent launch: as many blocks as fit on the device at once (at most one per tile).
+template <int MODE, bool STATS, bool SF>
+cudaError_t launch_tile_k(const StepArgs &a, cudaStream_t s) {
+    void (*kern)(StepArgs) = k_step_tile<MODE, STATS, SF>;
+    const size_t smem = 2 * (size_t)TileStage::bytes(a.tile.list_stage);
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kStepTileThreads, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)sms * (per > 0 ? per : 1);
+    if (grid > a.tile.max_tiles) grid = a.tile.max_tiles;
+    kern<<<(unsigned)(grid < 1 ? 1 : grid), kStepTileThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool SF>
+cudaError_t launch_step_tile_t(const StepArgs &a, int mode, cudaStream_t s) {
+    if (mode == kModeStep)
+        return a.stats ? launch_tile_k<kModeStep, true, SF>(a, s) : launch_tile_k<kModeStep, false, SF>(a, s);
+    if (mode == kModeInit) return launch_tile_k<kModeInit, true, SF>(a, s);
+    return launch_tile_k<kModeSync, true, SF>(a, s);
 }
 
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s) {
-    if (!a.batch.sys && a.tile.desc) {
-        // one block per possible tile; blocks past the tile count only join the reductions
-        const dim3 grid((unsigned)a.tile.max_tiles);
-        if (a.potential == 2) launch_step_tile_t<true>(a, mode, grid, s);
-        else launch_step_tile_t<false>(a, mode, grid, s);
-        return cudaGetLastError();
-    }
+    if (!a.batch.sys && a.tile.desc)
+        return a.potential == 2 ? launch_step_tile_t<true>(a, mode, s) : launch_step_tile_t<false>(a, mode, s);
     const int threads = a.batch.sys ? kChunk : kStepThreads;
     const int64_t blocks = (a.n + threads - 1) / threads;
     if (blocks < 1) return cudaSuccess;

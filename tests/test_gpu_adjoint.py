@@ -154,3 +154,38 @@ def test_adjoint_preconditions(cuda):
         s.step(3)
         with pytest.raises(m.MdlgError):
             s.adjoint(20, 10, 2.0)          # not at a re-sort
+
+
+def test_lj_gradients_elementwise_for_single_particles(cuda):
+    # Individual gradient entries: for 8 particles, each coordinate of x0 and v0
+    # perturbed alone by +-1e-6 (FP64 oracle trajectory, shifted-force LJ, 100
+    # steps, checkpoints every 20), the central difference against the adjoint's
+    # entry for that particle and coordinate.
+    n, rho, K, ckpt = 2048, 0.3, 100, 20
+    L = mi.box_for(n, rho, 4.0)
+    dx, width, h = 4.0, 2.0, 1e-6
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=n + 5)
+    p = m.Params(n=n, box=L, dx=dx, sort_every=ckpt, vmax=V, potential=m.POT_LJ_SF)
+    with m.Simulation(p, x0, v0) as s:
+        out = s.adjoint(K, ckpt, width, dloss=M2)
+    picks = np.random.default_rng(11).choice(n, size=8, replace=False)
+    got, fd = [], []
+    for i in picks:
+        for a in (0, 1):
+            for which in ("x", "v"):
+                e = np.zeros((n, 2))
+                e[i, a] = h
+                if which == "x":
+                    lp = _lj_loss(x0 + e, v0, L, 1.0, 1.0, K, dx, width, True)
+                    lm = _lj_loss(x0 - e, v0, L, 1.0, 1.0, K, dx, width, True)
+                    got.append(out["grad_x0"][i, a])
+                else:
+                    lp = _lj_loss(x0, v0 + e, L, 1.0, 1.0, K, dx, width, True)
+                    lm = _lj_loss(x0, v0 - e, L, 1.0, 1.0, K, dx, width, True)
+                    got.append(out["grad_v0"][i, a])
+                fd.append((lp - lm) / (2 * h))
+    got, fd = np.array(got), np.array(fd)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    assert np.all(np.abs(got - fd) <= 5e-3 * np.abs(fd) + 1e-3 * scale), \
+        (got.tolist(), fd.tolist())

@@ -33,24 +33,35 @@ def _min_image(d, L):
     return d - L * np.round(d / L)
 
 
-def _force_check(f_gpu, f_ref, scale, tol=1e-5):
+def _force_check(f_gpu, f_ref, scale, tol=1e-5, record=None):
     err = np.abs(f_gpu - f_ref).max(axis=1)
     bound = tol * np.maximum(scale, 1e-3)
     assert np.all(err <= bound), float((err / np.maximum(scale, 1e-3)).max())
+    # the plain relative error |dF| / |F| per particle, beside the term-magnitude bar:
+    # it is reported, and its 99th percentile must also stay within the tolerance
+    # (single particles whose pair forces nearly cancel may exceed it)
+    fn = np.linalg.norm(f_ref, axis=1)
+    rel = np.linalg.norm(f_gpu - f_ref, axis=1)[fn > 0] / fn[fn > 0]
+    stats = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
+             "median": float(np.median(rel)), "term_bar_max": float((err / np.maximum(scale, 1e-3)).max())}
+    print("force relative error |dF|/|F|:", stats)
+    if record is not None:
+        record("force_relative_error", stats)
+    assert stats["p99"] <= tol, stats
 
 
 @pytest.mark.parametrize("n,rho,seed", [(1024, 0.25, 1), (5000, 0.3, 2), (20000, 0.6, 3)])
-def test_forces_match_direct_sum(cuda, n, rho, seed):
+def test_forces_match_direct_sum(cuda, n, rho, seed, record_property):
     L = mi.box_for(n, rho, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed, quantum=Q)
     with _sim(n, L, x0, v0) as s:
         x, _, f = s.get_state(want_force=True)
     assert np.array_equal(x, x0)          # identical positions on both sides
     f_ref, scale, _, _ = oracle.lj_forces(x0, (L, L))
-    _force_check(f, f_ref, scale)
+    _force_check(f, f_ref, scale, record=record_property)
 
 
-def test_forces_full_size_sampled(cuda):
+def test_forces_full_size_sampled(cuda, record_property):
     c = mi.PRODUCTION_LJ
     x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1, quantum=Q)
     with _sim(c.n, c.box, x0, v0) as s:
@@ -59,7 +70,7 @@ def test_forces_full_size_sampled(cuda):
     rng = np.random.default_rng(0)
     which = np.concatenate([rng.choice(c.n, 150, replace=False), [0, c.n - 1]])
     f_ref, scale = oracle.lj_forces_sample(x0, (c.box, c.box), which)
-    _force_check(f[which], f_ref, scale)
+    _force_check(f[which], f_ref, scale, record=record_property)
 
 
 @pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3),

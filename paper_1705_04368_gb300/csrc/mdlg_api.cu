@@ -54,19 +54,10 @@ struct mdlg_ctx {
     bool moving = false;
     float2 *vsync = nullptr, *fsync = nullptr;
     double *xbuf = nullptr, *vbuf = nullptr, *fbuf = nullptr;
-    uint32_t *nbr = nullptr;      // Verlet list (cap x n 32-bit entries, or the tiled 16-bit list)
+    uint32_t *nbr = nullptr;      // Verlet list (cap x n)
     int32_t *ncount = nullptr;
     int32_t cap = 0;
     float list_radius = 0.f;
-    // tiles of the sorted state (single systems with a potential)
-    TileDesc *tdesc = nullptr;
-    TileLane *tlanes = nullptr;
-    int32_t *ntiles = nullptr, *row_tiles = nullptr;
-    int64_t max_tiles = 0;
-    int32_t list_stage = 0;       // tiled-list entries a step-kernel stage holds
-    size_t nbr_bytes = 0;
-    bool want_tiles = false;      // sorts build the tiled list
-    bool list_tiles = false;      // the current list is the tiled one
     // host-side schedule
     int64_t step = 0, last_sort = 0, stats_step = -1;
     int64_t intervals[kMaxLags]{};
@@ -242,18 +233,6 @@ double lj_dfc_dsigma(const mdlg_params &p) {
     return 24.0 * p.eps * (24.0 * sr6 * sr6 - 6.0 * sr6) / (p.sigma * p.rcut);
 }
 
-TileArgs tile_args(mdlg_ctx *c) {
-    TileArgs t{};
-    t.desc = c->tdesc;
-    t.ntiles = c->ntiles;
-    t.row_tiles = c->row_tiles;
-    t.max_tiles = c->max_tiles;
-    t.list = reinterpret_cast<uint16_t *>(c->nbr);
-    t.lanes = c->tlanes;
-    t.list_stage = c->list_stage;
-    return t;
-}
-
 StepArgs step_args(mdlg_ctx *c) {
     StepArgs a{};
     a.geo = c->geo;
@@ -288,7 +267,6 @@ StepArgs step_args(mdlg_ctx *c) {
     a.ncount = c->ncount;
     a.cap = c->cap;
     a.list_skin = c->list_radius - (float)rc;
-    if (c->list_tiles) a.tile = tile_args(c);
     return a;
 }
 
@@ -330,7 +308,6 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
 
 int do_sort(mdlg_ctx *c, bool launch = true) {
     if (!launch) {   // bookkeeping of a sort that a replayed graph performs
-        c->list_tiles = c->want_tiles;
         c->pos_cur ^= 1;
         c->meta_cur ^= 1;
         c->last_sort = c->step;
@@ -370,37 +347,13 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
     s.ncount = c->ncount;
     s.cap = c->cap;
     s.rl2 = c->list_radius * c->list_radius;
-    if (c->want_tiles) s.tile = tile_args(c);
     {
-        ProfScope ps(c, MDLG_PROF_SORT, c->want_tiles ? 11 : (c->nbr ? 7 : 6));
+        ProfScope ps(c, MDLG_PROF_SORT, c->nbr ? 7 : 6);
         MDLG_TRY(cuda_err(launch_sort(s, c->stream)));
     }
-    c->list_tiles = c->want_tiles;
     c->pos_cur ^= 1;
     c->meta_cur ^= 1;
     c->last_sort = c->step;
-    return MDLG_OK;
-}
-
-// The 32-bit Verlet list of the current (freshly sorted) state, replacing a
-// tiled one: the adjoint's kernels read that format.
-int rebuild_plain_list(mdlg_ctx *c) {
-    if (!c->list_tiles) return MDLG_OK;
-    SortArgs s{};
-    s.geo = c->geo;
-    s.n = c->slots;
-    s.batch = batch_of(c);
-    s.ncells = c->ncells;
-    s.cell_out = c->cell[c->meta_cur];
-    s.cl_out = c->cl[c->pos_cur];
-    s.cell_start = c->cell_start;
-    s.ctl = c->ctl;
-    s.nbr = c->nbr;
-    s.ncount = c->ncount;
-    s.cap = c->cap;
-    s.rl2 = c->list_radius * c->list_radius;
-    MDLG_TRY(cuda_err(launch_nlist(s, c->stream)));
-    c->list_tiles = false;
     return MDLG_OK;
 }
 
@@ -583,9 +536,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     const size_t NQ = (size_t)(n > c->slots ? n : c->slots);
     const int32_t nsb = nsys > 0 ? nsys : 1;
     for (int b = 0; b < 2; ++b) {
-        // two spare offsets: staged window copies round their end up to 16 bytes
-        if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N + 2)) ||
-            (rc = alloc_n(c, &c->vel[b], N + 2)) || (rc = alloc_n(c, &c->pid[b], N)))
+        if ((rc = alloc_n(c, &c->cell[b], N)) || (rc = alloc_n(c, &c->cl[b], N)) ||
+            (rc = alloc_n(c, &c->vel[b], N)) || (rc = alloc_n(c, &c->pid[b], N)))
             return fail(rc);
         for (int l = 0; l < p.nlags; ++l) {
             if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
@@ -628,34 +580,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
         if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x (cap + 1) words of shared memory
-        // one buffer holds either list format: cap 32-bit entries per slot, or
-        // (one system) cap 16-bit entries per tile slot plus 16 bytes of slack
-        // for the staged copies' rounding
-        c->nbr_bytes = sizeof(uint32_t) * (size_t)c->cap * N;
-        if (nsys == 0) {
-            c->max_tiles = max_tiles(c->slots, g.nc[1]);
-            const size_t tb = sizeof(uint16_t) * (size_t)c->max_tiles * kTileT * c->cap + 16;
-            if (tb > c->nbr_bytes) c->nbr_bytes = tb;
-        }
-        c->nbr_bytes = (c->nbr_bytes + 15) & ~(size_t)15;
-        if ((rc = alloc_n(c, &c->nbr, c->nbr_bytes / sizeof(uint32_t))) || (rc = alloc_n(c, &c->ncount, N)))
+        if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
             return fail(rc);
-        if (nsys == 0) {
-            // one system: tiles with staged windows, lane tables and the 16-bit list
-            if ((rc = alloc_n(c, &c->tdesc, (size_t)c->max_tiles)) ||
-                (rc = alloc_n(c, &c->tlanes, (size_t)c->max_tiles * kTileLanes)) ||
-                (rc = alloc_n(c, &c->ntiles, 1)) ||
-                (rc = alloc_n(c, &c->row_tiles, (size_t)g.nc[1] + 1)))
-                return fail(rc);
-            // entries a stage holds: a tile's mean plus six standard deviations
-            // (counts are near Poisson), at most the tile's capacity
-            const double et = kTileT * mean;
-            int64_t ls = (int64_t)std::ceil(et + 6.0 * std::sqrt(et) + 64.0);
-            ls = (ls + 7) / 8 * 8;
-            if (ls > (int64_t)kTileT * c->cap) ls = (int64_t)kTileT * c->cap;
-            c->list_stage = (int32_t)ls;
-            c->want_tiles = true;
-        }
     }
 
     cudaStream_t s = c->stream;
@@ -1143,15 +1069,6 @@ int mdlg_adjoint(mdlg_ctx *c, int64_t nsteps, int32_t ckpt_every, double width,
     const int64_t N = c->slots;
     const int Q = (2 * p.vmax + 1) * (2 * p.vmax + 1);
     const int64_t nseg = nsteps / ckpt_every;
-    // the adjoint's kernels read the 32-bit list: sorts of this call build it,
-    // and the tiled list of the current state is replaced by it
-    struct TilesOff {
-        mdlg_ctx *c;
-        bool was;
-        explicit TilesOff(mdlg_ctx *x) : c(x), was(x->want_tiles) { x->want_tiles = false; }
-        ~TilesOff() { c->want_tiles = was; }
-    } tiles_off(c);
-    MDLG_TRY(rebuild_plain_list(c));
     const size_t nc1 = (size_t)c->ncells + 1;
     cudaStream_t s = c->stream;
     TempAlloc tmp(c);
@@ -1370,7 +1287,7 @@ namespace {
 
 // Checkpoint layout: a header, then the device regions below in this order.
 constexpr uint64_t kCkptMagic = 0x54504b43474c444dull;   // "MDLGCKPT"
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 1;
 
 struct CkptHeader {
     uint64_t magic;
@@ -1380,7 +1297,6 @@ struct CkptHeader {
     int64_t step, last_sort, stats_step;
     int64_t intervals[kMaxLags];
     int32_t pos_cur, meta_cur;
-    int32_t list_tiles, pad_;   // format of the saved Verlet list
 };
 
 struct Region {
@@ -1434,13 +1350,8 @@ std::vector<Region> ckpt_regions(mdlg_ctx *c) {
     }
     r.push_back({c->cell_start, ((size_t)c->ncells + 1) * sizeof(int32_t)});
     if (c->nbr) {
-        r.push_back({c->nbr, c->nbr_bytes});
+        r.push_back({c->nbr, (size_t)c->cap * N * sizeof(uint32_t)});
         r.push_back({c->ncount, N * sizeof(int32_t)});
-    }
-    if (c->list_tiles) {
-        r.push_back({c->tdesc, (size_t)c->max_tiles * sizeof(TileDesc)});
-        r.push_back({c->tlanes, (size_t)c->max_tiles * kTileLanes * sizeof(TileLane)});
-        r.push_back({c->ntiles, sizeof(int32_t)});
     }
     r.push_back({c->ctl, sizeof(Control)});
     const size_t nsb = c->nsys > 0 ? (size_t)c->nsys : 1;
@@ -1492,7 +1403,6 @@ int mdlg_save(mdlg_ctx *c, void *buf, uint64_t bytes) {
     for (int l = 0; l < kMaxLags; ++l) h.intervals[l] = c->intervals[l];
     h.pos_cur = c->pos_cur;
     h.meta_cur = c->meta_cur;
-    h.list_tiles = c->list_tiles ? 1 : 0;
     memcpy(buf, &h, sizeof(h));
     unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(h);
     for (const Region &g : ckpt_regions(c)) {
@@ -1509,13 +1419,11 @@ int mdlg_load(mdlg_ctx *c, const void *buf, uint64_t bytes) {
     if (h.magic != kCkptMagic || h.version != kCkptVersion || h.nsys != (uint32_t)c->nsys)
         return MDLG_EINVAL;
     if (h.shape_hash != shape_hash(c) || bytes < h.total) return MDLG_EINVAL;
-    if ((h.pos_cur & ~1) || (h.meta_cur & ~1) || (h.list_tiles & ~1)) return MDLG_EINVAL;
-    if (h.list_tiles && !c->tdesc) return MDLG_EINVAL;
+    if ((h.pos_cur & ~1) || (h.meta_cur & ~1)) return MDLG_EINVAL;
     MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
     drop_graph(c);                 // a captured schedule refers to the old step count
     c->pos_cur = h.pos_cur;
     c->meta_cur = h.meta_cur;
-    c->list_tiles = h.list_tiles != 0;
     if (ckpt_total(c) != h.total) return MDLG_EINVAL;
     const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof(h);
     for (const Region &g : ckpt_regions(c)) {

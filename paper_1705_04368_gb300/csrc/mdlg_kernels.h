@@ -144,72 +144,6 @@ struct Control {
     long long stats_acc[5];    // fixed-point sums of a running stats launch (zero at rest)
 };
 
-// ---- tiles of the sorted state (single systems) ------------------------------
-// A tile is up to kTileT consecutive slots of one MD-cell row.  Its neighbour
-// window is the slots of the cells [cxa - 1, cxb + 1] of the rows above, at and
-// below (cxa, cxb: the first and last cell column of the tile's particles),
-// stored as up to three segments per row: the wrapped left cell, the main
-// range and the wrapped right cell (or the whole row when the range would
-// cover it).  Each segment is staged from an even slot so that its copy starts
-// on a 16-byte boundary; the window index of slot j of segment s is
-// off[s] + (src[s] & 1) + (j - src[s]).
-//
-// The tiled Verlet list holds, per tile, the entries of its particles one
-// after another (no padding), 16 bits each: window index | x-shift code << 10
-// | y-shift code << 13.  A shift code names the neighbour cell's origin minus
-// the particle's cell origin along one axis (kShift* below; the wrapped codes
-// cross the periodic boundary next to the last, possibly wider, cell).  The
-// particles of a tile are ranked by entry count, and step-kernel lane l
-// (0 <= l < kTileT / 2) takes ranks l and kTileT - 1 - l, so that every lane
-// has about the same number of entries: the tile's lane table gives each
-// lane its two slots, their counts and the offset of its entries.
-constexpr int kTileT = 128;        // slots per tile
-constexpr int kTileLanes = kTileT / 2;
-constexpr int kTileSegs = 9;       // three rows x (wrapped left cell, main range, wrapped right cell)
-constexpr int kTileWinCap = 512;   // window elements a stage holds (entry indices have 10 bits)
-constexpr int kTileWinMax = 1024;  // larger windows: the tile's particles use the cell stencil
-constexpr uint16_t kTileOverflow = 0xffffu;   // lane-table count of a particle past the capacity
-enum ShiftCode : int32_t {
-    kShiftMinus = 0,       // origin - w
-    kShiftZero = 1,        // same column / row
-    kShiftPlus = 2,        // origin + w
-    kShiftWrapMinus = 3,   // across the boundary to the last cell: -(its width)
-    kShiftWrapPlus = 4,    // from the last cell across the boundary: +(its width)
-};
-
-struct TileDesc {
-    int32_t t0, cnt;              // first slot, particles
-    int32_t ne;                   // list entries of the tile
-    int32_t wlen;                 // window elements, alignment padding included
-    int32_t whole;                // 1: every window row is its whole cell row
-    int32_t cxa, cxb;             // first and last cell column of the tile's particles
-    int32_t row;                  // the tile's cell row
-    int32_t src[kTileSegs];       // first slot of each segment
-    int32_t len[kTileSegs];       // its slots (0: absent)
-    int32_t off[kTileSegs];       // its first window element (even)
-    int32_t pad_[5];
-};
-
-// One step-kernel lane of a tile: slots (offsets from t0; 0xff: none) of the
-// particles of ranks l and kTileT - 1 - l, their entry counts (kTileOverflow:
-// list past the capacity, use the cell stencil) and the first entry of the
-// lane in the tile's list.
-struct TileLane {
-    uint8_t a, b;
-    uint16_t ca, cb;
-    uint16_t off;
-};
-
-struct TileArgs {
-    TileDesc *desc;               // max_tiles descriptors (null: no tiles)
-    int32_t *ntiles;              // tiles in use (device)
-    int32_t *row_tiles;           // nc_y + 1: tiles per cell row, then their exclusive prefix
-    int64_t max_tiles;
-    uint16_t *list;               // entries: tile t's at t * kTileT * cap
-    TileLane *lanes;              // max_tiles x kTileLanes
-    int32_t list_stage;           // entries a stage holds (the rest are read from global memory)
-};
-
 enum StepMode : int32_t {
     kModeStep = 0,   // F(x_n); v_{n+1/2} = v_{n-1/2} + F dt/m; x_{n+1} = x_n + v dt
     kModeInit = 1,   // F(x_0); v_{-1/2} = v_0 - F dt/(2m)        (positions kept)
@@ -241,7 +175,6 @@ struct StepArgs {
     int32_t stats;              // 1: FP64 reductions (Control::stats, or per system in a batch)
     Control *ctl;
     Batch batch;
-    TileArgs tile;              // tiled list (desc non-null): the staged-window step kernel
 };
 
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);
@@ -279,14 +212,10 @@ struct SortArgs {
     int32_t cap;
     float rl2;               // list radius squared
     Batch batch;
-    TileArgs tile;           // desc non-null: build tiles and the tiled 16-bit list instead
 };
 
 int64_t sort_scratch_blocks(int64_t ncells);
 cudaError_t launch_sort(const SortArgs &a, cudaStream_t s);
-// Verlet list (batches of four 32-bit entries) of an already sorted state.
-cudaError_t launch_nlist(const SortArgs &a, cudaStream_t s);
-int64_t max_tiles(int64_t n, int32_t rows);
 
 // Upload conversion: FP64 positions -> (cell, cl) in original order (unsorted).
 cudaError_t launch_pack(const Geom &geo, int64_t n, const double *x, const double *v,

@@ -108,8 +108,7 @@ def test_late_resort_uses_wider_stencil(cuda):
 def test_resort_interval_from_fastest_initial_speed(cuda):
     # sort_every = 0: the library re-sorts every floor(skin_eff / (2 x 1.15 vmax0 dt))
     # steps, vmax0 the fastest initial speed (reduced on the device by the upload
-    # kernel); counted here from the re-sort launches of 100 steps (11 per re-sort of a
-    # single system: the sort, the tile descriptors and the tiled list)
+    # kernel); counted here from the re-sort launches of 100 steps (7 per re-sort)
     n, L = 4096, mi.box_for(4096, 0.3, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=78)
     p = m.Params(n=n, box=L, dx=4.0, lag_steps=(5,))
@@ -124,7 +123,7 @@ def test_resort_interval_from_fastest_initial_speed(cuda):
         s.step(K)
         prof = s.profile(False)
         st, _, _ = s.stats()
-    assert prof["sort"][1] == 11 * ((K - 1) // every)
+    assert prof["sort"][1] == 7 * ((K - 1) // every)
     assert st["status"] == 0
 
 

@@ -722,15 +722,15 @@ def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev
                     "f_i to host) + mdlg_destroy, per step"}
 
 
-def run_ncu_target(md_steps):
+def run_ncu_target(md_steps, dense=False):
     """profiling target (ncu --profile-from-start off): the bench's production
-    system with the tuned geometry, one untimed bench step, then md_steps MD steps
-    between cudaProfilerStart and cudaProfilerStop -- the launch mix of the timed
-    region."""
+    system (dense: the rho = 0.6, T = 0.8 case) with the tuned geometry, one
+    untimed bench step, then md_steps MD steps between cudaProfilerStart and
+    cudaProfilerStop -- the launch mix of the timed region."""
     import torch
     import paper_1705_04368_gb300 as m
     from paper_1705_04368_gb300 import tune
-    c = _workload()
+    c = mi.PRODUCTION_LJ_DENSE if dense else _workload()
     x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=1)
     params, _ = tune.tune(_params(c, m), x0, v0, c.temperature)
     sim = m.Simulation(params, x0, v0)
@@ -844,6 +844,8 @@ def main():
     ap.add_argument("--ncu-target", type=int, default=0, metavar="MD_STEPS",
                     help="profiling target: the production system after one untimed bench "
                          "step, MD_STEPS MD steps inside cudaProfilerStart/Stop, exit")
+    ap.add_argument("--ncu-dense", action="store_true",
+                    help="with --ncu-target: the rho = 0.6, T = 0.8 production case")
     ap.add_argument("--ncu-collision", type=int, default=0, metavar="LAUNCHES",
                     help="profiling target: LAUNCHES collision-operator launches on the "
                          "production lattice, exit")
@@ -870,7 +872,7 @@ def main():
         run_ncu_collision(args.ncu_collision)
         return
     if args.ncu_target:
-        run_ncu_target(args.ncu_target)
+        run_ncu_target(args.ncu_target, dense=args.ncu_dense)
         return
     if args.warmup < 3:
         args.warmup = 3

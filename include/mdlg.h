@@ -82,7 +82,11 @@ typedef struct {
     double  dt;           /* MD time step (> 0)                                   */
     double  grid;         /* base grid g: a power of two; dx is a multiple of g   */
     double  skin;         /* minimum neighbour-cell skin beyond rcut (>= 0)        */
-    int32_t sort_every;   /* MD steps between cell re-sorts; 0 picks one          */
+    int32_t sort_every;   /* MD steps between cell re-sorts; 0 picks them: half the
+                             skin covered at 1.15 x the fastest initial speed, and
+                             later (unless use_graphs) at 1.1 x the larger of that
+                             speed and the fastest speed the device measured over
+                             the interval before the last one                    */
     double  dx;           /* lattice spacing Delta x (Sec. III)                   */
     int32_t nlags;        /* coarse time steps tracked, 1..MDLG_MAX_LAGS          */
     int32_t lag_steps[MDLG_MAX_LAGS]; /* Delta t of each, in MD steps (>= 1)      */
@@ -134,6 +138,11 @@ typedef struct {
                                      over particles and binned intervals of the
                                      squared displacement over the lag (0 if off) */
     double  lattice_u[2];         /* effective lattice drift: s1 / dt            */
+    int64_t stale_steps;          /* step launches so far that found the Verlet list
+                                     out of date (forces then came from the cell
+                                     stencil: correct, slower); 0 when the re-sort
+                                     schedule keeps up                           */
+    int32_t sort_every;           /* MD steps between re-sorts currently in use   */
 } mdlg_stats_out;
 
 /*

@@ -57,7 +57,8 @@ class _Stats(ctypes.Structure):
                 ("virial", ctypes.c_double), ("momentum", ctypes.c_double * 2),
                 ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
                 ("intervals", ctypes.c_int64 * MAX_LAGS), ("status", ctypes.c_int32),
-                ("msd", (ctypes.c_double * 2) * MAX_LAGS), ("lattice_u", ctypes.c_double * 2)]
+                ("msd", (ctypes.c_double * 2) * MAX_LAGS), ("lattice_u", ctypes.c_double * 2),
+                ("stale_steps", ctypes.c_int64), ("sort_every", ctypes.c_int32)]
 
 
 class _Lattice(ctypes.Structure):
@@ -263,7 +264,8 @@ class Simulation:
         _check(self._lib.mdlg_stats(self._h, ctypes.byref(out), counts.ctypes.data, fi.ctypes.data),
                "mdlg_stats")
         d = {k: getattr(out, k) for k in ("step", "stats_step", "kinetic", "potential", "virial",
-                                          "temperature", "pressure", "status")}
+                                          "temperature", "pressure", "status", "stale_steps",
+                                          "sort_every")}
         d["momentum"] = (out.momentum[0], out.momentum[1])
         d["intervals"] = [out.intervals[i] for i in range(nl)]
         d["msd"] = [(out.msd[i][0], out.msd[i][1]) for i in range(nl)]

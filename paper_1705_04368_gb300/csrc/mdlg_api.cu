@@ -62,6 +62,17 @@ struct mdlg_ctx {
     int64_t step = 0, last_sort = 0, stats_step = -1;
     int64_t intervals[kMaxLags]{};
     int32_t sort_every = 1;
+    // adaptive re-sort interval (params.sort_every = 0, no graphs): at every
+    // re-sort the largest speed of the interval just ended is copied to pinned
+    // host memory; the interval that starts at the following re-sort is set
+    // from it (one interval behind, so the host never waits for the stream to
+    // drain, and the schedule depends only on device values at fixed steps)
+    bool adaptive = false;
+    double vmax0 = 0.0;            // fastest uploaded speed
+    double skin_eff = 0.0;         // MD cell width minus rc
+    int64_t nsorts = 0;            // re-sorts since the upload
+    uint32_t *h_run = nullptr;     // pinned: vmax2_run copied at the last two re-sorts
+    cudaEvent_t ev_run[2]{};
     float rc = 0.f, round_margin = 0.f;
     // CUDA graph of two schedule periods (use_graphs)
     cudaGraph_t graph = nullptr;
@@ -306,6 +317,32 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
     return b;
 }
 
+// MD steps between re-sorts for a speed bound v: half the skin covered.
+int32_t interval_for(const mdlg_ctx *c, double v) {
+    const double k = std::floor(0.5 * c->skin_eff / (std::fmax(v, 1e-12) * c->p.dt));
+    return (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
+}
+
+// Adaptive schedule, at a re-sort (before its kernels are queued): queue the
+// copy of the speed bound of the interval that ends here, and set the next
+// interval from the copy queued at the previous re-sort.
+int adapt_interval(mdlg_ctx *c) {
+    const int64_t n = ++c->nsorts;
+    if (n >= 2) {
+        const int b = (int)((n - 1) & 1);
+        MDLG_TRY(cuda_err(cudaEventSynchronize(c->ev_run[b])));
+        uint32_t bits = c->h_run[b];
+        float v2;
+        memcpy(&v2, &bits, sizeof(v2));
+        // 10 % above the larger of the measured and the initial fastest speed
+        c->sort_every = interval_for(c, 1.1 * std::fmax(std::sqrt((double)v2), c->vmax0));
+    }
+    const int b = (int)(n & 1);
+    MDLG_TRY(cuda_err(cudaMemcpyAsync(&c->h_run[b], &c->ctl->vmax2_run, sizeof(uint32_t),
+                                      cudaMemcpyDeviceToHost, c->stream)));
+    return cuda_err(cudaEventRecord(c->ev_run[b], c->stream));
+}
+
 int do_sort(mdlg_ctx *c, bool launch = true) {
     if (!launch) {   // bookkeeping of a sort that a replayed graph performs
         c->pos_cur ^= 1;
@@ -313,6 +350,7 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
         c->last_sort = c->step;
         return MDLG_OK;
     }
+    if (c->adaptive && c->step > 0) MDLG_TRY(adapt_interval(c));
     SortArgs s{};
     s.geo = c->geo;
     s.n = c->slots;
@@ -657,13 +695,27 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     // (nothing above depends on it).  If the bound tracked on the device grows
     // past it earlier, the step kernel uses the cell stencil for the remaining
     // steps, so a late sort costs time, not accuracy.
+    c->vmax0 = vmax0;
+    c->skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
     if (p.sort_every > 0) {
         c->sort_every = p.sort_every;
     } else {
-        const double skin_eff = g.k * p.grid - (p.potential ? p.rcut : 0.0);
-        const double v = std::fmax(1.15 * vmax0, 1e-12);
-        double k = std::floor(0.5 * skin_eff / (v * p.dt));
-        c->sort_every = (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
+        c->sort_every = interval_for(c, 1.15 * vmax0);
+        // with graphs the captured schedule needs a fixed interval
+        if (!p.use_graphs) {
+            if (cudaMallocHost(&c->h_run, 2 * sizeof(uint32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(MDLG_ENOMEM);
+            }
+            c->h_run[0] = c->h_run[1] = 0u;
+            for (int b = 0; b < 2; ++b)
+                if ((rc = chk(cudaEventCreateWithFlags(&c->ev_run[b], cudaEventDisableTiming)))) {
+                    cudaFreeHost(c->h_run);
+                    c->h_run = nullptr;
+                    return fail(rc);
+                }
+            c->adaptive = true;
+        }
     }
     *out = c;
     return MDLG_OK;
@@ -904,6 +956,14 @@ int stats_impl(mdlg_ctx *c, int32_t k, mdlg_stats_out *out, uint64_t *counts, do
     out->status = status;
     for (int a = 0; a < 2; ++a)
         out->lattice_u[a] = (double)c->shift_m[a] * p.grid * (1.0 / 16777216.0) / p.dt;
+    {
+        Control h{};
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost,
+                                          c->stream)));
+        MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+        out->stale_steps = h.stale_steps;
+        out->sort_every = c->sort_every;
+    }
     if (p.msd) {
         double h[2 * kMaxLags];
         MDLG_TRY(cuda_err(cudaMemcpyAsync(h, c->msd_acc, sizeof(double) * 2 * p.nlags,
@@ -1287,7 +1347,7 @@ namespace {
 
 // Checkpoint layout: a header, then the device regions below in this order.
 constexpr uint64_t kCkptMagic = 0x54504b43474c444dull;   // "MDLGCKPT"
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct CkptHeader {
     uint64_t magic;
@@ -1297,6 +1357,13 @@ struct CkptHeader {
     int64_t step, last_sort, stats_step;
     int64_t intervals[kMaxLags];
     int32_t pos_cur, meta_cur;
+    // the re-sort schedule: current interval, re-sorts so far, the speed bounds
+    // copied at the last two re-sorts, the fastest uploaded speed
+    int32_t sort_every;
+    uint32_t run[2];
+    int32_t pad_;
+    int64_t nsorts;
+    double vmax0;
 };
 
 struct Region {
@@ -1328,7 +1395,8 @@ uint64_t shape_hash(const mdlg_ctx *c) {
     for (int l = 0; l < p.nlags; ++l) h = mix(h, p.lag_steps[l]);
     h = mix(h, p.vmax); h = mix(h, p.site_mode); h = mix(h, p.msd);
     h = mix(h, p.lattice_u[0]); h = mix(h, p.lattice_u[1]);
-    h = mix(h, c->sort_every); h = mix(h, c->slots); h = mix(h, c->ncells); h = mix(h, c->cap);
+    h = mix(h, p.sort_every); h = mix(h, c->adaptive); h = mix(h, c->slots); h = mix(h, c->ncells);
+    h = mix(h, c->cap);
     h = mix(h, c->nsys);
     if (c->nsys > 0) h = fnv1a(h, c->sys_host.data(), sizeof(SysInfo) * c->sys_host.size());
     return h;
@@ -1403,6 +1471,12 @@ int mdlg_save(mdlg_ctx *c, void *buf, uint64_t bytes) {
     for (int l = 0; l < kMaxLags; ++l) h.intervals[l] = c->intervals[l];
     h.pos_cur = c->pos_cur;
     h.meta_cur = c->meta_cur;
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));   // the speed copies have landed
+    h.sort_every = c->sort_every;
+    h.run[0] = c->h_run ? c->h_run[0] : 0u;
+    h.run[1] = c->h_run ? c->h_run[1] : 0u;
+    h.nsorts = c->nsorts;
+    h.vmax0 = c->vmax0;
     memcpy(buf, &h, sizeof(h));
     unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(h);
     for (const Region &g : ckpt_regions(c)) {
@@ -1434,6 +1508,14 @@ int mdlg_load(mdlg_ctx *c, const void *buf, uint64_t bytes) {
     c->step = h.step;
     c->last_sort = h.last_sort;
     c->stats_step = h.stats_step;
+    if (h.sort_every < 1) return MDLG_EINVAL;
+    c->sort_every = h.sort_every;
+    c->nsorts = h.nsorts;
+    c->vmax0 = h.vmax0;
+    if (c->h_run) {
+        c->h_run[0] = h.run[0];
+        c->h_run[1] = h.run[1];
+    }
     for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = h.intervals[l];
     return MDLG_OK;
 }
@@ -1469,6 +1551,9 @@ void mdlg_destroy(mdlg_ctx *c) {
     cudaStreamSynchronize(c->stream);
     drop_graph(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b)
+        if (c->ev_run[b]) cudaEventDestroy(c->ev_run[b]);
+    if (c->h_run) cudaFreeHost(c->h_run);
     free_all(c);
     delete c;
 }

@@ -142,6 +142,8 @@ struct Control {
     double stats[8];           // ke, pe, virial, px, py of the last stats launch
     unsigned long long vmax0_bits;   // max |v|^2 of the uploaded state (FP64 bits; >= 0)
     long long stats_acc[5];    // fixed-point sums of a running stats launch (zero at rest)
+    uint32_t vmax2_run;        // max |v|^2 of the half-step velocities since the last re-sort
+    uint32_t stale_steps;      // step launches that found the Verlet list out of date
 };
 
 enum StepMode : int32_t {

@@ -280,6 +280,8 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     }
     // the Verlet list holds every pair that can be closer than rc while 2D <= skin
     const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
+    if (a.potential && a.nbr && !list_ok && threadIdx.x == 0 && blockIdx.x == 0)
+        atomicAdd(&a.ctl->stale_steps, 1u);   // this launch takes the cell stencil
 
     PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
@@ -394,6 +396,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     if (threadIdx.x == 0) {
         if (MODE == kModeStep) {
             const uint32_t bits = atomicExch(&a.ctl->vmax2_bits, 0u);
+            atomicMax(&a.ctl->vmax2_run, bits);   // non-negative floats order like their bits
             const float vmax = sqrtf(__uint_as_float(bits));
             a.ctl->dbound = D + vmax * a.dt * 1.000001f + a.round_margin;
         }
@@ -525,6 +528,7 @@ __global__ void k_cell_start(SortArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.cell_start[a.ncells] = (int32_t)a.n;
         a.ctl->dbound = 0.0f;
+        a.ctl->vmax2_run = 0u;
     }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncells; c += stride)
         a.cell_start[c] = cell_begin(a, c);

@@ -106,9 +106,10 @@ def test_late_resort_uses_wider_stencil(cuda):
 
 
 def test_resort_interval_from_fastest_initial_speed(cuda):
-    # sort_every = 0: the library re-sorts every floor(skin_eff / (2 x 1.15 vmax0 dt))
+    # sort_every = 0: the first re-sort comes after floor(skin_eff / (2 x 1.15 vmax0 dt))
     # steps, vmax0 the fastest initial speed (reduced on the device by the upload
-    # kernel); counted here from the re-sort launches of 100 steps (7 per re-sort)
+    # kernel); counted from the re-sort launches (7 per re-sort).  Later intervals
+    # follow the fastest speed the device measured, so the list never goes stale.
     n, L = 4096, mi.box_for(4096, 0.3, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=78)
     p = m.Params(n=n, box=L, dx=4.0, lag_steps=(5,))
@@ -117,14 +118,40 @@ def test_resort_interval_from_fastest_initial_speed(cuda):
     vmax0 = math.sqrt(float((v0 * v0).sum(axis=1).max()))
     every = int(max(1.0, min(math.floor(0.5 * skin_eff / (1.15 * vmax0 * p.dt)), 1000.0)))
     assert 2 <= every <= 50
-    K = 100
     with m.Simulation(p, x0, v0) as s:
         s.profile(True)
-        s.step(K)
-        prof = s.profile(False)
+        s.step(every)
+        assert s.profile(False)["sort"][1] == 0
+        s.profile(True)
+        s.step(1)
+        assert s.profile(False)["sort"][1] == 7
+        s.step(400)
         st, _, _ = s.stats()
-    assert prof["sort"][1] == 7 * ((K - 1) // every)
+    assert st["status"] == 0 and st["stale_steps"] == 0
+    # the adapted interval: 1.1 x the larger of the measured and the initial fastest speed
+    assert every * 0.7 <= st["sort_every"] <= every * 1.15 / 1.1 + 1
+
+
+@pytest.mark.parametrize("rho,T,steps,max_stale_frac", [(0.3, 1.0, 600, 0.0), (0.6, 0.8, 600, 0.03)])
+def test_adaptive_resort_keeps_the_list_current(cuda, rho, T, steps, max_stale_frac):
+    # A gas placed at random heats up as it relaxes (at rho = 0.6, T = 0.8 the
+    # fastest speed grows by 30-50 %): a schedule fixed from the initial speeds
+    # lets the Verlet list go stale (every such step takes the slower cell
+    # stencil); the adaptive schedule keeps up, and the trajectory still
+    # conserves momentum exactly and energy to the FP32 bound.
+    n = 65536
+    L = mi.box_for(n, rho, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, T, seed=91)
+    with _sim(n, L, x0, v0) as s:
+        st0, _, _ = s.stats()
+        s.step(steps)
+        st, _, _ = s.stats()
     assert st["status"] == 0
+    assert st["stale_steps"] <= max_stale_frac * steps, st["stale_steps"]
+    e0 = st0["kinetic"] + st0["potential"]
+    e1 = st["kinetic"] + st["potential"]
+    assert abs(e1 - e0) / n < 4e-3
+    assert abs(st["momentum"][0]) / n < 1e-5 and abs(st["momentum"][1]) / n < 1e-5
 
 
 def test_fp64_reductions_at_start(cuda):

@@ -333,8 +333,8 @@ def run_ours(args, rank, world, local_rank):
     avg_step_s = step_ms / 1e3 / max(step_launches, 1)
     rho_eff = c.n / (c.box * c.box)
     roofline = _step_roofline(c.n, rho_eff, c.rc, avg_step_s, hbm_gbs, fp32_peak, peak_kind)
-    tpp = _traffic_record("k_step")
-    ipp = _traffic_record("k_step", "warp_inst_per_particle")
+    tpp = _traffic_record("k_step_loop")
+    ipp = _traffic_record("k_step_loop", "warp_inst_per_particle")
     roofline["traffic"] = (tpp * c.n) if tpp is not None else None
     # instruction issue: one warp instruction per clock per SM sub-partition
     issue_peak = sms * SMSP_PER_SM * sm_max_mhz * 1e6
@@ -463,7 +463,7 @@ def _step_roofline(n, rho_eff, rc, avg_step_s, hbm_gbs, fp32_peak, peak_kind):
     cap = min(1.0, intensity * hbm_gbs / 1e3 / fp32_peak)
     return {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
             "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind,
-            "kernel": "k_step (force + velocity-Verlet)",
+            "kernel": "k_step_loop (force + velocity-Verlet; k_step on statistics steps)",
             "algorithmic_bytes_per_launch": step_bytes, "avg_launch_us": avg_step_s * 1e6,
             "fp32": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
                      "frac": achieved_tf / fp32_peak, "flops_per_particle": fpp,

@@ -25,6 +25,9 @@ namespace mdlg {
 namespace {
 
 constexpr int kStepThreads = 256;   // one system; a batch uses one 128-slot chunk per block
+// plain steps of one system: resident blocks per SM of the looping kernel (8 at
+// 32 registers fills an SM)
+constexpr int kStepLoopBlocksPerSM = 8;
 constexpr int kListBatch = 4;       // list entries loaded before any is used (lists are
                                     // padded to a multiple of this)
 constexpr int kNlistThreads = 128;  // list-build block (entries staged in shared memory;
@@ -248,41 +251,50 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     }
 }
 
-// B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
-// per system); otherwise one system described by a.geo.
-template <int MODE, bool STATS, bool B, bool SF>
-__device__ __forceinline__ void step_body(const StepArgs &a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
-    const Geom &geo = sv.geo;
-    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
-    const bool act = i < a.n && (!B || cw != kGhostCell);
-    // negated origin shifts -((c_x - 1) w, (c_y - 1) w) of the 16 list offset
-    // codes of a regular neighbourhood (code 3: the padding entries' 2 w)
-    __shared__ float2 s_tab[16];
+// Negated origin shifts -((c_x - 1) w, (c_y - 1) w) of the 16 list offset
+// codes of a regular neighbourhood (code 3: the padding entries' 2 w), built
+// by the first 16 threads of a block.
+__device__ __forceinline__ void init_shift_table(const StepArgs &a, float2 *s_tab) {
     if (threadIdx.x < 16)
         s_tab[threadIdx.x] = make_float2(-fmaf((float)(threadIdx.x & 3u), a.cell_w, -a.cell_w),
                                          -fmaf((float)(threadIdx.x >> 2), a.cell_w, -a.cell_w));
-    __syncthreads();
+}
 
-    // Neighbour-cell radius for the displacement bound of the input positions
-    // (evaluated only where it is used: the cell-stencil path and the check).
-    const float D = a.ctl->dbound;
-    const auto stencil_radius = [&]() {
-        const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
-        // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
-        return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
-    };
+// Neighbour-cell radius for the displacement bound D of the input positions.
+__device__ __forceinline__ int stencil_radius(const StepArgs &a, float D) {
+    const float Rf = ceilf((a.rc + 2.0f * D) / a.cell_w);
+    // NaN -> 1; anything past the box is capped (stencil() then visits every cell once)
+    return (Rf >= 1.0f) ? (Rf < 65536.0f ? (int)Rf : 65536) : 1;
+}
+
+// Launch-wide check, once per launch (block 0, thread 0): the cell list far out
+// of date for the stencil radius of D.
+__device__ __forceinline__ void check_stencil(const StepArgs &a, const Geom &geo, float D) {
     if (a.potential && threadIdx.x == 0 && blockIdx.x == 0) {
-        const int R = stencil_radius();
+        const int R = stencil_radius(a, D);
         if (2 * R + 1 > geo.nc[0] || 2 * R + 1 > geo.nc[1])
             set_status(a.ctl, kErrOverflow);   // cell list far out of date: whole box searched
     }
-    // the Verlet list holds every pair that can be closer than rc while 2D <= skin
-    const bool list_ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
-    if (a.potential && a.nbr && !list_ok && threadIdx.x == 0 && blockIdx.x == 0)
-        atomicAdd(&a.ctl->stale_steps, 1u);   // this launch takes the cell stencil
+}
 
+// The Verlet list holds every pair that can be closer than rc while 2D <= skin;
+// a launch that finds it stale takes the cell stencil and is counted.
+__device__ __forceinline__ bool list_current(const StepArgs &a, float D) {
+    const bool ok = a.nbr != nullptr && 2.0f * D <= a.list_skin;
+    if (a.potential && a.nbr && !ok && threadIdx.x == 0 && blockIdx.x == 0)
+        atomicAdd(&a.ctl->stale_steps, 1u);
+    return ok;
+}
+
+// One slot's force and update.  Returns |v|^2 of the new half-step velocity
+// (kModeStep) and, with STATS, the slot's fixed-point inputs t[] (kinetic
+// energy at the integer step, halved pair energy and virial, momentum).
+template <int MODE, bool STATS, bool B, bool SF>
+__device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, int64_t cell0,
+                                           int64_t i, const float2 *s_tab, bool list_ok,
+                                           float (&t)[kStatsN]) {
+    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
+    const bool act = i < a.n && (!B || cw != kGhostCell);
     PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
     if (act) {
@@ -303,12 +315,14 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
                     forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
                 }
             } else {
-                const int R = stencil_radius();
+                // D re-read here (the bound only changes at the end of the launch)
+                // so that it is not held in a register across the list path
+                const int R = stencil_radius(a, a.ctl->dbound);
                 int lox, hix, loy, hiy;
                 stencil(R, geo.nc[0], lox, hix);
                 stencil(R, geo.nc[1], loy, hiy);
-                forces_cells<STATS, SF>(a, geo, a.cell_start + sv.cell0, i, cx, cy, p, lox, hix, loy,
-                                    hiy, acc);
+                forces_cells<STATS, SF>(a, geo, a.cell_start + cell0, i, cx, cy, p, lox, hix, loy,
+                                        hiy, acc);
             }
         }
     }
@@ -335,7 +349,21 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
             if (a.f_sync) a.f_sync[i] = make_float2(fx, fy);
         }
     }
+    if (STATS && act) {
+        t[0] = 0.5f * a.mass * fmaf(vn.x, vn.x, vn.y * vn.y);
+        t[1] = 0.5f * acc.pe;
+        t[2] = 0.5f * acc.vir;
+        t[3] = a.mass * vn.x;
+        t[4] = a.mass * vn.y;
+    }
+    return vmax2;
+}
 
+// End of a block: the block's largest |v|^2 and statistics are published, and
+// the last block of the launch (ticket) turns them into the launch's results.
+template <int MODE, bool STATS, bool B>
+__device__ __forceinline__ void step_epilogue(const StepArgs &a, int64_t sys, float D, float vmax2,
+                                              const float (&t)[kStatsN]) {
     constexpr int kWarps = (B ? kChunk : kStepThreads) / 32;
     __shared__ long long s_red[kWarps][kStatsN];
     __shared__ float s_max[kWarps];
@@ -346,15 +374,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
         if (lane == 0) s_max[warp] = m;
     }
     if (STATS) {
-        // per-particle FP32 terms -> multiples of 2^-24 -> exact 64-bit sums
-        float t[kStatsN] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (act) {
-            t[0] = 0.5f * a.mass * fmaf(vn.x, vn.x, vn.y * vn.y);
-            t[1] = 0.5f * acc.pe;
-            t[2] = 0.5f * acc.vir;
-            t[3] = a.mass * vn.x;
-            t[4] = a.mass * vn.y;
-        }
+        // per-slot FP32 terms -> multiples of 2^-24 -> exact 64-bit sums
 #pragma unroll
         for (int k = 0; k < kStatsN; ++k) {
             const long long r = warp_sum_ll(__float2ll_rn(t[k] * kFixScale));
@@ -370,13 +390,13 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
         }
         if (STATS) {
             for (int k = 0; k < kStatsN; ++k) {
-                long long t = 0;
-                for (int w = 0; w < kWarps; ++w) t += s_red[w][k];
+                long long s = 0;
+                for (int w = 0; w < kWarps; ++w) s += s_red[w][k];
                 // batched: a block is one chunk of one system.  Integer sums are
                 // exact, so the order of these atomics does not matter
-                atomicAdd(B ? (unsigned long long *)&a.batch.stats[sv.sys * kStatsN + k]
+                atomicAdd(B ? (unsigned long long *)&a.batch.stats[sys * kStatsN + k]
                             : (unsigned long long *)&a.ctl->stats_acc[k],
-                          (unsigned long long)t);
+                          (unsigned long long)s);
             }
         }
         __threadfence();
@@ -389,9 +409,9 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     __threadfence();
     if (STATS && !B && threadIdx.x < kStatsN) {
         // the launch's totals, and the accumulators back to zero for the next
-        const long long t =
+        const long long s =
             (long long)atomicExch((unsigned long long *)&a.ctl->stats_acc[threadIdx.x], 0ull);
-        a.ctl->stats[threadIdx.x] = (double)t * kFixInv;
+        a.ctl->stats[threadIdx.x] = (double)s * kFixInv;
     }
     if (threadIdx.x == 0) {
         if (MODE == kModeStep) {
@@ -402,6 +422,23 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
         }
         a.ctl->done = 0u;
     }
+}
+
+// B: batched systems (geometry per 128-slot chunk, ghosts skipped, statistics
+// per system); otherwise one system described by a.geo.  One slot per thread.
+template <int MODE, bool STATS, bool B, bool SF>
+__device__ __forceinline__ void step_body(const StepArgs &a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const SysView sv = sys_view<B>(a.geo, a.batch, i < a.n ? i : 0);
+    __shared__ float2 s_tab[16];
+    init_shift_table(a, s_tab);
+    __syncthreads();
+    const float D = a.ctl->dbound;
+    check_stencil(a, sv.geo, D);
+    const bool list_ok = list_current(a, D);
+    float t[kStatsN] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const float vmax2 = step_slot<MODE, STATS, B, SF>(a, sv.geo, sv.cell0, i, s_tab, list_ok, t);
+    step_epilogue<MODE, STATS, B>(a, sv.sys, D, vmax2, t);
 }
 
 // One system: 256-thread blocks, the register count left to the compiler.
@@ -416,6 +453,29 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
 template <int MODE, bool STATS, bool SF>
 __global__ void __launch_bounds__(kChunk, 16) k_step_batch(StepArgs a) {
     step_body<MODE, STATS, true, SF>(a);
+}
+
+// Plain steps of one system (no statistics): a grid of resident blocks, each
+// block taking the 256-slot chunks blockIdx, blockIdx + gridDim, ...  A warp
+// runs through its chunks without waiting for the other warps of its block,
+// and the block epilogue (barriers, the launch ticket) runs once per block
+// instead of once per chunk.  Same arithmetic per slot as k_step.
+template <bool SF>
+__global__ void __launch_bounds__(kStepThreads, 8) k_step_loop(StepArgs a) {
+    __shared__ float2 s_tab[16];
+    init_shift_table(a, s_tab);
+    __syncthreads();
+    const float D = a.ctl->dbound;
+    check_stencil(a, a.geo, D);
+    const bool list_ok = list_current(a, D);
+    float t[kStatsN] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float vmax2 = 0.f;
+    // slot numbers fit 28 bits wherever lists are used (the entries' j field)
+    const int32_t n = (int32_t)a.n, stride = (int32_t)gridDim.x * kStepThreads;
+    for (int32_t i = (int32_t)blockIdx.x * kStepThreads + threadIdx.x; i < n; i += stride)
+        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, false, SF>(a, a.geo, 0, i, s_tab,
+                                                                   list_ok, t));
+    step_epilogue<kModeStep, false, false>(a, 0, D, vmax2, t);
 }
 
 // ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
@@ -827,6 +887,8 @@ template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
     if (mode == kModeStep) {
         if (a.stats) launch_step_k<kModeStep, true, B, SF>(a, grid, block, s);
+        else if (!B && kStepLoopBlocksPerSM > 0)
+            k_step_loop<SF><<<grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM), block, 0, s>>>(a);
         else launch_step_k<kModeStep, false, B, SF>(a, grid, block, s);
     } else if (mode == kModeInit) {
         launch_step_k<kModeInit, true, B, SF>(a, grid, block, s);

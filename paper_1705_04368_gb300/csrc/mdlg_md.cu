@@ -28,6 +28,7 @@ constexpr int kStepThreads = 256;   // one system; a batch uses one 128-slot chu
 // plain steps of one system: resident blocks per SM of the looping kernel (8 at
 // 32 registers fills an SM)
 constexpr int kStepLoopBlocksPerSM = 8;
+constexpr bool kStepBatchLoop = true;   // plain steps of a batch loop over chunks too
 constexpr int kListBatch = 4;       // list entries loaded before any is used (lists are
                                     // padded to a multiple of this)
 constexpr int kNlistThreads = 128;  // list-build block (entries staged in shared memory;
@@ -478,6 +479,29 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_step_loop(StepArgs a) {
     step_epilogue<kModeStep, false, false>(a, 0, D, vmax2, t);
 }
 
+// Plain steps of a batch: the same loop over 128-slot chunks (one chunk per
+// block and round, 16 resident blocks per SM), each chunk with its own
+// system's geometry.
+template <bool SF>
+__global__ void __launch_bounds__(kChunk, 16) k_step_batch_loop(StepArgs a) {
+    __shared__ float2 s_tab[16];
+    init_shift_table(a, s_tab);
+    __syncthreads();
+    const float D = a.ctl->dbound;
+    check_stencil(a, sys_view<true>(a.geo, a.batch, 0).geo, D);
+    const bool list_ok = list_current(a, D);
+    float t[kStatsN] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float vmax2 = 0.f;
+    // slot numbers fit 28 bits wherever lists are used (the entries' j field)
+    const int32_t n = (int32_t)a.n, stride = (int32_t)gridDim.x * kChunk;
+    for (int32_t i = (int32_t)blockIdx.x * kChunk + threadIdx.x; i < n; i += stride) {
+        const SysView sv = sys_view<true>(a.geo, a.batch, i);
+        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, true, SF>(a, sv.geo, sv.cell0, i, s_tab,
+                                                                  list_ok, t));
+    }
+    step_epilogue<kModeStep, false, true>(a, 0, D, vmax2, t);
+}
+
 // ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
 //      order inside a cell) ---------------------------------------------------
 
@@ -889,6 +913,8 @@ void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStrea
         if (a.stats) launch_step_k<kModeStep, true, B, SF>(a, grid, block, s);
         else if (!B && kStepLoopBlocksPerSM > 0)
             k_step_loop<SF><<<grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM), block, 0, s>>>(a);
+        else if (B && kStepBatchLoop)
+            k_step_batch_loop<SF><<<grid_for(a.n, kChunk, 16), block, 0, s>>>(a);
         else launch_step_k<kModeStep, false, B, SF>(a, grid, block, s);
     } else if (mode == kModeInit) {
         launch_step_k<kModeInit, true, B, SF>(a, grid, block, s);

@@ -82,11 +82,18 @@ typedef struct {
     double  dt;           /* MD time step (> 0)                                   */
     double  grid;         /* base grid g: a power of two; dx is a multiple of g   */
     double  skin;         /* minimum neighbour-cell skin beyond rcut (>= 0)        */
-    int32_t sort_every;   /* MD steps between cell re-sorts; 0 picks them: half the
-                             skin covered at 1.15 x the fastest initial speed, and
-                             later (unless use_graphs) at 1.1 x the larger of that
-                             speed and the fastest speed the device measured over
-                             the interval before the last one                    */
+    int32_t sort_every;   /* MD steps between cell re-sorts; 0 picks them.  With
+                             use_graphs: half the skin covered at 1.15 x the
+                             fastest initial speed.  Otherwise the device paces
+                             them: every step writes its displacement bound and
+                             largest speed to pinned host memory, and mdlg_step
+                             re-sorts before a step whose input bound, predicted
+                             from the values of 3 steps earlier (1.1 x that
+                             speed for the 2 steps between), would exceed half
+                             the skin.  mdlg_step then keeps at most 3 steps
+                             queued ahead of the device (it waits for the rest);
+                             the schedule depends only on device values, so a
+                             repeated or resumed run re-sorts at the same steps */
     double  dx;           /* lattice spacing Delta x (Sec. III)                   */
     int32_t nlags;        /* coarse time steps tracked, 1..MDLG_MAX_LAGS          */
     int32_t lag_steps[MDLG_MAX_LAGS]; /* Delta t of each, in MD steps (>= 1)      */
@@ -142,7 +149,9 @@ typedef struct {
                                      out of date (forces then came from the cell
                                      stencil: correct, slower); 0 when the re-sort
                                      schedule keeps up                           */
-    int32_t sort_every;           /* MD steps between re-sorts currently in use   */
+    int32_t sort_every;           /* MD steps between re-sorts: the fixed interval,
+                                     or (device-paced schedule) the length of the
+                                     last completed interval                     */
 } mdlg_stats_out;
 
 /*
@@ -200,7 +209,10 @@ int mdlg_stats_system(mdlg_ctx *ctx, int32_t system, mdlg_stats_out *out, uint64
  * count is a multiple of lag_steps[k], the particles are binned for lag k
  * (Eq. MDni) against their lattice cells lag_steps[k] steps earlier and the
  * counts are added to the lag's totals (Eq. fieq).  FP64 reductions run on
- * multiples of stats_every.  Asynchronous.  Errors: MDLG_EINVAL, MDLG_ECUDA.
+ * multiples of stats_every.  Asynchronous with a fixed re-sort interval;
+ * with the device-paced schedule (sort_every = 0, no graphs) it returns once
+ * the device has finished all but the last 3 steps.  Errors: MDLG_EINVAL,
+ * MDLG_ECUDA.
  */
 int mdlg_step(mdlg_ctx *ctx, int64_t nsteps);
 

@@ -1,10 +1,12 @@
 // mdlg_api.cu -- the C ABI of include/mdlg.h: context lifecycle, step
 // scheduling and host <-> device marshalling.  All arithmetic of the method
 // runs in the kernels of mdlg_md.cu and mdlg_bin.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -12,6 +14,11 @@
 #include "mdlg_kernels.h"
 
 using namespace mdlg;
+
+// Adaptive re-sort schedule: the host decides whether step t re-sorts from the
+// device values of step t - kPaceLag, so that many steps stay queued.
+constexpr int64_t kPaceLag = 3;
+static_assert(kPaceLag < kPaceRing, "the slot waited for must not be overwritten");
 
 struct mdlg_ctx {
     mdlg_params p{};
@@ -62,17 +69,17 @@ struct mdlg_ctx {
     int64_t step = 0, last_sort = 0, stats_step = -1;
     int64_t intervals[kMaxLags]{};
     int32_t sort_every = 1;
-    // adaptive re-sort interval (params.sort_every = 0, no graphs): at every
-    // re-sort the largest speed of the interval just ended is copied to pinned
-    // host memory; the interval that starts at the following re-sort is set
-    // from it (one interval behind, so the host never waits for the stream to
-    // drain, and the schedule depends only on device values at fixed steps)
+    // adaptive re-sort schedule (params.sort_every = 0, no graphs): every step
+    // launch writes its displacement bound and largest speed into a host-mapped
+    // ring; before queuing step t the host waits for the slot of step
+    // t - kPaceLag and re-sorts if the bound of step t's input, predicted from
+    // it, would reach half the skin (pace_decide).  sort_every is then the
+    // length of the last interval.
     bool adaptive = false;
     double vmax0 = 0.0;            // fastest uploaded speed
     double skin_eff = 0.0;         // MD cell width minus rc
-    int64_t nsorts = 0;            // re-sorts since the upload
-    uint32_t *h_run = nullptr;     // pinned: vmax2_run copied at the last two re-sorts
-    cudaEvent_t ev_run[2]{};
+    PaceSlot *pace = nullptr;      // host-mapped ring (kPaceRing slots), host view
+    PaceSlot *pace_dev = nullptr;  // the same ring, device view
     float rc = 0.f, round_margin = 0.f;
     // CUDA graph of two schedule periods (use_graphs)
     cudaGraph_t graph = nullptr;
@@ -135,6 +142,9 @@ void free_all(mdlg_ctx *c) {
         else c->alloc.free(p, c->alloc.user);
     }
     c->owned.clear();
+    if (c->pace) cudaFreeHost(c->pace);
+    c->pace = nullptr;
+    c->pace_dev = nullptr;
 }
 
 // Launch-group bracketing for mdlg_profile.
@@ -278,6 +288,8 @@ StepArgs step_args(mdlg_ctx *c) {
     a.ncount = c->ncount;
     a.cap = c->cap;
     a.list_skin = c->list_radius - (float)rc;
+    a.pace = c->pace_dev;
+    a.step = c->step;
     return a;
 }
 
@@ -323,24 +335,40 @@ int32_t interval_for(const mdlg_ctx *c, double v) {
     return (int32_t)std::fmax(1.0, std::fmin(k, 1000.0));
 }
 
-// Adaptive schedule, at a re-sort (before its kernels are queued): queue the
-// copy of the speed bound of the interval that ends here, and set the next
-// interval from the copy queued at the previous re-sort.
-int adapt_interval(mdlg_ctx *c) {
-    const int64_t n = ++c->nsorts;
-    if (n >= 2) {
-        const int b = (int)((n - 1) & 1);
-        MDLG_TRY(cuda_err(cudaEventSynchronize(c->ev_run[b])));
-        uint32_t bits = c->h_run[b];
-        float v2;
-        memcpy(&v2, &bits, sizeof(v2));
-        // 10 % above the larger of the measured and the initial fastest speed
-        c->sort_every = interval_for(c, 1.1 * std::fmax(std::sqrt((double)v2), c->vmax0));
+// Adaptive schedule: whether step t re-sorts.  The slot of step t - kPaceLag
+// holds the displacement bound of step t - kPaceLag + 1's input positions and
+// that step's largest speed; the bound of step t's input is predicted by adding
+// the remaining kPaceLag - 1 steps at 1.1x that speed (plus the per-step
+// rounding margin).  Step t re-sorts if twice the prediction exceeds the skin.
+// The host waits only for step t - kPaceLag, so kPaceLag steps stay queued, and
+// the decision depends only on device values of fixed steps: a run and its
+// repetition (or a resumed checkpoint) re-sort at the same steps.  Until
+// kPaceLag steps after a re-sort the last interval's length decides.
+int pace_decide(mdlg_ctx *c, bool *sort) {
+    const int64_t t = c->step, since = t - c->last_sort;
+    *sort = since >= c->sort_every;
+    if (since < kPaceLag) return MDLG_OK;
+    const int64_t s = t - kPaceLag;
+    volatile PaceSlot *ps = c->pace + (s & (kPaceRing - 1));
+    for (int64_t k = 1; ps->step != s; ++k) {
+        if (k % 64 == 0) {
+            const cudaError_t q = cudaStreamQuery(c->stream);
+            if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_err(q);
+            // the stream is idle and the slot was never written (no step launch
+            // for step s in this context): keep the interval rule
+            if (q == cudaSuccess && ps->step != s) return MDLG_OK;
+        }
+        std::this_thread::yield();
     }
-    const int b = (int)(n & 1);
-    MDLG_TRY(cuda_err(cudaMemcpyAsync(&c->h_run[b], &c->ctl->vmax2_run, sizeof(uint32_t),
-                                      cudaMemcpyDeviceToHost, c->stream)));
-    return cuda_err(cudaEventRecord(c->ev_run[b], c->stream));
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const float D = ps->dbound;
+    const uint32_t bits = ps->vmax2_bits;
+    float v2;
+    memcpy(&v2, &bits, sizeof(v2));
+    const double v = std::sqrt((double)v2);
+    const double pred = (double)D + (kPaceLag - 1) * (1.1 * v * c->p.dt + c->round_margin);
+    *sort = 2.0 * pred > c->skin_eff;
+    return MDLG_OK;
 }
 
 int do_sort(mdlg_ctx *c, bool launch = true) {
@@ -350,7 +378,7 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
         c->last_sort = c->step;
         return MDLG_OK;
     }
-    if (c->adaptive && c->step > 0) MDLG_TRY(adapt_interval(c));
+    if (c->adaptive && c->step > c->last_sort) c->sort_every = (int32_t)(c->step - c->last_sort);
     SortArgs s{};
     s.geo = c->geo;
     s.n = c->slots;
@@ -703,17 +731,16 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         c->sort_every = interval_for(c, 1.15 * vmax0);
         // with graphs the captured schedule needs a fixed interval
         if (!p.use_graphs) {
-            if (cudaMallocHost(&c->h_run, 2 * sizeof(uint32_t)) != cudaSuccess) {
+            void *ring = nullptr;
+            if (cudaHostAlloc(&ring, kPaceRing * sizeof(PaceSlot), cudaHostAllocMapped) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(MDLG_ENOMEM);
             }
-            c->h_run[0] = c->h_run[1] = 0u;
-            for (int b = 0; b < 2; ++b)
-                if ((rc = chk(cudaEventCreateWithFlags(&c->ev_run[b], cudaEventDisableTiming)))) {
-                    cudaFreeHost(c->h_run);
-                    c->h_run = nullptr;
-                    return fail(rc);
-                }
+            c->pace = static_cast<PaceSlot *>(ring);
+            for (int k = 0; k < kPaceRing; ++k) c->pace[k] = PaceSlot{-1, 0.0f, 0u};
+            void *dev = nullptr;
+            if ((rc = chk(cudaHostGetDevicePointer(&dev, ring, 0)))) return fail(rc);
+            c->pace_dev = static_cast<PaceSlot *>(dev);
             c->adaptive = true;
         }
     }
@@ -768,7 +795,9 @@ namespace {
 int step_loop(mdlg_ctx *c, int64_t nsteps, bool launch) {
     const mdlg_params &p = c->p;
     for (int64_t it = 0; it < nsteps; ++it) {
-        if (c->step - c->last_sort >= c->sort_every) MDLG_TRY(do_sort(c, launch));
+        bool sort = c->step - c->last_sort >= c->sort_every;
+        if (c->pace && launch) MDLG_TRY(pace_decide(c, &sort));
+        if (sort) MDLG_TRY(do_sort(c, launch));
         const bool stats = p.stats_every > 0 && c->step % p.stats_every == 0;
         if (launch) {
             StepArgs a = step_args(c);
@@ -1347,7 +1376,7 @@ namespace {
 
 // Checkpoint layout: a header, then the device regions below in this order.
 constexpr uint64_t kCkptMagic = 0x54504b43474c444dull;   // "MDLGCKPT"
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 struct CkptHeader {
     uint64_t magic;
@@ -1357,13 +1386,12 @@ struct CkptHeader {
     int64_t step, last_sort, stats_step;
     int64_t intervals[kMaxLags];
     int32_t pos_cur, meta_cur;
-    // the re-sort schedule: current interval, re-sorts so far, the speed bounds
-    // copied at the last two re-sorts, the fastest uploaded speed
+    // the re-sort schedule: current interval, the fastest uploaded speed and
+    // (adaptive schedule) the slots of the last kPaceLag steps (step -1: none)
     int32_t sort_every;
-    uint32_t run[2];
     int32_t pad_;
-    int64_t nsorts;
     double vmax0;
+    PaceSlot pace[kPaceLag];
 };
 
 struct Region {
@@ -1471,12 +1499,15 @@ int mdlg_save(mdlg_ctx *c, void *buf, uint64_t bytes) {
     for (int l = 0; l < kMaxLags; ++l) h.intervals[l] = c->intervals[l];
     h.pos_cur = c->pos_cur;
     h.meta_cur = c->meta_cur;
-    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));   // the speed copies have landed
+    MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));   // every slot has been written
     h.sort_every = c->sort_every;
-    h.run[0] = c->h_run ? c->h_run[0] : 0u;
-    h.run[1] = c->h_run ? c->h_run[1] : 0u;
-    h.nsorts = c->nsorts;
     h.vmax0 = c->vmax0;
+    for (int64_t k = 0; k < kPaceLag; ++k) {
+        const int64_t st = c->step - kPaceLag + k;
+        h.pace[k] = PaceSlot{-1, 0.0f, 0u};
+        if (c->pace && st >= 0 && c->pace[st & (kPaceRing - 1)].step == st)
+            h.pace[k] = c->pace[st & (kPaceRing - 1)];
+    }
     memcpy(buf, &h, sizeof(h));
     unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(h);
     for (const Region &g : ckpt_regions(c)) {
@@ -1510,11 +1541,12 @@ int mdlg_load(mdlg_ctx *c, const void *buf, uint64_t bytes) {
     c->stats_step = h.stats_step;
     if (h.sort_every < 1) return MDLG_EINVAL;
     c->sort_every = h.sort_every;
-    c->nsorts = h.nsorts;
     c->vmax0 = h.vmax0;
-    if (c->h_run) {
-        c->h_run[0] = h.run[0];
-        c->h_run[1] = h.run[1];
+    if (c->pace) {
+        for (int k = 0; k < kPaceRing; ++k) c->pace[k] = PaceSlot{-1, 0.0f, 0u};
+        for (int64_t k = 0; k < kPaceLag; ++k)
+            if (h.pace[k].step >= 0 && h.pace[k].step == c->step - kPaceLag + k)
+                c->pace[h.pace[k].step & (kPaceRing - 1)] = h.pace[k];
     }
     for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = h.intervals[l];
     return MDLG_OK;
@@ -1551,9 +1583,6 @@ void mdlg_destroy(mdlg_ctx *c) {
     cudaStreamSynchronize(c->stream);
     drop_graph(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    for (int b = 0; b < 2; ++b)
-        if (c->ev_run[b]) cudaEventDestroy(c->ev_run[b]);
-    if (c->h_run) cudaFreeHost(c->h_run);
     free_all(c);
     delete c;
 }

@@ -142,9 +142,18 @@ struct Control {
     double stats[8];           // ke, pe, virial, px, py of the last stats launch
     unsigned long long vmax0_bits;   // max |v|^2 of the uploaded state (FP64 bits; >= 0)
     long long stats_acc[5];    // fixed-point sums of a running stats launch (zero at rest)
-    uint32_t vmax2_run;        // max |v|^2 of the half-step velocities since the last re-sort
     uint32_t stale_steps;      // step launches that found the Verlet list out of date
 };
+
+// One MD step's displacement bound and largest speed, written by the last block
+// of the step launch into host-mapped memory; the host paces the re-sorts from
+// these (ring of kPaceRing slots indexed by step).
+struct PaceSlot {
+    int64_t step;              // MD step whose launch wrote the slot (-1: empty)
+    float dbound;              // bound after that step (the next step's input positions)
+    uint32_t vmax2_bits;       // largest |v|^2 of the step's half-step velocities (float bits)
+};
+constexpr int kPaceRing = 8;
 
 enum StepMode : int32_t {
     kModeStep = 0,   // F(x_n); v_{n+1/2} = v_{n-1/2} + F dt/m; x_{n+1} = x_n + v dt
@@ -177,6 +186,8 @@ struct StepArgs {
     int32_t stats;              // 1: FP64 reductions (Control::stats, or per system in a batch)
     Control *ctl;
     Batch batch;
+    PaceSlot *pace;             // kModeStep: host-mapped ring for this step's bound, or null
+    int64_t step;               // MD step of this launch (slot step % kPaceRing)
 };
 
 cudaError_t launch_step(const StepArgs &a, int mode, cudaStream_t s);

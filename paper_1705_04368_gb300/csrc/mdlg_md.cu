@@ -417,9 +417,18 @@ __device__ __forceinline__ void step_epilogue(const StepArgs &a, int64_t sys, fl
     if (threadIdx.x == 0) {
         if (MODE == kModeStep) {
             const uint32_t bits = atomicExch(&a.ctl->vmax2_bits, 0u);
-            atomicMax(&a.ctl->vmax2_run, bits);   // non-negative floats order like their bits
             const float vmax = sqrtf(__uint_as_float(bits));
-            a.ctl->dbound = D + vmax * a.dt * 1.000001f + a.round_margin;
+            const float dn = D + vmax * a.dt * 1.000001f + a.round_margin;
+            a.ctl->dbound = dn;
+            if (a.pace) {
+                // host-mapped slot: the values first, then (after a system-scope
+                // fence) the step number that marks them complete
+                volatile PaceSlot *ps = a.pace + (a.step & (kPaceRing - 1));
+                ps->dbound = dn;
+                ps->vmax2_bits = bits;
+                __threadfence_system();
+                ps->step = a.step;
+            }
         }
         a.ctl->done = 0u;
     }
@@ -612,7 +621,6 @@ __global__ void k_cell_start(SortArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.cell_start[a.ncells] = (int32_t)a.n;
         a.ctl->dbound = 0.0f;
-        a.ctl->vmax2_run = 0u;
     }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncells; c += stride)
         a.cell_start[c] = cell_begin(a, c);

@@ -105,11 +105,16 @@ def test_late_resort_uses_wider_stencil(cuda):
     assert st["status"] == 0
 
 
-def test_resort_interval_from_fastest_initial_speed(cuda):
-    # sort_every = 0: the first re-sort comes after floor(skin_eff / (2 x 1.15 vmax0 dt))
-    # steps, vmax0 the fastest initial speed (reduced on the device by the upload
-    # kernel); counted from the re-sort launches (7 per re-sort).  Later intervals
-    # follow the fastest speed the device measured, so the list never goes stale.
+def test_device_paced_resort_schedule(cuda):
+    # sort_every = 0 without graphs: the device paces the re-sorts.  Until 3
+    # steps after the upload the interval rule of the fastest initial speed
+    # (half the skin at 1.15 vmax0) applies, so no re-sort comes in the first
+    # 3 steps; afterwards a step re-sorts only when the displacement bound of
+    # its input would pass half the skin.  Over 400 steps: the list never goes
+    # stale, the intervals are no shorter than ~0.8x the fixed rule's (the
+    # fastest speed of a step stays near the initial one at T = 1), and a
+    # second context on the same input re-sorts at the same steps (identical
+    # positions and launch counts).
     n, L = 4096, mi.box_for(4096, 0.3, 4.0)
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=78)
     p = m.Params(n=n, box=L, dx=4.0, lag_steps=(5,))
@@ -117,27 +122,33 @@ def test_resort_interval_from_fastest_initial_speed(cuda):
     skin_eff = k * p.grid - p.rcut
     vmax0 = math.sqrt(float((v0 * v0).sum(axis=1).max()))
     every = int(max(1.0, min(math.floor(0.5 * skin_eff / (1.15 * vmax0 * p.dt)), 1000.0)))
-    assert 2 <= every <= 50
-    with m.Simulation(p, x0, v0) as s:
-        s.profile(True)
-        s.step(every)
-        assert s.profile(False)["sort"][1] == 0
-        s.profile(True)
-        s.step(1)
-        assert s.profile(False)["sort"][1] == 7
-        s.step(400)
-        st, _, _ = s.stats()
-    assert st["status"] == 0 and st["stale_steps"] == 0
-    # the adapted interval: 1.1 x the larger of the measured and the initial fastest speed
-    assert every * 0.7 <= st["sort_every"] <= every * 1.15 / 1.1 + 1
+    assert 4 <= every <= 50
+    runs = []
+    for _ in range(2):
+        with m.Simulation(p, x0, v0) as s:
+            s.profile(True)
+            s.step(3)
+            assert s.profile(False)["sort"][1] == 0
+            s.profile(True)
+            s.step(397)
+            sorts = s.profile(False)["sort"][1]
+            assert sorts % 7 == 0             # 7 launches per re-sort
+            x, _ = s.get_state()
+            st, _, _ = s.stats()
+        assert st["status"] == 0 and st["stale_steps"] == 0
+        assert 1 <= sorts // 7 <= 400 / (0.8 * every) + 1, (sorts // 7, every)
+        assert st["sort_every"] >= 0.8 * every
+        runs.append((sorts, x))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
 
 
-@pytest.mark.parametrize("rho,T,steps,max_stale_frac", [(0.3, 1.0, 600, 0.0), (0.6, 0.8, 600, 0.03)])
+@pytest.mark.parametrize("rho,T,steps,max_stale_frac", [(0.3, 1.0, 600, 0.0), (0.6, 0.8, 600, 0.01)])
 def test_adaptive_resort_keeps_the_list_current(cuda, rho, T, steps, max_stale_frac):
     # A gas placed at random heats up as it relaxes (at rho = 0.6, T = 0.8 the
     # fastest speed grows by 30-50 %): a schedule fixed from the initial speeds
     # lets the Verlet list go stale (every such step takes the slower cell
-    # stencil); the adaptive schedule keeps up, and the trajectory still
+    # stencil); the device-paced schedule keeps up, and the trajectory still
     # conserves momentum exactly and energy to the FP32 bound.
     n = 65536
     L = mi.box_for(n, rho, 4.0)

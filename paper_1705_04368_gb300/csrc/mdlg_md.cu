@@ -630,8 +630,10 @@ __global__ void k_cell_start(SortArgs a) {
 // finds its rank by particle number among its cell's arrivals, then is copied
 // from the old order to its final place, its position re-expressed against the
 // new cell's origin.
-template <bool B>
-__global__ void k_sort_scatter(SortArgs a) {
+// Without MSD the kernel fits 32 registers (8 blocks of 256 per SM: full
+// occupancy for the gathers from the old order).
+template <bool B, bool MSD>
+__global__ void __launch_bounds__(256, MSD ? 4 : 8) k_sort_scatter(SortArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
         const SysView sv = sys_view<B>(a.geo, a.batch, t);
@@ -646,13 +648,14 @@ __global__ void k_sort_scatter(SortArgs a) {
         const float2 p = a.cl_in[from];
         const float2 vv = a.v_in[from];
         const int32_t pid = a.pid_in[from];
+        // MSD (a compile-time choice): the offsets at each lag's last binning
+        // move too, so without it they take no registers
         uint32_t lp[kMaxLags];
-        float2 mp[kMaxLags];
-        const bool msd = a.mprev_in[0] != nullptr;
+        float2 mp[MSD ? kMaxLags : 1];
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l) {
             lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
-            mp[l] = (msd && l < a.nlags) ? a.mprev_in[l][from] : make_float2(0.f, 0.f);
+            if (MSD) mp[l] = l < a.nlags ? a.mprev_in[l][from] : make_float2(0.f, 0.f);
         }
         const int64_t c = key_cell<B>(sv, cw);
         const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
@@ -674,7 +677,7 @@ __global__ void k_sort_scatter(SortArgs a) {
         for (int l = 0; l < kMaxLags; ++l)
             if (l < a.nlags) {
                 a.lprev_out[l][to] = lp[l];
-                if (msd) a.mprev_out[l][to] = make_float2(mp[l].x + sx, mp[l].y + sy);
+                if (MSD) a.mprev_out[l][to] = make_float2(mp[l].x + sx, mp[l].y + sy);
             }
     }
 }
@@ -682,7 +685,8 @@ __global__ void k_sort_scatter(SortArgs a) {
 // Verlet list of the freshly sorted state: every j != i closer than the list
 // radius, found in the 3 x 3 cell stencil (cells are at least that wide and
 // every particle is inside its cell).  Candidates are fetched four at a time
-// (predicated) so their loads overlap.  Every candidate's entry is written to
+// (predicated; past the end of a range the position is a far sentinel whose
+// distance fails the radius test) so their loads overlap.  Every candidate's entry is written to
 // the next free staging slot and the count advances only on a hit, so the
 // lanes of a warp do not diverge over the test (staging holds cap + 1 slots per
 // thread: entries past the capacity all land in the spare one, and such a list
@@ -736,7 +740,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const bool g1 = j >= m1, g2 = j >= m2;   // in cell cx, cx + 1
                             const float odx = g2 ? sxp : (g1 ? 0.0f : sxm);
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            const bool hit = j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            const bool hit = j != i && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] =
                                 ((uint32_t)j | ycode) + (g1 ? (1u << 28) : 0u) + (g2 ? (1u << 28) : 0u);
                             cnt += hit;
@@ -760,7 +764,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                         for (int u = 0; u < 4; ++u) {
                             const int32_t j = b + u;
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            const bool hit = j < e && j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            const bool hit = j != i && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] = (uint32_t)j | code;
                             cnt += hit;
                         }
@@ -960,7 +964,8 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
     k_sort_place<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
-    k_sort_scatter<B><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    if (a.mprev_in[0]) k_sort_scatter<B, true><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    else k_sort_scatter<B, false><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     if (a.nbr) {
         const int nt = (size_t)kNlistThreads * (a.cap + 1) * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;
         const size_t smem = sizeof(uint32_t) * (size_t)nt * (a.cap + 1);

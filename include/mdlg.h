@@ -73,7 +73,8 @@ extern "C" {
  */
 typedef struct {
     int32_t dim;          /* must be 2 (the paper's test case, Sec. IV)          */
-    int64_t n;            /* particles, >= 1                                     */
+    int64_t n;            /* particles, >= 1 (at most 2^28 slots, counting a
+                             batch's padding, with a potential)                 */
     double  box[2];       /* periodic box L_x, L_y; integer multiples of dx       */
     int32_t potential;    /* MDLG_POT_LJ_TS, MDLG_POT_LJ_SF or MDLG_POT_NONE      */
     double  eps, sigma;   /* Lennard-Jones energy and length (Sec. IV)            */

@@ -50,6 +50,7 @@ struct mdlg_ctx {
     uint32_t *key = nullptr;
     int32_t *slot = nullptr, *count = nullptr, *block_sums = nullptr;
     unsigned long long *entry = nullptr;
+    uint8_t *col = nullptr;        // base column inside the new cell (lists on)
     Control *ctl = nullptr;
     unsigned long long *counts = nullptr;   // nlags x q1
     uint32_t *site_n = nullptr, *site_counts = nullptr;
@@ -407,6 +408,7 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
     s.slot = c->slot;
     s.count = c->count;
     s.entry = c->entry;
+    s.col = c->col;
     s.block_sums = c->block_sums;
     s.ctl = c->ctl;
     s.nbr = c->nbr;
@@ -583,6 +585,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         c->ncells = cell;
     }
     if (c->ncells > (int64_t)4096 * 4096) return early(MDLG_EINVAL);
+    // Verlet-list entries hold slot numbers in 28 bits
+    if (p.potential != MDLG_POT_NONE && c->slots > ((int64_t)1 << 28)) return early(MDLG_EINVAL);
     c->ratio_shift = log2_exact(g.ratio);
     c->q1 = (2 * p.vmax + 1) * (2 * p.vmax + 1) + 1;
     for (int a = 0; a < 2; ++a) c->shift_m[a] = std::llround(p.lattice_u[a] * p.dt / p.grid * 16777216.0);
@@ -646,7 +650,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         const double mean = rho_max * 3.14159265358979 * (double)c->list_radius * c->list_radius;
         c->cap = (int32_t)std::ceil((3.0 * mean + 16.0) / 4.0) * 4;
         if (c->cap > 512) c->cap = 512;   // list-build staging: 64 threads x (cap + 1) words of shared memory
-        if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)))
+        if ((rc = alloc_n(c, &c->nbr, (size_t)c->cap * N)) || (rc = alloc_n(c, &c->ncount, N)) ||
+            (rc = alloc_n(c, &c->col, N)))
             return fail(rc);
     }
 

@@ -217,6 +217,7 @@ struct SortArgs {
     int32_t *slot;           // n
     int32_t *count;          // ncells
     unsigned long long *entry;  // n
+    uint8_t *col;            // n: base column inside the new MD cell (lists on), or null
     int32_t *block_sums;     // scan partials
     Control *ctl;
     // Verlet list built from the sorted state (nbr null: none)

@@ -511,8 +511,9 @@ __global__ void __launch_bounds__(kChunk, 16) k_step_batch_loop(StepArgs a) {
     step_epilogue<kModeStep, false, true>(a, 0, D, vmax2, t);
 }
 
-// ---- neighbour-cell sort (counting sort keyed by MD cell, particle-number
-//      order inside a cell) ---------------------------------------------------
+// ---- neighbour-cell sort (counting sort keyed by MD cell; inside a cell by
+//      base column, then particle number, when Verlet lists are built, else by
+//      particle number) -------------------------------------------------------
 
 
 template <bool B>
@@ -524,6 +525,7 @@ __global__ void k_sort_key(SortArgs a) {
         const uint32_t cw = a.cell_in[i];
         uint32_t key = kGhostCell;
         int64_t c = sv.cell0 + sv.ncells;   // a system's ghost cell
+        int32_t col = 0;                    // base column inside the new cell
         if (!B || cw != kGhostCell) {
             const float2 p = a.cl_in[i];
             const int32_t bx = base_cell(cell_x(cw) * geo.k, p.x, geo.inv_g, geo.lg[0]);
@@ -533,8 +535,10 @@ __global__ void k_sort_key(SortArgs a) {
             ny = ny < geo.nc[1] ? ny : geo.nc[1] - 1;
             key = (uint32_t)nx | ((uint32_t)ny << 16);
             c = sv.cell0 + ny * geo.nc[0] + nx;
+            col = bx - nx * geo.k;
         }
         a.key[i] = key;
+        if (a.col) a.col[i] = (uint8_t)(col < 15 ? col : 15);
         a.slot[i] = atomicAdd(&a.count[c], 1);
     }
 }
@@ -610,7 +614,10 @@ __global__ void k_sort_place(SortArgs a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const SysView sv = sys_view<B>(a.geo, a.batch, i);
         const int64_t at = (int64_t)cell_begin(a, key_cell<B>(sv, a.key[i])) + a.slot[i];
-        a.entry[at] = ((unsigned long long)(uint32_t)a.pid_in[i] << 32) | (uint32_t)i;
+        // rank key of the scatter: base column (lists on; particle numbers are
+        // then below 2^28), then particle number
+        const uint32_t rk = (uint32_t)a.pid_in[i] + (a.col ? (uint32_t)a.col[i] << 28 : 0u);
+        a.entry[at] = ((unsigned long long)rk << 32) | (uint32_t)i;
     }
 }
 
@@ -627,7 +634,8 @@ __global__ void k_cell_start(SortArgs a) {
 }
 
 // One thread per slot of the new order: the particle that arrived in that slot
-// finds its rank by particle number among its cell's arrivals, then is copied
+// finds its rank by its entry's rank key (base column, then particle number)
+// among its cell's arrivals, then is copied
 // from the old order to its final place, its position re-expressed against the
 // new cell's origin.
 // Without MSD the kernel fits 32 registers (8 blocks of 256 per SM: full
@@ -724,10 +732,34 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                 const int32_t row = ny * geo.nc[0];
                 if (interior) {
                     // cells cx-1, cx, cx+1 of this row are one contiguous range
-                    const int32_t s = __ldg(cs + row + cx - 1);
+                    const int32_t s0 = __ldg(cs + row + cx - 1);
                     const int32_t m1 = __ldg(cs + row + cx);
                     const int32_t m2 = __ldg(cs + row + cx + 1);
-                    const int32_t e = __ldg(cs + row + cx + 2);
+                    const int32_t e0 = __ldg(cs + row + cx + 2);
+                    // A candidate of cell cx-1 whose offset is below p.x, or of
+                    // cell cx+1 above it, lies a whole cell width (the list
+                    // radius) or more away along x: its rounded distance fails
+                    // the test below.  Cells are ordered by base column, so such
+                    // candidates lead cell cx-1 and trail cell cx+1; up to four
+                    // are dropped at each end of the range.
+                    int32_t s = s0, e = e0;
+                    {
+                        const float *clx = reinterpret_cast<const float *>(a.cl_out);
+                        float lx[4], rx[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            lx[u] = s0 + u < m1 ? __ldg(clx + 2 * (int64_t)(s0 + u)) : 3.0e38f;
+                            rx[u] = e0 - 1 - u >= m2 ? __ldg(clx + 2 * (int64_t)(e0 - 1 - u)) : -3.0e38f;
+                        }
+                        bool gl = true, gr = true;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            gl = gl && lx[u] < p.x;
+                            gr = gr && rx[u] > p.x;
+                            s += gl;
+                            e -= gr;
+                        }
+                    }
                     for (int32_t b = s; b < e; b += 4) {
                         float2 q[4];
 #pragma unroll

@@ -73,6 +73,27 @@ def test_batch_of_one_equals_single(cuda):
     assert np.array_equal(xb, x1) and np.array_equal(cb, c1)
 
 
+def test_batch_paced_resorts_are_deterministic(cuda):
+    # sort_every = 0 without graphs: the device paces the batch's re-sorts from
+    # the largest displacement bound of all systems.  The lists stay current and
+    # a second batch on the same input re-sorts at the same steps.
+    xs, vs, ns, boxes = _states()
+    p = _params(sort_every=0)
+    runs = []
+    for _ in range(2):
+        with m.BatchSimulation(p, ns, boxes, np.concatenate(xs), np.concatenate(vs)) as bt:
+            bt.profile(True)
+            bt.step(300)
+            sorts = bt.profile(False)["sort"][1]
+            xb, vb = bt.get_state()
+            st = bt.stats()[0]
+        assert st["status"] == 0 and st["stale_steps"] == 0
+        assert sorts > 0
+        runs.append((sorts, xb, vb))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+
+
 def test_batch_rejects_per_site_outputs_and_bad_boxes(cuda):
     xs, vs, ns, boxes = _states()
     with pytest.raises(m.MdlgError):

@@ -326,14 +326,17 @@ int mdlg_profile(mdlg_ctx *ctx, int enable, double *ms, int64_t *launches);
  * state of a context -- sorted particle state, every lag's stored lattice cells
  * (and displacement origins), the Verlet list of the last re-sort, the device
  * control block, MDLG totals, per-site fields and the host schedule (step, last
- * re-sort, binned intervals) -- so that a context restored from it continues
- * bit for bit as the saved one would have.
+ * re-sort, binned intervals, the device-paced schedule's last three step slots)
+ * -- so that a context restored from it continues bit for bit as the saved one
+ * would have.
  *
  * mdlg_checkpoint_size -- bytes of this context's checkpoint (host out).
  * mdlg_save  -- synchronize and write the checkpoint into buf (host memory of at
  *               least that many bytes).
  * mdlg_load  -- restore a checkpoint into a context created with the same
- *               parameters (use_graphs and stats_every may differ) and, for a
+ *               parameters (stats_every may differ, and use_graphs too when
+ *               sort_every > 0: with sort_every = 0 it selects the schedule)
+ *               and, for a
  *               batch, the same systems; the state it was created with is
  *               replaced.  Synchronizes.
  * Errors: MDLG_EINVAL (NULL arguments, buffer too small, not a checkpoint, or

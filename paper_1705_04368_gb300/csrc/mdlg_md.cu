@@ -692,9 +692,10 @@ __global__ void __launch_bounds__(256, MSD ? 4 : 8) k_sort_scatter(SortArgs a) {
 
 // Verlet list of the freshly sorted state: every j != i closer than the list
 // radius, found in the 3 x 3 cell stencil (cells are at least that wide and
-// every particle is inside its cell).  Candidates are fetched four at a time
-// (predicated; past the end of a range the position is a far sentinel whose
-// distance fails the radius test) so their loads overlap.  Every candidate's entry is written to
+// every particle is inside its cell).  Candidates are fetched a few at a time
+// (two in the interior rows, whose ranges are short after the skip below; four
+// elsewhere; predicated: past the end of a range the position is a far sentinel
+// whose distance fails the radius test) so their loads overlap.  Every candidate's entry is written to
 // the next free staging slot and the count advances only on a hit, so the
 // lanes of a warp do not diverge over the test (staging holds cap + 1 slots per
 // thread: entries past the capacity all land in the spare one, and such a list
@@ -760,14 +761,14 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             e -= gr;
                         }
                     }
-                    for (int32_t b = s; b < e; b += 4) {
-                        float2 q[4];
+                    for (int32_t b = s; b < e; b += 2) {
+                        float2 q[2];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
+                        for (int u = 0; u < 2; ++u)
                             q[u] = (b + u < e) ? __ldg(a.cl_out + b + u)
                                                : make_float2(1.0e18f, 1.0e18f);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 2; ++u) {
                             const int32_t j = b + u;
                             const bool g1 = j >= m1, g2 = j >= m2;   // in cell cx, cx + 1
                             const float odx = g2 ? sxp : (g1 ? 0.0f : sxm);

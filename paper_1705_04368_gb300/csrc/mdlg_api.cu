@@ -338,18 +338,21 @@ int32_t interval_for(const mdlg_ctx *c, double v) {
 
 // Adaptive schedule: whether step t re-sorts.  The slot of step t - kPaceLag
 // holds the displacement bound of step t - kPaceLag + 1's input positions and
-// that step's largest speed; the bound of step t's input is predicted by adding
-// the remaining kPaceLag - 1 steps at 1.1x that speed (plus the per-step
-// rounding margin).  Step t re-sorts if twice the prediction exceeds the skin.
-// The host waits only for step t - kPaceLag, so kPaceLag steps stay queued, and
-// the decision depends only on device values of fixed steps: a run and its
-// repetition (or a resumed checkpoint) re-sort at the same steps.  Until
-// kPaceLag steps after a re-sort the last interval's length decides.
+// that step's largest speed v.  The bound of step t's input is predicted from
+// it: the slot's bound plus the remaining kPaceLag - 1 steps at 1.1 v (plus the
+// per-step rounding margin), or, when the last re-sort came after that slot's
+// step (the bound restarted from zero there), the steps since the re-sort at
+// 1.1 v.  Step t re-sorts if twice the prediction exceeds the skin.  The host
+// waits only for step t - kPaceLag, so kPaceLag steps stay queued, and the
+// decision depends only on device values of fixed steps: a run and its
+// repetition (or a resumed checkpoint) re-sort at the same steps.  Before the
+// first kPaceLag steps of a context, or when no step of this context wrote the
+// slot, the last interval's length decides.
 int pace_decide(mdlg_ctx *c, bool *sort) {
     const int64_t t = c->step, since = t - c->last_sort;
     *sort = since >= c->sort_every;
-    if (since < kPaceLag) return MDLG_OK;
     const int64_t s = t - kPaceLag;
+    if (s < 0) return MDLG_OK;
     volatile PaceSlot *ps = c->pace + (s & (kPaceRing - 1));
     for (int64_t k = 1; ps->step != s; ++k) {
         if (k % 64 == 0) {
@@ -366,8 +369,9 @@ int pace_decide(mdlg_ctx *c, bool *sort) {
     const uint32_t bits = ps->vmax2_bits;
     float v2;
     memcpy(&v2, &bits, sizeof(v2));
-    const double v = std::sqrt((double)v2);
-    const double pred = (double)D + (kPaceLag - 1) * (1.1 * v * c->p.dt + c->round_margin);
+    const double per_step = 1.1 * std::sqrt((double)v2) * c->p.dt + c->round_margin;
+    const double pred = since >= kPaceLag ? (double)D + (kPaceLag - 1) * per_step
+                                          : (double)since * per_step;
     *sort = 2.0 * pred > c->skin_eff;
     return MDLG_OK;
 }

@@ -143,6 +143,37 @@ def test_device_paced_resort_schedule(cuda):
     assert np.array_equal(runs[0][1], runs[1][1])
 
 
+def test_paced_schedule_recovers_after_a_hot_start(cuda):
+    # One particle launched at 12 sigma/tau into a T = 1 gas with a small skin
+    # (cells of 2.75 sigma): the first interval from the fastest uploaded speed is
+    # a single step.  Once that particle has shared its energy (a few hundred
+    # steps), the re-sorts must come every few steps again, predicted from the
+    # device's speeds even in the first steps after each re-sort, and not stay at
+    # the first interval's length.
+    n, L = 4096, mi.box_for(4096, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=79)
+    v0 = v0.copy()
+    v0[0] = (12.0, 0.0)
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=(5,), grid=0.25, skin=0.25)
+    k = math.ceil((p.rcut + p.skin) / p.grid - 1e-12)
+    skin_eff = k * p.grid - p.rcut
+    assert math.floor(0.5 * skin_eff / (1.15 * 12.0 * p.dt)) <= 1
+    runs = []
+    for _ in range(2):
+        with m.Simulation(p, x0, v0) as s:
+            s.step(400)
+            s.profile(True)
+            s.step(100)
+            sorts = s.profile(False)["sort"][1] // 7
+            x, _ = s.get_state()
+            st, _, _ = s.stats()
+        assert st["status"] == 0
+        assert st["stale_steps"] <= 10, st["stale_steps"]
+        assert 1 <= sorts <= 50, sorts          # intervals of two steps or more
+        runs.append((sorts, x))
+    assert runs[0][0] == runs[1][0] and np.array_equal(runs[0][1], runs[1][1])
+
+
 @pytest.mark.parametrize("rho,T,steps,max_stale_frac", [(0.3, 1.0, 600, 0.0), (0.6, 0.8, 600, 0.01)])
 def test_adaptive_resort_keeps_the_list_current(cuda, rho, T, steps, max_stale_frac):
     # A gas placed at random heats up as it relaxes (at rho = 0.6, T = 0.8 the

@@ -90,8 +90,8 @@ typedef struct {
                              largest speed to pinned host memory, and mdlg_step
                              re-sorts before a step whose input bound, predicted
                              from the values of 3 steps earlier (1.1 x that
-                             speed for the 2 steps between), would exceed half
-                             the skin.  mdlg_step then keeps at most 3 steps
+                             speed for the steps between, or for the steps since
+                             a more recent re-sort), would exceed half the skin.  mdlg_step then keeps at most 3 steps
                              queued ahead of the device (it waits for the rest);
                              the schedule depends only on device values, so a
                              repeated or resumed run re-sorts at the same steps */

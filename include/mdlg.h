@@ -115,6 +115,9 @@ typedef struct {
                              exact.  {0, 0}: the lattice is at rest.               */
     int32_t msd;          /* 1: accumulate, for every lag, the mean-square
                              displacement <dx_a^2> over the lag (Sec. IV-A)       */
+    int32_t vacf;         /* 1: accumulate, for every lag, the velocity
+                             correlation <v_a(t) v_a(t - Dt)> over the lag
+                             (Sec. IV-A, Fig. VD(a)); see mdlg_stats_out.vacf  */
 } mdlg_params;
 
 /*
@@ -153,6 +156,13 @@ typedef struct {
     int32_t sort_every;           /* MD steps between re-sorts: the fixed interval,
                                      or (device-paced schedule) the length of the
                                      last completed interval                     */
+    double  vacf[MDLG_MAX_LAGS][2];/* params.vacf: <v_a(t) v_a(t - Dt)> per lag and
+                                     axis, the mean over particles and binned
+                                     intervals (0 if off).  v(t) is the leapfrog
+                                     half-step velocity of the step that ends at
+                                     t, (x(t) - x(t - dt)) / dt (at t = 0:
+                                     v_0 - F(x_0) dt / 2m), so both ends of the
+                                     correlation are sampled half a step early  */
 } mdlg_stats_out;
 
 /*
@@ -179,8 +189,8 @@ int mdlg_create(const mdlg_params *params, const double *x0, const double *v0,
  * trajectory and counts are exactly those of a context made for it alone with
  * the same sort_every (set sort_every > 0 to compare).
  *   params : shared parameters; params->n and params->box are ignored;
- *            params->site_mode and params->msd must be 0 and
- *            params->lattice_u {0, 0}.
+ *            params->site_mode, params->msd and params->vacf must be 0
+ *            and params->lattice_u {0, 0}.
  *   nsys   : systems, 1..65535.
  *   n      : host, nsys particle counts; each system is padded to a multiple
  *            of 128 slots, and the total of the padded counts must stay

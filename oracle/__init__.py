@@ -10,7 +10,8 @@ Contents
                  forces, velocity-Verlet, MDLG occupation numbers (Eq. MDni),
                  the binary32 ideal-gas stream-and-bin, FP64 reductions, the
                  moving lattice of Sec. IV, the collision operator Xi_i (Eq.
-                 Xi), the mean-square displacement (Sec. IV-A).
+                 Xi), the mean-square displacement and the velocity
+                 correlation (Sec. IV-A).
   closed_form.py the Gaussian/wedge equilibrium of Eq. fialpha.
 
 Parity status per function (what pins it, see tests/test_oracle_*.py):
@@ -35,6 +36,11 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                      conservation without overflow, the Fig. 2 worked example.
   msd                pinned: exact dyadic free flight across the boundary; the
                      ballistic value T dt^2 within sampling error.
+  half_velocity      pinned: equal to v_n + F(x_n) dt / 2m from the oracle's own
+                     forces after a velocity-Verlet step; exact in free flight.
+  vacf               pinned: free flight gives <v_a^2> exactly; the correlation
+                     of the one-step velocities with themselves, times dt^2,
+                     equals msd over that step.
   closed_form        pinned: numerical quadrature of the wedge integral (Eq.
                      fieqW), Monte-Carlo binning, normalisation and first
                      moment identities, the second-moment offset of Sec. VI.
@@ -112,6 +118,8 @@ def _load():
             lib.oracle_mdlg_bin_shifted.argtypes = [I64, P, P, D, P, ctypes.c_int, P, P, P, P, P, P]
             lib.oracle_collision.argtypes = [P, ctypes.c_int, P, P, P]
             lib.oracle_msd.argtypes = [I64, P, P, P, P]
+            lib.oracle_half_velocity.argtypes = [I64, P, P, P, D, P]
+            lib.oracle_vacf.argtypes = [I64, P, P, P]
             lib.oracle_kinetic.argtypes = [I64, P, D, P]
             lib.oracle_set_shifted_force.argtypes = [ctypes.c_int]
             lib.oracle_set_shifted_force.restype = None
@@ -122,7 +130,8 @@ def _load():
             for name in ("oracle_lj_forces_direct", "oracle_lj_forces_cells",
                          "oracle_lj_forces_sample", "oracle_vv", "oracle_free_stream",
                          "oracle_mdlg_bin", "oracle_stream_bin_f32", "oracle_kinetic",
-                         "oracle_mdlg_bin_shifted", "oracle_collision", "oracle_msd"):
+                         "oracle_mdlg_bin_shifted", "oracle_collision", "oracle_msd",
+                         "oracle_half_velocity", "oracle_vacf"):
                 getattr(lib, name).restype = None
             _lib = lib
     return _lib
@@ -281,6 +290,31 @@ def msd(xprev, xcur, box):
     xp, xc = _f64(xprev), _f64(xcur)
     out = np.zeros(2)
     lib.oracle_msd(xp.shape[0], _p(xp), _p(xc), _p(_f64(box)), _p(out))
+    return out
+
+
+def half_velocity(xprev, xcur, box, dt):
+    """Leapfrog half-step velocity of the step from xprev to xcur: the
+    minimum-image displacement over dt."""
+    xp, xc = _f64(xprev), _f64(xcur)
+    out = np.zeros_like(xc)
+    _load().oracle_half_velocity(xp.shape[0], _p(xp), _p(xc), _p(_f64(box)), float(dt), _p(out))
+    return out
+
+
+def initial_half_velocity(x0, v0, box, dt, mass=1.0, eps=1.0, sigma=1.0, rc=2.5,
+                          shifted_force=False):
+    """v_{-1/2} = v_0 - F(x_0) dt / (2m): the half-step velocity before the first step."""
+    f, _, _, _ = lj_forces(x0, box, eps, sigma, rc, cells=_f64(x0).shape[0] > 2048,
+                           shifted_force=shifted_force)
+    return _f64(v0) - f * (dt / (2.0 * mass))
+
+
+def vacf(vprev, vcur):
+    """Per axis, the mean over particles of v_a(now) v_a(before) (Sec. IV-A)."""
+    vp, vc = _f64(vprev), _f64(vcur)
+    out = np.zeros(2)
+    _load().oracle_vacf(vp.shape[0], _p(vp), _p(vc), _p(out))
     return out
 
 

@@ -517,3 +517,29 @@ void oracle_msd(int64_t n, const double *xprev, const double *xcur, const double
     out[0] = n ? sx / (double)n : 0.0;
     out[1] = n ? sy / (double)n : 0.0;
 }
+
+
+/* Leapfrog half-step velocity of the step that ends at xcur (Sec. III,
+ * velocity Verlet): v = (xcur - xprev) / dt, the displacement taken by minimum
+ * image (one step moves far less than half the box). */
+void oracle_half_velocity(int64_t n, const double *xprev, const double *xcur, const double *L,
+                          double dt, double *vout)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        vout[2 * j] = min_image(xcur[2 * j] - xprev[2 * j], L[0]) / dt;
+        vout[2 * j + 1] = min_image(xcur[2 * j + 1] - xprev[2 * j + 1], L[1]) / dt;
+    }
+}
+
+/* Velocity correlation between two samples of the same particles (Sec. IV-A,
+ * Fig. VD(a)): per axis, the mean over particles of v_a(now) v_a(before). */
+void oracle_vacf(int64_t n, const double *vprev, const double *vcur, double *out)
+{
+    double sx = 0.0, sy = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        sx += vcur[2 * j] * vprev[2 * j];
+        sy += vcur[2 * j + 1] * vprev[2 * j + 1];
+    }
+    out[0] = n ? sx / (double)n : 0.0;
+    out[1] = n ? sy / (double)n : 0.0;
+}

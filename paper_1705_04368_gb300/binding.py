@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
                 ("lag_steps", ctypes.c_int32 * MAX_LAGS), ("vmax", ctypes.c_int32),
                 ("site_mode", ctypes.c_int32), ("stats_every", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("lattice_u", ctypes.c_double * 2),
-                ("msd", ctypes.c_int32)]
+                ("msd", ctypes.c_int32), ("vacf", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -58,7 +58,8 @@ class _Stats(ctypes.Structure):
                 ("temperature", ctypes.c_double), ("pressure", ctypes.c_double),
                 ("intervals", ctypes.c_int64 * MAX_LAGS), ("status", ctypes.c_int32),
                 ("msd", (ctypes.c_double * 2) * MAX_LAGS), ("lattice_u", ctypes.c_double * 2),
-                ("stale_steps", ctypes.c_int64), ("sort_every", ctypes.c_int32)]
+                ("stale_steps", ctypes.c_int64), ("sort_every", ctypes.c_int32),
+                ("vacf", (ctypes.c_double * 2) * MAX_LAGS)]
 
 
 class _Lattice(ctypes.Structure):
@@ -195,6 +196,7 @@ class Params:
     use_graphs: bool = False
     lattice_u: tuple = (0.0, 0.0)
     msd: bool = False
+    vacf: bool = False
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -219,6 +221,7 @@ class Params:
         p.use_graphs = int(bool(self.use_graphs))
         p.lattice_u[0], p.lattice_u[1] = float(self.lattice_u[0]), float(self.lattice_u[1])
         p.msd = int(bool(self.msd))
+        p.vacf = int(bool(self.vacf))
         return p
 
     @property
@@ -269,6 +272,7 @@ class Simulation:
         d["momentum"] = (out.momentum[0], out.momentum[1])
         d["intervals"] = [out.intervals[i] for i in range(nl)]
         d["msd"] = [(out.msd[i][0], out.msd[i][1]) for i in range(nl)]
+        d["vacf"] = [(out.vacf[i][0], out.vacf[i][1]) for i in range(nl)]
         d["lattice_u"] = (out.lattice_u[0], out.lattice_u[1])
         return d, counts, fi
 

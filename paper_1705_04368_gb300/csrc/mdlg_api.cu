@@ -44,6 +44,8 @@ struct mdlg_ctx {
     uint32_t *lprev[2][kMaxLags]{};
     float2 *mprev[2][kMaxLags]{};  // mean-square displacement origins (params.msd)
     double *msd_acc = nullptr;     // nlags x 2
+    float2 *vprev[2][kMaxLags]{};  // velocity-correlation origins (params.vacf)
+    double *vacf_acc = nullptr;    // nlags x 2
     int pos_cur = 0, meta_cur = 0;
     int32_t *cell_start = nullptr;
     // scratch
@@ -213,6 +215,7 @@ int validate(const mdlg_params *p) {
     if ((p->site_mode & MDLG_SITES_FIELD) && (p->site_mode & MDLG_SITES_ACCUM)) return MDLG_EINVAL;
     if ((p->site_mode & MDLG_SITES_XI) && !(p->site_mode & MDLG_SITES_FIELD)) return MDLG_EINVAL;
     if (p->msd != 0 && p->msd != 1) return MDLG_EINVAL;
+    if (p->vacf != 0 && p->vacf != 1) return MDLG_EINVAL;
     for (int a = 0; a < 2; ++a)   // per-step shift below 2^16 base cells
         if (!std::isfinite(p->lattice_u[a]) || std::fabs(p->lattice_u[a] * p->dt) >= 65536.0 * p->grid)
             return MDLG_EINVAL;
@@ -327,6 +330,11 @@ StateBinArgs bin_args(mdlg_ctx *c, uint32_t mask) {
         for (int l = 0; l < c->p.nlags; ++l) b.mprev[l] = c->mprev[c->meta_cur][l];
         b.msd_acc = c->msd_acc;
     }
+    b.vel = c->vel[c->pos_cur];
+    if (c->p.vacf) {
+        for (int l = 0; l < c->p.nlags; ++l) b.vprev[l] = c->vprev[c->meta_cur][l];
+        b.vacf_acc = c->vacf_acc;
+    }
     return b;
 }
 
@@ -405,6 +413,10 @@ int do_sort(mdlg_ctx *c, bool launch = true) {
         if (c->p.msd) {
             s.mprev_in[l] = c->mprev[mi][l];
             s.mprev_out[l] = c->mprev[mi ^ 1][l];
+        }
+        if (c->p.vacf) {
+            s.vprev_in[l] = c->vprev[mi][l];
+            s.vprev_out[l] = c->vprev[mi ^ 1][l];
         }
     }
     s.cell_start = c->cell_start;
@@ -518,7 +530,7 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
     if (nsys > 0) {
         if (!ns || !boxes || nsys > 65535) return MDLG_EINVAL;
         // per-site outputs, the moving lattice and the displacement sums: single systems only
-        if (params->site_mode || params->msd || params->lattice_u[0] != 0.0 ||
+        if (params->site_mode || params->msd || params->vacf || params->lattice_u[0] != 0.0 ||
             params->lattice_u[1] != 0.0)
             return MDLG_EINVAL;
         ntot = 0;
@@ -616,9 +628,11 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         for (int l = 0; l < p.nlags; ++l) {
             if ((rc = alloc_n(c, &c->lprev[b][l], N))) return fail(rc);
             if (p.msd && (rc = alloc_n(c, &c->mprev[b][l], N))) return fail(rc);
+            if (p.vacf && (rc = alloc_n(c, &c->vprev[b][l], N))) return fail(rc);
         }
     }
     if (p.msd && (rc = alloc_n(c, &c->msd_acc, (size_t)2 * p.nlags))) return fail(rc);
+    if (p.vacf && (rc = alloc_n(c, &c->vacf_acc, (size_t)2 * p.nlags))) return fail(rc);
     const int64_t nb = sort_scratch_blocks(c->ncells);
     if ((rc = alloc_n(c, &c->cell_start, (size_t)c->ncells + 1)) ||
         (rc = alloc_n(c, &c->key, N)) || (rc = alloc_n(c, &c->slot, N)) ||
@@ -681,6 +695,8 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
             return fail(rc);
     }
     if (p.msd && (rc = chk(cudaMemsetAsync(c->msd_acc, 0, sizeof(double) * 2 * p.nlags, s))))
+        return fail(rc);
+    if (p.vacf && (rc = chk(cudaMemsetAsync(c->vacf_acc, 0, sizeof(double) * 2 * p.nlags, s))))
         return fail(rc);
     if (nsys > 0) {
         std::vector<uint16_t> cs(N / kChunk);
@@ -1013,6 +1029,17 @@ int stats_impl(mdlg_ctx *c, int32_t k, mdlg_stats_out *out, uint64_t *counts, do
                 out->msd[l][a] = denom > 0 ? h[2 * l + a] / denom : 0.0;
             }
     }
+    if (p.vacf) {
+        double h[2 * kMaxLags];
+        MDLG_TRY(cuda_err(cudaMemcpyAsync(h, c->vacf_acc, sizeof(double) * 2 * p.nlags,
+                                          cudaMemcpyDeviceToHost, c->stream)));
+        MDLG_TRY(cuda_err(cudaStreamSynchronize(c->stream)));
+        for (int l = 0; l < p.nlags; ++l)
+            for (int a = 0; a < 2; ++a) {
+                const double denom = (double)n * (double)c->intervals[l];
+                out->vacf[l][a] = denom > 0 ? h[2 * l + a] / denom : 0.0;
+            }
+    }
     if (counts || fi) {
         const int32_t nsb = c->nsys > 0 ? c->nsys : 1;
         std::vector<unsigned long long> h((size_t)nsb * p.nlags * c->q1);
@@ -1113,6 +1140,8 @@ int mdlg_reset_counts(mdlg_ctx *c) {
     }
     if (c->msd_acc)
         MDLG_TRY(cuda_err(cudaMemsetAsync(c->msd_acc, 0, sizeof(double) * 2 * c->p.nlags, c->stream)));
+    if (c->vacf_acc)
+        MDLG_TRY(cuda_err(cudaMemsetAsync(c->vacf_acc, 0, sizeof(double) * 2 * c->p.nlags, c->stream)));
     for (int l = 0; l < kMaxLags; ++l) c->intervals[l] = 0;
     return MDLG_OK;
 }
@@ -1430,7 +1459,7 @@ uint64_t shape_hash(const mdlg_ctx *c) {
     h = mix(h, p.dt); h = mix(h, p.grid); h = mix(h, p.skin); h = mix(h, p.dx);
     h = mix(h, p.nlags);
     for (int l = 0; l < p.nlags; ++l) h = mix(h, p.lag_steps[l]);
-    h = mix(h, p.vmax); h = mix(h, p.site_mode); h = mix(h, p.msd);
+    h = mix(h, p.vmax); h = mix(h, p.site_mode); h = mix(h, p.msd); h = mix(h, p.vacf);
     h = mix(h, p.lattice_u[0]); h = mix(h, p.lattice_u[1]);
     h = mix(h, p.sort_every); h = mix(h, c->adaptive); h = mix(h, c->slots); h = mix(h, c->ncells);
     h = mix(h, c->cap);
@@ -1452,6 +1481,10 @@ std::vector<Region> ckpt_regions(mdlg_ctx *c) {
     if (c->p.msd) {
         for (int l = 0; l < nl; ++l) r.push_back({c->mprev[mc][l], N * sizeof(float2)});
         r.push_back({c->msd_acc, 2 * nl * sizeof(double)});
+    }
+    if (c->p.vacf) {
+        for (int l = 0; l < nl; ++l) r.push_back({c->vprev[mc][l], N * sizeof(float2)});
+        r.push_back({c->vacf_acc, 2 * nl * sizeof(double)});
     }
     r.push_back({c->cell_start, ((size_t)c->ncells + 1) * sizeof(int32_t)});
     if (c->nbr) {

@@ -249,9 +249,11 @@ __device__ __forceinline__ int32_t state_base(const Geom &geo, const LatticeShif
 
 // Binning of the simulation state (sorted by MD cell) for the lags in `mask`:
 // the lattice cell now versus the one stored at the lag's previous binning,
-// which is then replaced.  Lag 0 may also write per-site outputs; with
-// msd_acc set every binned lag also adds the squared displacement since its
-// previous binning.  Every load of an iteration is issued before any of its
+// which is then replaced.  Lag 0 may also write per-site outputs.  The MSD
+// instantiation carries the optional per-lag sums, each on when its
+// accumulator is set: with msd_acc every binned lag also adds the squared
+// displacement since its previous binning, with vacf_acc the product of the
+// velocity now and the one stored at that binning (Sec. IV-A).  Every load of an iteration is issued before any of its
 // stores (a store followed by a load the compiler cannot prove independent
 // stalls the thread), and the lag loop is unrolled over the compile-time
 // maximum, predicated by the mask.
@@ -262,24 +264,27 @@ __global__ void k_bin_state(StateBinArgs sa) {
     const Geom &geo = sa.geo;
     const int w = 2 * geo.vmax + 1, q1 = w * w + 1;
     const int center = geo.vmax * w + geo.vmax;
-    constexpr bool msd = MSD;
+    const bool msd = MSD && sa.msd_acc != nullptr;
+    const bool vc = MSD && sa.vacf_acc != nullptr;
     for (int b = threadIdx.x; b < q1 * kMaxLags; b += blockDim.x) sh[b] = 0;
     __syncthreads();
-    float m2[kMaxLags][2];
+    float m2[kMaxLags][2], c2[kMaxLags][2];
 #pragma unroll
-    for (int l = 0; l < kMaxLags; ++l) m2[l][0] = m2[l][1] = 0.0f;
+    for (int l = 0; l < kMaxLags; ++l) m2[l][0] = m2[l][1] = c2[l][0] = c2[l][1] = 0.0f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < sa.n; base += stride) {
         const int64_t j = base + threadIdx.x;
         const bool act = j < sa.n;
         uint32_t before[kMaxLags];
-        float2 mp[kMaxLags];
+        float2 mp[kMaxLags], vp[kMaxLags];
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l) {
             const bool on = act && ((sa.mask >> l) & 1u);
             before[l] = on ? sa.lprev[l][j] : 0u;
             mp[l] = (on && msd) ? sa.mprev[l][j] : make_float2(0.f, 0.f);
+            vp[l] = (on && vc) ? sa.vprev[l][j] : make_float2(0.f, 0.f);
         }
+        const float2 vel = (act && vc) ? sa.vel[j] : make_float2(0.f, 0.f);
         int32_t lx = 0, ly = 0;
         float2 p = make_float2(0.f, 0.f);
         if (act) {
@@ -311,6 +316,11 @@ __global__ void k_bin_state(StateBinArgs sa) {
                     m2[l][1] += ddy * ddy;
                     sa.mprev[l][j] = p;
                 }
+                if (vc) {
+                    c2[l][0] = fmaf(vel.x, vp[l].x, c2[l][0]);
+                    c2[l][1] = fmaf(vel.y, vp[l].y, c2[l][1]);
+                    sa.vprev[l][j] = vel;
+                }
                 if (l == 0 && sa.site_n) {
                     const int64_t site = (int64_t)ly * geo.lat[0] + lx;
                     atomicAdd(&sa.site_n[site], 1u);
@@ -330,6 +340,14 @@ __global__ void k_bin_state(StateBinArgs sa) {
             if ((sa.mask >> l) & 1u) {
                 block_sum_add(m2[l][0], red, sa.msd_acc + 2 * l);
                 block_sum_add(m2[l][1], red, sa.msd_acc + 2 * l + 1);
+            }
+    }
+    if (vc) {
+#pragma unroll
+        for (int l = 0; l < kMaxLags; ++l)
+            if ((sa.mask >> l) & 1u) {
+                block_sum_add(c2[l][0], red, sa.vacf_acc + 2 * l);
+                block_sum_add(c2[l][1], red, sa.vacf_acc + 2 * l + 1);
             }
     }
 }
@@ -491,7 +509,8 @@ __global__ void __launch_bounds__(kChunk) k_bin_state_batch(StateBinArgs sa) {
     }
 }
 
-// Lattice cell of every particle, stored as the starting point of every lag.
+// Lattice cell of every particle, stored as the starting point of every lag
+// (with the position and velocity origins of the optional sums).
 template <bool B>
 __global__ void k_bin_seed(StateBinArgs sa) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -510,6 +529,7 @@ __global__ void k_bin_seed(StateBinArgs sa) {
             if ((sa.mask >> l) & 1u) {
                 sa.lprev[l][j] = now;
                 if (sa.msd_acc) sa.mprev[l][j] = p;
+                if (sa.vacf_acc) sa.vprev[l][j] = sa.vel[j];
             }
     }
 }
@@ -785,7 +805,7 @@ cudaError_t launch_bin_state(const StateBinArgs &sa, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int threads = 256;
-    const bool msd = sa.msd_acc != nullptr, move = sa.shift.on != 0;
+    const bool msd = sa.msd_acc != nullptr || sa.vacf_acc != nullptr, move = sa.shift.on != 0;
     if (!msd && !move) {
         const int K = __builtin_popcount(sa.mask);
         void (*kv)(StateBinArgs) = nullptr;

@@ -111,6 +111,9 @@ struct StateBinArgs {
     float2 *mprev[kMaxLags];  // per lag: offset at its previous binning, against the
                               // particle's current MD cell (mean-square displacement), or null
     double *msd_acc;        // nlags x 2 sums of squared displacements (added to)
+    const float2 *vel;        // half-step velocities of the binned state
+    float2 *vprev[kMaxLags];  // per lag: velocity at its previous binning (correlation), or null
+    double *vacf_acc;         // nlags x 2 sums of velocity products (added to), or null
 };
 
 struct CollArgs {
@@ -211,6 +214,8 @@ struct SortArgs {
     uint32_t *lprev_out[kMaxLags];
     const float2 *mprev_in[kMaxLags];   // mean-square displacement origins, or null
     float2 *mprev_out[kMaxLags];
+    const float2 *vprev_in[kMaxLags];   // velocity-correlation origins, or null
+    float2 *vprev_out[kMaxLags];
     int32_t *cell_start;     // ncells + 1
     // scratch
     uint32_t *key;           // n, packed new cell

@@ -656,14 +656,19 @@ __global__ void __launch_bounds__(256, MSD ? 4 : 8) k_sort_scatter(SortArgs a) {
         const float2 p = a.cl_in[from];
         const float2 vv = a.v_in[from];
         const int32_t pid = a.pid_in[from];
-        // MSD (a compile-time choice): the offsets at each lag's last binning
-        // move too, so without it they take no registers
+        // MSD (a compile-time choice): the offsets and velocities at each lag's
+        // last binning (mean-square displacement, velocity correlation; each
+        // when its arrays are set) move too, so without it they take no registers
+        const bool mo = MSD && a.mprev_in[0] != nullptr, vo = MSD && a.vprev_in[0] != nullptr;
         uint32_t lp[kMaxLags];
-        float2 mp[MSD ? kMaxLags : 1];
+        float2 mp[MSD ? kMaxLags : 1], vp[MSD ? kMaxLags : 1];
 #pragma unroll
         for (int l = 0; l < kMaxLags; ++l) {
             lp[l] = l < a.nlags ? a.lprev_in[l][from] : 0u;
-            if (MSD) mp[l] = l < a.nlags ? a.mprev_in[l][from] : make_float2(0.f, 0.f);
+            if (MSD) {
+                mp[l] = (mo && l < a.nlags) ? a.mprev_in[l][from] : make_float2(0.f, 0.f);
+                vp[l] = (vo && l < a.nlags) ? a.vprev_in[l][from] : make_float2(0.f, 0.f);
+            }
         }
         const int64_t c = key_cell<B>(sv, cw);
         const int32_t s = a.cell_start[c], e = a.cell_start[c + 1];
@@ -685,7 +690,8 @@ __global__ void __launch_bounds__(256, MSD ? 4 : 8) k_sort_scatter(SortArgs a) {
         for (int l = 0; l < kMaxLags; ++l)
             if (l < a.nlags) {
                 a.lprev_out[l][to] = lp[l];
-                if (MSD) a.mprev_out[l][to] = make_float2(mp[l].x + sx, mp[l].y + sy);
+                if (MSD && mo) a.mprev_out[l][to] = make_float2(mp[l].x + sx, mp[l].y + sy);
+                if (MSD && vo) a.vprev_out[l][to] = vp[l];
             }
     }
 }
@@ -997,7 +1003,7 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
     k_sort_place<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
-    if (a.mprev_in[0]) k_sort_scatter<B, true><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
+    if (a.mprev_in[0] || a.vprev_in[0]) k_sort_scatter<B, true><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     else k_sort_scatter<B, false><<<grid_for(a.n, t, 16), t, 0, s>>>(a);
     if (a.nbr) {
         const int nt = (size_t)kNlistThreads * (a.cap + 1) * sizeof(uint32_t) <= 96 * 1024 ? kNlistThreads : 64;

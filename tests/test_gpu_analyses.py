@@ -1,6 +1,6 @@
 """GPU parity of the paper analyses against the FP64 oracle: the moving lattice
-(Sec. IV), the MDLG collision operator Xi_i (Eq. Xi) and the per-lag
-mean-square displacement (Sec. IV-A).
+(Sec. IV), the MDLG collision operator Xi_i (Eq. Xi), the per-lag mean-square
+displacement and velocity correlation (Sec. IV-A).
 
 Tolerances: every count, Xi value and per-site sum bit-exact on identical
 snapshots; the mean-square displacement within 1e-4 relative (per-particle
@@ -285,6 +285,59 @@ def test_msd_free_flight_exact_value(cuda):
         want = ((v0 * lag * dt) ** 2).mean(axis=0)
         assert np.allclose(st["msd"][li], want, rtol=1e-6, atol=0)
         assert np.allclose(st2["msd"][li], want, rtol=1e-6, atol=0)   # after a reset
+
+
+def test_vacf_matches_oracle_lj(cuda):
+    # Velocity correlation of every lag (Sec. IV-A, Fig. VD(a)) against the
+    # oracle on the engine's own snapshots: the half-step velocity of the step
+    # ending at t is the displacement over dt, v_{-1/2} = v_0 - F(x_0) dt / 2 at
+    # t = 0; re-sorts every 3 steps move the stored velocities with their
+    # particles.  The engine multiplies its binary32 velocities, the oracle the
+    # FP64 displacements of the stored positions over dt (which differ by the
+    # rounding of one position update, ~1e-7 sigma / dt).
+    n, L = 20000, mi.box_for(20000, 0.3, 4.0)
+    x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=20, quantum=2.0 ** -20)
+    lags, steps = (1, 4, 10), 40
+    p = m.Params(n=n, box=L, dx=4.0, lag_steps=lags, vmax=V, msd=True, vacf=True, sort_every=3)
+    traj = []
+    with m.Simulation(p, x0, v0) as s:
+        traj.append(s.get_state()[0])
+        for _ in range(steps):
+            s.step(1)
+            traj.append(s.get_state()[0])
+        st, _, _ = s.stats()
+    vh = [oracle.initial_half_velocity(traj[0], v0, (L, L), p.dt)]
+    vh += [oracle.half_velocity(traj[t - 1], traj[t], (L, L), p.dt) for t in range(1, steps + 1)]
+    for li, lag in enumerate(lags):
+        ref = np.mean([oracle.vacf(vh[t - lag], vh[t]) for t in range(lag, steps + 1, lag)], axis=0)
+        assert np.allclose(st["vacf"][li], ref, rtol=1e-3, atol=0), (lag, st["vacf"][li], ref)
+        # the mean-square displacement of the same run is unchanged by the second sum
+        mref = np.mean([oracle.msd(traj[t - lag], traj[t], (L, L))
+                        for t in range(lag, steps + 1, lag)], axis=0)
+        assert np.allclose(st["msd"][li], mref, rtol=1e-4, atol=0)
+
+
+def test_vacf_free_flight_value(cuda):
+    # no forces, dyadic velocities: every half-step velocity is v_0, so every
+    # lag's correlation is <v_a^2> (to binary32 summation), also after a reset
+    n, L, dt = 30000, 64.0, 0.125
+    x0, _ = _dyadic_free_flight(n, L, seed=82)
+    rng = np.random.default_rng(83)
+    v0 = np.round(rng.normal(0.0, 1.5, size=(n, 2)) * 256) / 256
+    lags = (2, 5)
+    p = m.Params(n=n, box=L, dx=4.0, dt=dt, potential=m.POT_NONE, lag_steps=lags, sort_every=3,
+                 vmax=V, vacf=True)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(20)
+        st, _, _ = s.stats()
+        s.reset_counts()
+        s.step(10)
+        st2, _, _ = s.stats()
+    want = (v0 ** 2).mean(axis=0)
+    for li in range(len(lags)):
+        assert np.allclose(st["vacf"][li], want, rtol=1e-6, atol=0)
+        assert np.allclose(st2["vacf"][li], want, rtol=1e-6, atol=0)
+        assert st["msd"][li] == (0.0, 0.0)                              # msd off
 
 
 def test_moving_lattice_equilibrium_and_moments(cuda):

@@ -15,7 +15,8 @@ def _record(s, xi=False):
     x, v = s.get_state()
     st, counts, fi = s.stats()
     out = {"x": x, "v": v, "counts": counts, "ke": st["kinetic"], "pe": st["potential"],
-           "step": st["step"], "intervals": st["intervals"], "msd": np.array(st["msd"])}
+           "step": st["step"], "intervals": st["intervals"], "msd": np.array(st["msd"]),
+           "vacf": np.array(st["vacf"])}
     if xi:
         out["xi"] = s.get_collision()[0]
         out["sites"] = s.get_sites()[0]
@@ -24,7 +25,7 @@ def _record(s, xi=False):
 
 def _same(a, b, msd_exact=True):
     for k in a:
-        if k == "msd" and not msd_exact:
+        if k in ("msd", "vacf") and not msd_exact:
             assert np.allclose(a[k], b[k], rtol=1e-12), k      # FP64 atomic sums
         elif isinstance(a[k], np.ndarray):
             assert np.array_equal(a[k], b[k]), k
@@ -37,6 +38,7 @@ def test_resume_single_system_bit_identical(cuda):
     x0, v0 = mi.lj_initial_state(n, L, 1.0, seed=31)
     x1, v1 = mi.lj_initial_state(n, L, 1.0, seed=32)
     p = m.Params(n=n, box=L, dx=4.0, lag_steps=(3, 7, 50), sort_every=5, stats_every=10, msd=True,
+                 vacf=True,
                  site_mode=m.SITES_FIELD | m.SITES_XI, lattice_u=(0.2, -0.1))
     with m.Simulation(p, x0, v0) as ref:
         ref.step(2000)

@@ -6,7 +6,8 @@ with it).  Checked against what the paper states and the closed forms:
 
   * energy conservation of the integrator;
   * the mean-square displacement follows Eq. vca with an exponential velocity
-    correlation of decay time tau ~ 0.5 (Fig. VD: tau = 0.5);
+    correlation of decay time tau ~ 0.5 (Fig. VD: tau = 0.5), and the velocity
+    correlation measured in the same run decays with that tau (Fig. VD(a));
   * f_i of Eq. MDni matches Eq. feqfull at a^2 = <dx^2>/dx^2 measured in the
     same run (Fig. fi), for coarse steps from the ballistic to the diffusive
     regime;
@@ -36,7 +37,7 @@ U_LATTICE = 0.1         # imposed velocity in lattice units at that step
 def _run(lattice_u):
     x0, v0 = mi.lj_initial_state(C.n, C.box, C.temperature, seed=5)
     p = m.Params(n=C.n, box=C.box, dx=C.dx, dt=C.dt, lag_steps=C.lags, vmax=C.vmax, msd=True,
-                 stats_every=10000, lattice_u=lattice_u)
+                 vacf=True, stats_every=10000, lattice_u=lattice_u)
     with m.Simulation(p, x0, v0) as s:
         st0, _, _ = s.stats()
         s.step(DISCARD)
@@ -72,6 +73,25 @@ def test_msd_follows_exponential_vacf_with_tau_one_half(rest):
     assert 0.45 < tau < 0.55, tau
     model = np.array([cf.msd_exponential_vacf(T, 0.5, ti) for ti in t])
     assert np.all(np.abs(msd / model - 1.0) < 0.03), msd / model
+
+
+def test_vacf_decays_exponentially_with_tau_one_half(rest):
+    # Fig. VD(a): the measured velocity correlation against k_B T exp(-t/tau)
+    # at the early lags (t <= 0.7 tau, before the two-dimensional long-time
+    # tail): the decay time fitted there is ~0.5, and the shortest lag's value is
+    # the temperature times exp(-t/0.5) within 3 %
+    _, st, _, _ = rest
+    T = st["temperature"]
+    t = np.array(C.lags) * C.dt
+    c = np.array([0.5 * (a + b) for a, b in st["vacf"]])
+    early = t <= 0.7 + 1e-12
+    taus = np.linspace(0.1, 1.5, 1401)
+    err = [np.sum((np.log(c[early]) - np.log(T) + t[early] / tau) ** 2) for tau in taus]
+    tau = float(taus[int(np.argmin(err))])
+    assert 0.45 < tau < 0.55, (tau, c / T)
+    assert c[0] / (T * math.exp(-t[0] / 0.5)) == pytest.approx(1.0, abs=0.03)
+    # later lags: well below the early values, and no larger than T
+    assert np.all(c[~early] < 0.2 * T)
 
 
 def test_fi_matches_closed_form_at_measured_width(rest):

@@ -641,7 +641,8 @@ def _analyses(m, torch, dev, stream, local_rank, params, c, x0, v0, hbm_gbs, pla
     """(1) mdlg_collision on the production lattice (935 x 935 sites, V = 3) with
     random fields, algorithmic bytes 12 Q + 12 per site; (2) the production run
     (200 MD steps per step) with lattice drift U = (0.3, 0.1), the Xi field of
-    lag 0 and the mean-square displacement of every lag, against the plain run."""
+    lag 0, and the mean-square displacement and velocity correlation of every
+    lag, against the plain run."""
     import dataclasses
     C = (int(round(c.box / c.dx)),) * 2
     q = 49
@@ -667,7 +668,7 @@ def _analyses(m, torch, dev, stream, local_rank, params, c, x0, v0, hbm_gbs, pla
     coll_bytes = sites * (COLLISION_BYTES_PER_SITE_Q * q + COLLISION_BYTES_PER_SITE)
     del fields, xi, dm, dj
 
-    p = dataclasses.replace(params, lattice_u=(0.3, 0.1), msd=True,
+    p = dataclasses.replace(params, lattice_u=(0.3, 0.1), msd=True, vacf=True,
                             site_mode=m.SITES_FIELD | m.SITES_XI)
     with m.Simulation(p, x0, v0, stream=stream, device=local_rank) as s:
         s.step(MD_STEPS_PER_STEP)
@@ -691,7 +692,8 @@ def _analyses(m, torch, dev, stream, local_rank, params, c, x0, v0, hbm_gbs, pla
                 "particle_steps_per_s": on_value, "plain_particle_steps_per_s": plain_value,
                 "overhead": plain_value / on_value - 1.0,
                 "bin_ms_per_200_steps": prof["bin"][0] / 3, "bin_launches": prof["bin"][1],
-                "what": "moving lattice + SITES_FIELD|SITES_XI + msd, graphs off (both arms)"}}
+                "vacf_lag0": st["vacf"][0],
+                "what": "moving lattice + SITES_FIELD|SITES_XI + msd + vacf, graphs off (both arms)"}}
 
 
 def _e2e(m, torch, params, c, x0, v0, stream, local_rank, args, world, dist, dev):
@@ -753,7 +755,9 @@ def run_state_point(total: int, discard: int):
     first `discard` are dropped (the paper: 3e6 and 1e6).  Lattice dx = 100 sigma,
     coarse step dt_LG = 34.16 tau (341 600 MD steps), imposed lattice velocity u =
     0 ... 0.5 (lattice units) by moving the lattice; the MSD of six shorter lags
-    gives the decay time tau of Eq. vca.  Prints one JSON line: per u the
+    gives the decay time tau of Eq. vca, and their velocity correlation (u = 0)
+    gives it a second time, from T exp(-t/tau) at the lags up to 0.7 tau
+    (Fig. VD(a)).  Prints one JSON line: per u the
     measured f_i against Eq. feqfull (at the measured a^2) and against the D2Q9
     equilibrium of Eq. f0lb (theta = 1/3)."""
     import torch
@@ -769,7 +773,7 @@ def run_state_point(total: int, discard: int):
     for u in (0.0, 0.1, 0.2, 0.3, 0.4, 0.5):
         U = u * dx / (lag * c.dt)
         p = m.Params(n=c.n, box=c.box, dx=dx, dt=c.dt, lag_steps=lags, vmax=c.vmax, msd=True,
-                     stats_every=10000, lattice_u=(U, 0.0))
+                     vacf=(u == 0.0), stats_every=10000, lattice_u=(U, 0.0))
         with m.Simulation(p, x0, v0) as s:
             s.step(discard)
             s.reset_counts()
@@ -785,6 +789,13 @@ def run_state_point(total: int, discard: int):
                        for t, mm in zip(ts, msd)) for tau in grid]
             out["tau_fit"] = float(grid[int(np.argmin(err))])
             out["temperature"] = T
+            # Fig. VD(a): the velocity correlation per lag, and the decay time of
+            # T exp(-t/tau) fitted to the lags up to 0.7 tau
+            vc = [0.5 * (a + b) for a, b in st["vacf"][:-1]]
+            out["vacf_over_T"] = {f"{t:g}": cv / T for t, cv in zip(ts, vc)}
+            early = [(t, cv) for t, cv in zip(ts, vc) if t <= 0.7 + 1e-12 and cv > 0]
+            err = [sum((math.log(cv / T) + t / tau) ** 2 for t, cv in early) for tau in grid]
+            out["tau_fit_vacf"] = float(grid[int(np.argmin(err))])
         ueff = st["lattice_u"][0] * lag * c.dt / dx
         a = math.sqrt(msd[-1]) / dx
         f = fi[-1]

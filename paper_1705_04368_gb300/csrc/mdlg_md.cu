@@ -25,10 +25,10 @@ namespace mdlg {
 namespace {
 
 constexpr int kStepThreads = 256;   // one system; a batch uses one 128-slot chunk per block
-// plain steps of one system: resident blocks per SM of the looping kernel (8 at
-// 32 registers fills an SM)
+// plain steps: resident blocks per SM of the looping kernels (at 32 registers,
+// 8 of 256 threads or 16 of one 128-slot chunk fill an SM)
 constexpr int kStepLoopBlocksPerSM = 8;
-constexpr bool kStepBatchLoop = true;   // plain steps of a batch loop over chunks too
+constexpr int kStepBatchBlocksPerSM = 16;
 constexpr int kListBatch = 4;       // list entries loaded before any is used (lists are
                                     // padded to a multiple of this)
 constexpr int kNlistThreads = 128;  // list-build block (entries staged in shared memory;
@@ -451,17 +451,18 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     step_epilogue<MODE, STATS, B>(a, sv.sys, D, vmax2, t);
 }
 
-// One system: 256-thread blocks, the register count left to the compiler.
+// One chunk of 256 slots per block: the statistics, initial and sync launches
+// of one system (the register count left to the compiler).
 template <int MODE, bool STATS, bool SF>
 __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     step_body<MODE, STATS, false, SF>(a);
 }
 
-// A batch: one 128-slot chunk per block, 16 blocks per SM (32 registers: the
-// per-chunk geometry would otherwise take the count to 40 and the occupancy
-// to 48 warps; 4 % faster for the 256-system batch).
+// The same launches of a batch: one 128-slot chunk per block, 16 blocks per
+// SM (32 registers: the per-chunk geometry would otherwise take the count to 40
+// and the occupancy to 48 warps; 4 % faster for the 256-system batch).
 template <int MODE, bool STATS, bool SF>
-__global__ void __launch_bounds__(kChunk, 16) k_step_batch(StepArgs a) {
+__global__ void __launch_bounds__(kChunk, kStepBatchBlocksPerSM) k_step_batch(StepArgs a) {
     step_body<MODE, STATS, true, SF>(a);
 }
 
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kChunk, 16) k_step_batch(StepArgs a) {
 // and the block epilogue (barriers, the launch ticket) runs once per block
 // instead of once per chunk.  Same arithmetic per slot as k_step.
 template <bool SF>
-__global__ void __launch_bounds__(kStepThreads, 8) k_step_loop(StepArgs a) {
+__global__ void __launch_bounds__(kStepThreads, kStepLoopBlocksPerSM) k_step_loop(StepArgs a) {
     __shared__ float2 s_tab[16];
     init_shift_table(a, s_tab);
     __syncthreads();
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_step_loop(StepArgs a) {
 // block and round, 16 resident blocks per SM), each chunk with its own
 // system's geometry.
 template <bool SF>
-__global__ void __launch_bounds__(kChunk, 16) k_step_batch_loop(StepArgs a) {
+__global__ void __launch_bounds__(kChunk, kStepBatchBlocksPerSM) k_step_batch_loop(StepArgs a) {
     __shared__ float2 s_tab[16];
     init_shift_table(a, s_tab);
     __syncthreads();
@@ -961,12 +962,10 @@ void launch_step_k(const StepArgs &a, dim3 grid, dim3 block, cudaStream_t s) {
 template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
     if (mode == kModeStep) {
+        // statistics steps one chunk per block; plain steps the looping kernels
         if (a.stats) launch_step_k<kModeStep, true, B, SF>(a, grid, block, s);
-        else if (!B && kStepLoopBlocksPerSM > 0)
-            k_step_loop<SF><<<grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM), block, 0, s>>>(a);
-        else if (B && kStepBatchLoop)
-            k_step_batch_loop<SF><<<grid_for(a.n, kChunk, 16), block, 0, s>>>(a);
-        else launch_step_k<kModeStep, false, B, SF>(a, grid, block, s);
+        else if (B) k_step_batch_loop<SF><<<grid_for(a.n, kChunk, kStepBatchBlocksPerSM), block, 0, s>>>(a);
+        else k_step_loop<SF><<<grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM), block, 0, s>>>(a);
     } else if (mode == kModeInit) {
         launch_step_k<kModeInit, true, B, SF>(a, grid, block, s);
     } else {

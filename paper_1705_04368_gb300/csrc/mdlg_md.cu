@@ -229,7 +229,7 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     const float w = a.cell_w;
     const int nb = (cnt + kListBatch - 1) / kListBatch;
     for (int b = 0; b < nb; ++b) {
-        const uint4 e4 = __ldg(e + (int64_t)b * n);
+        const uint4 e4 = __ldcs(e + (int64_t)b * n);
         const uint32_t ent[kListBatch] = {e4.x, e4.y, e4.z, e4.w};
         float2 q[kListBatch];
 #pragma unroll
@@ -294,16 +294,16 @@ template <int MODE, bool STATS, bool B, bool SF>
 __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, int64_t cell0,
                                            int64_t i, const float2 *s_tab, bool list_ok,
                                            float (&t)[kStatsN]) {
-    const uint32_t cw = i < a.n ? a.cell[i] : kGhostCell;
+    const uint32_t cw = i < a.n ? __ldcs(a.cell + i) : kGhostCell;
     const bool act = i < a.n && (!B || cw != kGhostCell);
     PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
     if (act) {
         p = a.cl_in[i];
-        v = a.v_in[i];
+        v = __ldcs(a.v_in + i);
         if (a.potential) {
             const int32_t cx = cell_x(cw), cy = cell_y(cw);
-            const int cnt = list_ok ? a.ncount[i] : a.cap + 1;
+            const int cnt = list_ok ? __ldcs(a.ncount + i) : a.cap + 1;
             if (cnt <= a.cap) {
                 // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
                 if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
@@ -336,7 +336,7 @@ __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, i
             vn = make_float2(fmaf(fx, a.half_dt_m, v.x), fmaf(fy, a.half_dt_m, v.y));
             const float2 vh = make_float2(fmaf(fx, a.dt_m, v.x), fmaf(fy, a.dt_m, v.y));
             const float2 pn = make_float2(fmaf(vh.x, a.dt, p.x), fmaf(vh.y, a.dt, p.y));
-            a.v_out[i] = vh;
+            __stcs(a.v_out + i, vh);
             a.cl_out[i] = pn;
             vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
             if (!(vmax2 < 3.0e38f) || !(fabsf(pn.x) < 3.0e38f) || !(fabsf(pn.y) < 3.0e38f))

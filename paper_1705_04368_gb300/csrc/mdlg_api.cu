@@ -362,15 +362,19 @@ int pace_decide(mdlg_ctx *c, bool *sort) {
     const int64_t s = t - kPaceLag;
     if (s < 0) return MDLG_OK;
     volatile PaceSlot *ps = c->pace + (s & (kPaceRing - 1));
+    // Busy-wait: only kPaceLag steps (a few hundred microseconds) are queued, so
+    // giving the core away (a yield can cost a scheduler quantum on a loaded
+    // host) would leave the device idle.  Only after ~2^20 polls, a wait far
+    // longer than a step, does the loop also yield.
     for (int64_t k = 1; ps->step != s; ++k) {
-        if (k % 64 == 0) {
+        if (k % 1024 == 0) {
             const cudaError_t q = cudaStreamQuery(c->stream);
             if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_err(q);
             // the stream is idle and the slot was never written (no step launch
             // for step s in this context): keep the interval rule
             if (q == cudaSuccess && ps->step != s) return MDLG_OK;
+            if (k >= (int64_t)1 << 20) std::this_thread::yield();
         }
-        std::this_thread::yield();
     }
     std::atomic_thread_fence(std::memory_order_acquire);
     const float D = ps->dbound;

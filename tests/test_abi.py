@@ -33,7 +33,7 @@ def test_strerror_names_every_code():
 
 
 def _params(**kw):
-    raw = {k: kw.pop(k) for k in ("msd",) if k in kw}     # set on the C struct unchecked
+    raw = {k: kw.pop(k) for k in ("msd", "vacf") if k in kw}   # set on the C struct unchecked
     base = dict(n=16, box=16.0, dx=4.0, grid=0.5, lag_steps=(5,))
     base.update(kw)
     p = m.Params(**base).to_c()
@@ -47,7 +47,8 @@ BAD = [
     dict(vmax=0), dict(vmax=16), dict(lag_steps=()), dict(lag_steps=(0,)), dict(dt=0.0),
     dict(rcut=9.0), dict(box=8.0, dx=4.0), dict(potential=7), dict(site_mode=3),
     dict(skin=-1.0), dict(sort_every=-2), dict(mass=0.0),
-    dict(site_mode=4), dict(site_mode=6), dict(msd=2), dict(lattice_u=(float("nan"), 0.0)),
+    dict(site_mode=4), dict(site_mode=6), dict(msd=2), dict(vacf=2),
+    dict(lattice_u=(float("nan"), 0.0)),
     dict(lattice_u=(0.0, 1e9)),
 ]
 
@@ -130,11 +131,12 @@ def test_context_free_entry_points_validate():
 
 
 def test_batch_rejects_single_system_analyses():
-    # the moving lattice, displacement sums and per-site outputs are single-system only
+    # the moving lattice, displacement and velocity sums and per-site outputs are
+    # single-system only
     x = np.full((32, 2), 1.0)
     ns = np.array([16, 16], np.int64)
     boxes = np.array([[16.0, 16.0], [16.0, 16.0]])
-    for kw in (dict(msd=1), dict(lattice_u=(0.5, 0.0)), dict(site_mode=1)):
+    for kw in (dict(msd=1), dict(vacf=1), dict(lattice_u=(0.5, 0.0)), dict(site_mode=1)):
         p = _params(**kw)
         h = ctypes.c_void_p()
         rc = m.lib().mdlg_create_batch(ctypes.byref(p), 2, ns.ctypes.data, boxes.ctypes.data,

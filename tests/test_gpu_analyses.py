@@ -340,6 +340,28 @@ def test_vacf_free_flight_value(cuda):
         assert st["msd"][li] == (0.0, 0.0)                              # msd off
 
 
+def test_msd_and_vacf_free_flight_at_full_size(cuda):
+    # the production particle count (N = 4 194 304) in free flight on dyadic
+    # values, re-sorted every 3 steps: the displacement and velocity sums of every
+    # lag take their exact values, (lag dt v)^2 and v^2 per axis, to binary32
+    # summation
+    n, L, dt = 4194304, 4096.0, 0.125
+    rng = np.random.default_rng(84)
+    x0 = mi.dyadic_positions(n, L, seed=85, bits=10)
+    v0 = np.round(rng.normal(0.0, 1.5, size=(n, 2)) * 256) / 256
+    lags = (2, 5)
+    p = m.Params(n=n, box=L, dx=4.0, dt=dt, potential=m.POT_NONE, lag_steps=lags, sort_every=3,
+                 vmax=V, msd=True, vacf=True)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(20)
+        st, counts, _ = s.stats()
+    assert st["status"] == 0
+    for li, lag in enumerate(lags):
+        assert np.allclose(st["msd"][li], ((v0 * lag * dt) ** 2).mean(axis=0), rtol=1e-5, atol=0)
+        assert np.allclose(st["vacf"][li], (v0 ** 2).mean(axis=0), rtol=1e-5, atol=0)
+        assert int(counts[li].sum()) == n * st["intervals"][li]
+
+
 def test_moving_lattice_equilibrium_and_moments(cuda):
     # Fig. wi_u (Sec. V): the ballistic gas seen from a lattice drifting at U has
     # the equilibrium of Eq. feqfull at u = U dt / dx; every bin within 4

@@ -73,6 +73,27 @@ def test_forces_full_size_sampled(cuda, record_property):
     _force_check(f[which], f_ref, scale, record=record_property)
 
 
+def test_forces_full_size_after_resorts_bench_geometry(cuda, record_property):
+    # The benchmark's configuration: N = 4 194 304, the tuned MD cells of 3.25
+    # sigma (grid 0.25, skin 0.75), the device-paced re-sorts.  After 40 steps
+    # (three or four re-sorts, each with a Verlet list built on cells ordered by
+    # base column) the forces the engine evaluates from its current list match
+    # the oracle's direct sums at the engine's own positions, on sampled particles.
+    c = mi.PRODUCTION_LJ
+    x0, v0 = mi.lj_initial_state(c.n, c.box, c.temperature, seed=3)
+    p = m.Params(n=c.n, box=c.box, dx=c.dx, lag_steps=c.lags, stats_every=100, grid=0.25,
+                 skin=0.75)
+    with m.Simulation(p, x0, v0) as s:
+        s.step(40)
+        x, _, f = s.get_state(want_force=True)
+        st, _, _ = s.stats()
+    assert st["status"] == 0 and st["stale_steps"] == 0
+    rng = np.random.default_rng(4)
+    which = np.concatenate([rng.choice(c.n, 200, replace=False), [0, c.n - 1]])
+    f_ref, scale = oracle.lj_forces_sample(x, (c.box, c.box), which)
+    _force_check(f[which], f_ref, scale, record=record_property)
+
+
 @pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3),
                                                (4096, 0.3, 1000)])
 def test_ten_step_trajectory(cuda, n, rho, sort_every):

@@ -73,8 +73,9 @@ extern "C" {
  */
 typedef struct {
     int32_t dim;          /* must be 2 (the paper's test case, Sec. IV)          */
-    int64_t n;            /* particles, >= 1 (at most 2^28 slots, counting a
-                             batch's padding, with a potential)                 */
+    int64_t n;            /* particles, >= 1 (below 2^28 with a potential, and
+                             for a batch its padded slot total too: Verlet-list
+                             entries hold slot numbers in 28 bits)              */
     double  box[2];       /* periodic box L_x, L_y; integer multiples of dx       */
     int32_t potential;    /* MDLG_POT_LJ_TS, MDLG_POT_LJ_SF or MDLG_POT_NONE      */
     double  eps, sigma;   /* Lennard-Jones energy and length (Sec. IV)            */

@@ -605,8 +605,6 @@ int create_impl(const mdlg_params *params, int32_t nsys, const int64_t *ns, cons
         c->ncells = cell;
     }
     if (c->ncells > (int64_t)4096 * 4096) return early(MDLG_EINVAL);
-    // Verlet-list entries hold slot numbers in 28 bits
-    if (p.potential != MDLG_POT_NONE && c->slots > ((int64_t)1 << 28)) return early(MDLG_EINVAL);
     c->ratio_shift = log2_exact(g.ratio);
     c->q1 = (2 * p.vmax + 1) * (2 * p.vmax + 1) + 1;
     for (int a = 0; a < 2; ++a) c->shift_m[a] = std::llround(p.lattice_u[a] * p.dt / p.grid * 16777216.0);

@@ -67,6 +67,31 @@ def test_create_rejects_bad_parameters(kw):
     assert rc == -1 and not h.value
 
 
+def test_create_limits_particles_to_what_list_entries_hold():
+    # Verlet-list entries hold slot numbers in 28 bits: with a potential, 2^28
+    # particles are rejected while the parameters are checked, before any device
+    # work and before the inputs are read (a one-particle buffer stands in for
+    # them); 2^28 - 1 passes the check (and fails only at allocation without a
+    # GPU, or is not tried with one), and without a potential 2^28 passes too
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the passing sizes would allocate and read a 4 GB input")
+    x = np.zeros((1, 2))
+
+    def rc_for(n, pot):
+        p = _params(n=n, box=12000.0, dx=4.0, grid=0.5, potential=pot)
+        h = ctypes.c_void_p()
+        rc = m.lib().mdlg_create(ctypes.byref(p), x.ctypes.data, x.ctypes.data, None, None,
+                                 ctypes.byref(h))
+        assert not h.value
+        return rc
+
+    for pot in (m.POT_LJ_TS, m.POT_LJ_SF):
+        assert rc_for(1 << 28, pot) == -1
+        assert rc_for((1 << 28) - 1, pot) != -1
+    assert rc_for(1 << 28, m.POT_NONE) != -1
+
+
 def test_create_rejects_null_state():
     p = _params()
     h = ctypes.c_void_p()

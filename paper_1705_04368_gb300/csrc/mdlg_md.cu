@@ -219,8 +219,11 @@ __device__ __forceinline__ void forces_cells(const StepArgs &a, const Geom &geo,
 // from a 16-entry shared-memory table indexed by the entry's four code bits;
 // at the periodic edges and next to the wider last cell they are selected
 // from the four per-particle shifts.  Entries are evaluated two at a time on
-// packed pairs (pair_terms2_masked).
-template <bool STATS, bool REGULAR, bool SF>
+// packed pairs (pair_terms2_masked).  IDX25: every slot number is below 2^25,
+// so bits 25-27 of an entry are zero and entry >> 25 is its code times 8, the
+// byte offset of the code's float2 in the table (one shift instead of a shift
+// and a scaling).
+template <bool STATS, bool REGULAR, bool SF, bool IDX25>
 __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2 p, int cnt,
                                             const float2 *tab, float sxm, float sxp, float sym,
                                             float syp, PairAcc &acc) {
@@ -238,7 +241,10 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
         float2 ns[kListBatch];
 #pragma unroll
         for (int u = 0; u < kListBatch; ++u) {
-            if (REGULAR) {
+            if (REGULAR && IDX25) {
+                ns[u] = *reinterpret_cast<const float2 *>(reinterpret_cast<const char *>(tab) +
+                                                          (ent[u] >> 25));
+            } else if (REGULAR) {
                 ns[u] = tab[ent[u] >> 28];
             } else {
                 const uint32_t ox = (ent[u] >> 28) & 3u, oy = ent[u] >> 30;
@@ -290,7 +296,8 @@ __device__ __forceinline__ bool list_current(const StepArgs &a, float D) {
 // One slot's force and update.  Returns |v|^2 of the new half-step velocity
 // (kModeStep) and, with STATS, the slot's fixed-point inputs t[] (kinetic
 // energy at the integer step, halved pair energy and virial, momentum).
-template <int MODE, bool STATS, bool B, bool SF>
+// IDX25: slot numbers below 2^25 (see forces_list).
+template <int MODE, bool STATS, bool B, bool SF, bool IDX25 = false>
 __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, int64_t cell0,
                                            int64_t i, const float2 *s_tab, bool list_ok,
                                            float (&t)[kStatsN]) {
@@ -307,13 +314,13 @@ __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, i
             if (cnt <= a.cap) {
                 // neighbouring cells of full width and no periodic wrap: shifts (code - 1) w
                 if (cx >= 1 && cx + 2 <= geo.nc[0] && cy >= 1 && cy + 2 <= geo.nc[1]) {
-                    forces_list<STATS, true, SF>(a, i, p, cnt, s_tab, 0.f, 0.f, 0.f, 0.f, acc);
+                    forces_list<STATS, true, SF, IDX25>(a, i, p, cnt, s_tab, 0.f, 0.f, 0.f, 0.f, acc);
                 } else {
                     const float sxm = cell_shift(cx, -1, geo.nc[0], geo.k, geo.lg[0], geo.g);
                     const float sxp = cell_shift(cx, +1, geo.nc[0], geo.k, geo.lg[0], geo.g);
                     const float sym = cell_shift(cy, -1, geo.nc[1], geo.k, geo.lg[1], geo.g);
                     const float syp = cell_shift(cy, +1, geo.nc[1], geo.k, geo.lg[1], geo.g);
-                    forces_list<STATS, false, SF>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
+                    forces_list<STATS, false, SF, IDX25>(a, i, p, cnt, s_tab, sxm, sxp, sym, syp, acc);
                 }
             } else {
                 // D re-read here (the bound only changes at the end of the launch)
@@ -470,8 +477,9 @@ __global__ void __launch_bounds__(kChunk, kStepBatchBlocksPerSM) k_step_batch(St
 // block taking the 256-slot chunks blockIdx, blockIdx + gridDim, ...  A warp
 // runs through its chunks without waiting for the other warps of its block,
 // and the block epilogue (barriers, the launch ticket) runs once per block
-// instead of once per chunk.  Same arithmetic per slot as k_step.
-template <bool SF>
+// instead of once per chunk.  Same arithmetic per slot as k_step.  IDX25: a
+// system of at most 2^25 slots (see forces_list).
+template <bool SF, bool IDX25>
 __global__ void __launch_bounds__(kStepThreads, kStepLoopBlocksPerSM) k_step_loop(StepArgs a) {
     __shared__ float2 s_tab[16];
     init_shift_table(a, s_tab);
@@ -484,15 +492,15 @@ __global__ void __launch_bounds__(kStepThreads, kStepLoopBlocksPerSM) k_step_loo
     // slot numbers fit 28 bits wherever lists are used (the entries' j field)
     const int32_t n = (int32_t)a.n, stride = (int32_t)gridDim.x * kStepThreads;
     for (int32_t i = (int32_t)blockIdx.x * kStepThreads + threadIdx.x; i < n; i += stride)
-        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, false, SF>(a, a.geo, 0, i, s_tab,
-                                                                   list_ok, t));
+        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, false, SF, IDX25>(a, a.geo, 0, i, s_tab,
+                                                                          list_ok, t));
     step_epilogue<kModeStep, false, false>(a, 0, D, vmax2, t);
 }
 
 // Plain steps of a batch: the same loop over 128-slot chunks (one chunk per
 // block and round, 16 resident blocks per SM), each chunk with its own
-// system's geometry.
-template <bool SF>
+// system's geometry.  IDX25: at most 2^25 slots in all.
+template <bool SF, bool IDX25>
 __global__ void __launch_bounds__(kChunk, kStepBatchBlocksPerSM) k_step_batch_loop(StepArgs a) {
     __shared__ float2 s_tab[16];
     init_shift_table(a, s_tab);
@@ -506,8 +514,8 @@ __global__ void __launch_bounds__(kChunk, kStepBatchBlocksPerSM) k_step_batch_lo
     const int32_t n = (int32_t)a.n, stride = (int32_t)gridDim.x * kChunk;
     for (int32_t i = (int32_t)blockIdx.x * kChunk + threadIdx.x; i < n; i += stride) {
         const SysView sv = sys_view<true>(a.geo, a.batch, i);
-        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, true, SF>(a, sv.geo, sv.cell0, i, s_tab,
-                                                                  list_ok, t));
+        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, true, SF, IDX25>(a, sv.geo, sv.cell0, i,
+                                                                         s_tab, list_ok, t));
     }
     step_epilogue<kModeStep, false, true>(a, 0, D, vmax2, t);
 }
@@ -719,6 +727,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
+        const int32_t i32 = (int32_t)i;   // slot numbers are below 2^28 wherever lists are built
         int cnt = 0;
         const uint32_t cw = i < a.n ? a.cell_out[i] : kGhostCell;
         if (i < a.n && B && cw == kGhostCell) a.ncount[i] = 0;
@@ -780,7 +789,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const bool g1 = j >= m1, g2 = j >= m2;   // in cell cx, cx + 1
                             const float odx = g2 ? sxp : (g1 ? 0.0f : sxm);
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            const bool hit = j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            const bool hit = j != i32 && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] =
                                 ((uint32_t)j | ycode) + (g1 ? (1u << 28) : 0u) + (g2 ? (1u << 28) : 0u);
                             cnt += hit;
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                         for (int u = 0; u < 4; ++u) {
                             const int32_t j = b + u;
                             const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
-                            const bool hit = j != i && fmaf(dx, dx, dy * dy) < a.rl2;
+                            const bool hit = j != i32 && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] = (uint32_t)j | code;
                             cnt += hit;
                         }
@@ -963,9 +972,15 @@ template <bool B, bool SF>
 void launch_step_t(const StepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s) {
     if (mode == kModeStep) {
         // statistics steps one chunk per block; plain steps the looping kernels
+        // (slot numbers below 2^25: the one-shift table index of forces_list)
+        const bool small = a.n <= ((int64_t)1 << 25);
+        const int gb = grid_for(a.n, kChunk, kStepBatchBlocksPerSM);
+        const int gs = grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM);
         if (a.stats) launch_step_k<kModeStep, true, B, SF>(a, grid, block, s);
-        else if (B) k_step_batch_loop<SF><<<grid_for(a.n, kChunk, kStepBatchBlocksPerSM), block, 0, s>>>(a);
-        else k_step_loop<SF><<<grid_for(a.n, kStepThreads, kStepLoopBlocksPerSM), block, 0, s>>>(a);
+        else if (B && small) k_step_batch_loop<SF, true><<<gb, block, 0, s>>>(a);
+        else if (B) k_step_batch_loop<SF, false><<<gb, block, 0, s>>>(a);
+        else if (small) k_step_loop<SF, true><<<gs, block, 0, s>>>(a);
+        else k_step_loop<SF, false><<<gs, block, 0, s>>>(a);
     } else if (mode == kModeInit) {
         launch_step_k<kModeInit, true, B, SF>(a, grid, block, s);
     } else {

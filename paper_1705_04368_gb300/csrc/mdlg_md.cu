@@ -230,7 +230,7 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     const uint4 *e = reinterpret_cast<const uint4 *>(a.nbr) + i;
     const int64_t n = a.n;
     const float w = a.cell_w;
-    const int nb = (cnt + kListBatch - 1) / kListBatch;
+    const int nb = (int)((uint32_t)(cnt + kListBatch - 1) / kListBatch);   // cnt >= 0
     for (int b = 0; b < nb; ++b) {
         const uint4 e4 = __ldcs(e + (int64_t)b * n);
         const uint32_t ent[kListBatch] = {e4.x, e4.y, e4.z, e4.w};
@@ -346,8 +346,10 @@ __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, i
             __stcs(a.v_out + i, vh);
             a.cl_out[i] = pn;
             vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
-            if (!(vmax2 < 3.0e38f) || !(fabsf(pn.x) < 3.0e38f) || !(fabsf(pn.y) < 3.0e38f))
-                set_status(a.ctl, kErrNonFinite);
+            // the input offset is finite (checked at upload, by this test at
+            // every earlier step, and re-expressed by finite shifts at each
+            // sort), so a finite |v|^2 below 3e38 also bounds the new offset
+            if (!(vmax2 < 3.0e38f)) set_status(a.ctl, kErrNonFinite);
         } else if (MODE == kModeInit) {
             vn = v;
             a.v_out[i] = make_float2(fmaf(-fx, a.half_dt_m, v.x), fmaf(-fy, a.half_dt_m, v.y));
@@ -748,17 +750,21 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                 const uint32_t ycode = (uint32_t)(oy + 1) << 30;
                 const int32_t row = ny * geo.nc[0];
                 if (interior) {
+                    // the particle's offset minus each column's origin shift and
+                    // the row's, formed once: one subtraction per axis and candidate
+                    const float pyr = p.y - ody, pxm = p.x - sxm, pxp = p.x - sxp;
                     // cells cx-1, cx, cx+1 of this row are one contiguous range
                     const int32_t s0 = __ldg(cs + row + cx - 1);
                     const int32_t m1 = __ldg(cs + row + cx);
                     const int32_t m2 = __ldg(cs + row + cx + 1);
                     const int32_t e0 = __ldg(cs + row + cx + 2);
                     // A candidate of cell cx-1 whose offset is below p.x, or of
-                    // cell cx+1 above it, lies a whole cell width (the list
-                    // radius) or more away along x: its rounded distance fails
-                    // the test below.  Cells are ordered by base column, so such
-                    // candidates lead cell cx-1 and trail cell cx+1; up to four
-                    // are dropped at each end of the range.
+                    // cell cx+1 above it, lies more than a whole cell width (the
+                    // list radius) away along x, so it cannot come within rc
+                    // before the displacement bound forces the next sort.  Cells
+                    // are ordered by base column, so such candidates lead cell
+                    // cx-1 and trail cell cx+1; up to four are dropped at each
+                    // end of the range.
                     int32_t s = s0, e = e0;
                     {
                         const float *clx = reinterpret_cast<const float *>(a.cl_out);
@@ -787,8 +793,8 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                         for (int u = 0; u < 2; ++u) {
                             const int32_t j = b + u;
                             const bool g1 = j >= m1, g2 = j >= m2;   // in cell cx, cx + 1
-                            const float odx = g2 ? sxp : (g1 ? 0.0f : sxm);
-                            const float dx = (p.x - q[u].x) - odx, dy = (p.y - q[u].y) - ody;
+                            const float pxs = g2 ? pxp : (g1 ? p.x : pxm);
+                            const float dx = pxs - q[u].x, dy = pyr - q[u].y;
                             const bool hit = j != i32 && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] =
                                 ((uint32_t)j | ycode) + (g1 ? (1u << 28) : 0u) + (g2 ? (1u << 28) : 0u);

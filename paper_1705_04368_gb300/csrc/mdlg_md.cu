@@ -751,8 +751,10 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                 const int32_t row = ny * geo.nc[0];
                 if (interior) {
                     // the particle's offset minus each column's origin shift and
-                    // the row's, formed once: one subtraction per axis and candidate
+                    // the row's, formed once: one subtraction per axis and
+                    // candidate; the entry codes of the three columns likewise
                     const float pyr = p.y - ody, pxm = p.x - sxm, pxp = p.x - sxp;
+                    const uint32_t codeM = ycode + (1u << 28), codeR = ycode + (2u << 28);
                     // cells cx-1, cx, cx+1 of this row are one contiguous range
                     const int32_t s0 = __ldg(cs + row + cx - 1);
                     const int32_t m1 = __ldg(cs + row + cx);
@@ -797,7 +799,7 @@ __global__ void __launch_bounds__(kNlistThreads) k_nlist(SortArgs a) {
                             const float dx = pxs - q[u].x, dy = pyr - q[u].y;
                             const bool hit = j != i32 && fmaf(dx, dx, dy * dy) < a.rl2;
                             s_ent[min(cnt, last) * nt + threadIdx.x] =
-                                ((uint32_t)j | ycode) + (g1 ? (1u << 28) : 0u) + (g2 ? (1u << 28) : 0u);
+                                (uint32_t)j + (g2 ? codeR : (g1 ? codeM : ycode));
                             cnt += hit;
                         }
                     }

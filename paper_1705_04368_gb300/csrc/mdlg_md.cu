@@ -1025,8 +1025,9 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
     k_scan_top<<<1, kScanThreads, 0, s>>>(a.block_sums, nb);
     k_sort_place<B><<<grid_for(a.n, t), t, 0, s>>>(a);
     k_cell_start<<<grid_for(a.ncells, t), t, 0, s>>>(a);
-    // scatter and list build: 64 blocks per SM in the grid (several rounds of
-    // resident blocks; uneven cells and lists balance better than with one)
+    // scatter and list build: 64 and 128 blocks per SM in the grid (several
+    // rounds of resident blocks; uneven cells and lists balance better than
+    // with one)
     if (a.mprev_in[0] || a.vprev_in[0]) k_sort_scatter<B, true><<<grid_for(a.n, t, 64), t, 0, s>>>(a);
     else k_sort_scatter<B, false><<<grid_for(a.n, t, 64), t, 0, s>>>(a);
     if (a.nbr) {
@@ -1037,7 +1038,7 @@ cudaError_t launch_sort_t(const SortArgs &a, cudaStream_t s) {
                                      (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_nlist<B><<<grid_for(a.n, nt, 64), nt, smem, s>>>(a);
+        k_nlist<B><<<grid_for(a.n, nt, 128), nt, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

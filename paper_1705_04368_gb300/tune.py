@@ -23,9 +23,10 @@ import numpy as np
 
 from .binding import Params, Simulation
 
-# (grid, skin) pairs giving MD cell widths (= list radii at rc = 2.5) of 2.75 ... 4.0
-DEFAULT_CANDIDATES = ((0.25, 0.25), (0.5, 0.5), (0.25, 0.75), (0.5, 1.0), (0.25, 1.25),
-                      (0.5, 1.5))
+# (grid, skin) pairs giving MD cell widths (= list radii at rc = 2.5) of 2.75 ... 4.0,
+# in steps of 0.25 and, on the 0.125 grid, 3.125 and 3.375 around the usual optimum
+DEFAULT_CANDIDATES = ((0.25, 0.25), (0.5, 0.5), (0.125, 0.625), (0.25, 0.75), (0.125, 0.875),
+                      (0.5, 1.0), (0.25, 1.25), (0.5, 1.5))
 
 
 def cache_path() -> str:

@@ -94,6 +94,54 @@ def test_forces_full_size_after_resorts_bench_geometry(cuda, record_property):
     _force_check(f[which], f_ref, scale, record=record_property)
 
 
+def test_tiled_system_past_2_25_slots_repeats_its_tile(cuda, record_property):
+    # A periodic gas of n0 particles in a box L0 that holds a whole number of MD
+    # cells (544 of 3.25 sigma) and of lattice cells (442 of 4 sigma), tiled 6 x 6:
+    # 36 n0 = 33 758 892 > 2^25 particles, so the plain steps take the general
+    # list-entry decode and every slot index of the sort, list and step kernels
+    # runs past 2^25.  Positions on multiples of 2^-20 make every copy's cell
+    # offsets identical, and particle numbers interleaved by copy (j * 36 + c)
+    # order each cell's particles as in the tile, so the lists, the forces and the
+    # device-paced re-sorts are the tile's: after 40 steps every copy equals the
+    # tile bit for bit, the exact FP64 sums and the MDLG counts are 36 times the
+    # tile's, and the forces match the oracle's direct sums on sampled particles.
+    L0, T = 1768.0, 6
+    n0 = int(round(0.3 * L0 * L0))
+    x0, v0 = mi.lj_initial_state(n0, L0, 1.0, seed=11, quantum=Q)
+    shifts = np.array([(a * L0, b * L0) for b in range(T) for a in range(T)])
+    nc = len(shifts)
+    X = (x0[:, None, :] + shifts[None, :, :]).reshape(-1, 2)    # particle j * 36 + c
+    V = np.repeat(v0, nc, axis=0)
+    assert X.shape[0] > (1 << 25)
+    kw = dict(dx=4.0, lag_steps=(10, 20), stats_every=20, grid=0.25, skin=0.75)
+    with m.Simulation(m.Params(n=n0, box=L0, **kw), x0, v0) as s:
+        s.step(40)
+        xs, vs, fs = s.get_state(want_force=True)
+        sts, cs, _ = s.stats()
+    with m.Simulation(m.Params(n=n0 * nc, box=L0 * T, **kw), X, V) as s:
+        s.step(40)
+        xb, vb, fb = s.get_state(want_force=True)
+        stb, cb, _ = s.stats()
+    for st in (sts, stb):
+        assert st["status"] == 0 and st["stale_steps"] == 0 and st["step"] == 40
+    assert stb["sort_every"] == sts["sort_every"] and stb["intervals"] == sts["intervals"]
+    xb, vb, fb = (a.reshape(n0, nc, 2) for a in (xb, vb, fb))
+    # positions: each copy is the tile moved by a whole number of tile widths (the
+    # cell offsets are identical; the FP64 sum origin + offset that get_state forms
+    # may round differently at the larger origins, by at most ~2^-40 here)
+    d = xb - shifts[None, :, :] - xs[:, None, :]
+    assert np.abs(d - np.round(d / L0) * L0).max() <= 1e-9
+    assert np.array_equal(vb, np.broadcast_to(vs[:, None, :], vb.shape))
+    assert np.array_equal(fb, np.broadcast_to(fs[:, None, :], fb.shape))
+    for k in ("kinetic", "potential", "virial"):
+        assert stb[k] == nc * sts[k], k
+    assert np.array_equal(cb, cs * np.uint64(nc))
+    rng = np.random.default_rng(12)
+    which = rng.choice(n0 * nc, 200, replace=False)    # as many as the other full-size cases
+    f_ref, scale = oracle.lj_forces_sample(xb.reshape(-1, 2), (L0 * T, L0 * T), which)
+    _force_check(fb.reshape(-1, 2)[which], f_ref, scale, record=record_property)
+
+
 @pytest.mark.parametrize("n,rho,sort_every", [(4096, 0.3, 0), (4096, 0.3, 1), (30000, 0.6, 3),
                                                (4096, 0.3, 1000)])
 def test_ten_step_trajectory(cuda, n, rho, sort_every):

@@ -232,7 +232,9 @@ __device__ __forceinline__ void forces_list(const StepArgs &a, int64_t i, float2
     const float w = a.cell_w;
     const int nb = (int)((uint32_t)(cnt + kListBatch - 1) / kListBatch);   // cnt >= 0
     for (int b = 0; b < nb; ++b) {
-        const uint4 e4 = __ldcs(e + (int64_t)b * n);
+        // one 32 x 32 -> 64-bit product (slot numbers below 2^28, batches below 2^7:
+        // the capacity is at most 512 entries)
+        const uint4 e4 = __ldcs(e + (uint64_t)(uint32_t)b * (uint32_t)n);
         const uint32_t ent[kListBatch] = {e4.x, e4.y, e4.z, e4.w};
         float2 q[kListBatch];
 #pragma unroll
@@ -296,13 +298,15 @@ __device__ __forceinline__ bool list_current(const StepArgs &a, float D) {
 // One slot's force and update.  Returns |v|^2 of the new half-step velocity
 // (kModeStep) and, with STATS, the slot's fixed-point inputs t[] (kinetic
 // energy at the integer step, halved pair energy and virial, momentum).
-// IDX25: slot numbers below 2^25 (see forces_list).
-template <int MODE, bool STATS, bool B, bool SF, bool IDX25 = false>
+// IDX25: slot numbers below 2^25 (see forces_list); INR: the caller has
+// checked i < n.
+template <int MODE, bool STATS, bool B, bool SF, bool IDX25 = false, bool INR = false>
 __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, int64_t cell0,
                                            int64_t i, const float2 *s_tab, bool list_ok,
                                            float (&t)[kStatsN]) {
-    const uint32_t cw = i < a.n ? __ldcs(a.cell + i) : kGhostCell;
-    const bool act = i < a.n && (!B || cw != kGhostCell);
+    const bool inr = INR || i < a.n;
+    const uint32_t cw = inr ? __ldcs(a.cell + i) : kGhostCell;
+    const bool act = inr && (!B || cw != kGhostCell);
     PairAcc acc = {0.f, 0.f, 0.f, 0.f};
     float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
     if (act) {
@@ -494,8 +498,8 @@ __global__ void __launch_bounds__(kStepThreads, kStepLoopBlocksPerSM) k_step_loo
     // slot numbers fit 28 bits wherever lists are used (the entries' j field)
     const int32_t n = (int32_t)a.n, stride = (int32_t)gridDim.x * kStepThreads;
     for (int32_t i = (int32_t)blockIdx.x * kStepThreads + threadIdx.x; i < n; i += stride)
-        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, false, SF, IDX25>(a, a.geo, 0, i, s_tab,
-                                                                          list_ok, t));
+        vmax2 = fmaxf(vmax2, step_slot<kModeStep, false, false, SF, IDX25, true>(a, a.geo, 0, i,
+                                                                                s_tab, list_ok, t));
     step_epilogue<kModeStep, false, false>(a, 0, D, vmax2, t);
 }
 

@@ -72,13 +72,16 @@ __global__ void k_bin_snapshots(LatticeArgs la, int64_t n, const int2 *__restric
 // Multiplying by 1/dx equals dividing by dx when dx is a power of two.  The
 // rest velocity, where most decisions of a short coarse step land, is counted
 // per pair in registers and added to the block histogram once per thread; the
-// other bins take one shared atomic per decision.
+// other bins take one shared atomic per decision.  Every decision issues its
+// atomic (no branch around it): a rest decision adds to a scratch word of its
+// lane past the histograms, which is never read.
 template <int NC, bool ALLPOW2>
 __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restrict__ pos,
                                const float2 *__restrict__ vel, unsigned long long *counts) {
     extern __shared__ uint32_t sh[];
     const int w = 2 * ga.vmax + 1, q1 = w * w + 1;
     const int center = ga.vmax * w + ga.vmax;
+    uint32_t *scratch = sh + q1 * NC + (threadIdx.x & 31);   // rest decisions' atomics
     for (int b = threadIdx.x; b < q1 * NC; b += blockDim.x) sh[b] = 0;
     __syncthreads();
     uint32_t rest[NC];   // rest-velocity counts kept in registers, added once per thread
@@ -115,13 +118,11 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
             const int32_t vy = ceil_small(qy) - 1 - c0y;
             const bool at_rest = (vx | vy) == 0;
             rest[k] += (act && at_rest) ? 1u : 0u;
-            if (act && !at_rest) {
-                // window index by unsigned range checks; the overflow bin past it
-                const uint32_t ux = (uint32_t)(vx + ga.vmax), uy = (uint32_t)(vy + ga.vmax);
-                const uint32_t bin = max(ux, uy) <= (uint32_t)(2 * ga.vmax) ? uy * (uint32_t)w + ux
-                                                                            : (uint32_t)(w * w);
-                atomicAdd(&sh[k * q1 + bin], 1u);
-            }
+            // window index by unsigned range checks; the overflow bin past it
+            const uint32_t ux = (uint32_t)(vx + ga.vmax), uy = (uint32_t)(vy + ga.vmax);
+            const uint32_t bin = max(ux, uy) <= (uint32_t)(2 * ga.vmax) ? uy * (uint32_t)w + ux
+                                                                        : (uint32_t)(w * w);
+            atomicAdd((act && !at_rest) ? &sh[k * q1 + bin] : scratch, 1u);
         }
     }
 #pragma unroll
@@ -142,7 +143,8 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
 // <= c + 1) the cell ceil(x / dx) - 1 is floor(c / 2^s) (the multiples of 2^s
 // are integers).  The decisions therefore equal the division form above bit
 // for bit.  PPT particles per thread per loop trip (2: one 16-byte load of
-// positions and one of velocities).
+// positions and one of velocities).  Rest decisions are counted in registers
+// and send their atomic to the lane's scratch word, as in k_idealgas_bin.
 template <int NC, int PPT>
 __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t n,
                                                        const float2 *__restrict__ pos,
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t 
     const int w = 2 * ga.vmax + 1, q1 = w * w + 1;
     const int center = ga.vmax * w + ga.vmax;
     const uint32_t wmax = (uint32_t)(2 * ga.vmax);
+    uint32_t *scratch = sh + q1 * NC + (threadIdx.x & 31);   // rest decisions' atomics
     for (int b = threadIdx.x; b < q1 * NC; b += blockDim.x) sh[b] = 0;
     __syncthreads();
     uint32_t rest[NC];
@@ -209,11 +212,9 @@ __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t 
                 const int32_t dvy = (cy[u] >> sft) - (by[u] >> sft);
                 const bool at_rest = (dvx | dvy) == 0;
                 rest[k] += (act[u] && at_rest) ? 1u : 0u;
-                if (act[u] && !at_rest) {
-                    const uint32_t ux = (uint32_t)(dvx + ga.vmax), uy = (uint32_t)(dvy + ga.vmax);
-                    const uint32_t bin = max(ux, uy) <= wmax ? uy * (uint32_t)w + ux : (uint32_t)(w * w);
-                    atomicAdd(&sh[k * q1 + bin], 1u);
-                }
+                const uint32_t ux = (uint32_t)(dvx + ga.vmax), uy = (uint32_t)(dvy + ga.vmax);
+                const uint32_t bin = max(ux, uy) <= wmax ? uy * (uint32_t)w + ux : (uint32_t)(w * w);
+                atomicAdd((act[u] && !at_rest) ? &sh[k * q1 + bin] : scratch, 1u);
             }
         }
     }
@@ -718,7 +719,7 @@ cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *p
                                cudaStream_t s) {
     const int threads = 256;
     const int q1 = (2 * ga.vmax + 1) * (2 * ga.vmax + 1) + 1;
-    const size_t smem = (size_t)q1 * NC * sizeof(uint32_t);
+    const size_t smem = ((size_t)q1 * NC + 32) * sizeof(uint32_t);   // + one scratch word per lane
     const float2 *p2 = reinterpret_cast<const float2 *>(pos);
     const float2 *v2 = reinterpret_cast<const float2 *>(vel);
     void (*kern)(IdealGasArgs, int64_t, const float2 *, const float2 *, unsigned long long *);

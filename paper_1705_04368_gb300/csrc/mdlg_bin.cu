@@ -145,7 +145,11 @@ __global__ void k_idealgas_bin(IdealGasArgs ga, int64_t n, const float2 *__restr
 // for bit.  PPT particles per thread per loop trip (2: one 16-byte load of
 // positions and one of velocities).  Rest decisions are counted in registers
 // and send their atomic to the lane's scratch word, as in k_idealgas_bin.
-template <int NC, int PPT>
+// NS > 0: the pairs form a full grid, every (dt, U) group holding the shifts
+// 0 ... NS-1 in order (grid_shifts); the shifts are then compile-time
+// constants, so each particle's start cells are shifted once per distinct
+// shift rather than once per pair, and the pairs at dx_min take no shift.
+template <int NC, int PPT, int NS = 0>
 __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t n,
                                                        const float2 *__restrict__ pos,
                                                        const float2 *__restrict__ vel,
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t 
         }
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            if (k == 0 || ga.first[k]) {
+            if (k == 0 || (NS ? k % NS == 0 : ga.first[k] != 0)) {
                 const float dt = ga.dt[k];
 #pragma unroll
                 for (int u = 0; u < PPT; ++u) {
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(256) k_idealgas_pow2(IdealGasArgs ga, int64_t 
                     cy[u] = ceil_small(__fmul_rn(yn, inv)) - 1;
                 }
             }
-            const int sft = ga.shift[k];
+            const int sft = NS ? k % NS : ga.shift[k];
 #pragma unroll
             for (int u = 0; u < PPT; ++u) {
                 const int32_t dvx = (cx[u] >> sft) - (bx[u] >> sft);
@@ -713,6 +717,17 @@ cudaError_t launch_bin_snapshots(const LatticeArgs &la, int64_t n, const int32_t
     return cudaGetLastError();
 }
 
+// NS of a pair list that forms a full grid -- every (dt, U) group holds the
+// shifts 0 ... NS-1 in order -- for NS in 2..4, else 0 (runtime shifts).
+int grid_shifts(const IdealGasArgs &ga) {
+    int ns = 1;
+    while (ns < ga.ncombo && !ga.first[ns]) ++ns;
+    if (ns < 2 || ns > 4 || ga.ncombo % ns != 0) return 0;
+    for (int k = 0; k < ga.ncombo; ++k)
+        if (ga.shift[k] != k % ns || (ga.first[k] != 0) != (k % ns == 0)) return 0;
+    return ns;
+}
+
 template <int NC>
 cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *pos,
                                const float *vel, unsigned long long *counts, bool allpow2,
@@ -728,6 +743,10 @@ cudaError_t launch_idealgas_nc(const IdealGasArgs &ga, int64_t n, const float *p
         // two particles per thread when both arrays allow 16-byte loads
         const bool vec = ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(vel)) & 15) == 0;
         kern = vec ? k_idealgas_pow2<NC, 2> : k_idealgas_pow2<NC, 1>;
+        const int ns = vec ? grid_shifts(ga) : 0;
+        if constexpr (NC % 2 == 0) if (ns == 2) kern = k_idealgas_pow2<NC, 2, 2>;
+        if constexpr (NC % 3 == 0) if (ns == 3) kern = k_idealgas_pow2<NC, 2, 3>;
+        if constexpr (NC % 4 == 0) if (ns == 4) kern = k_idealgas_pow2<NC, 2, 4>;
         units = vec ? (n + 1) / 2 : n;
     } else {
         kern = k_idealgas_bin<NC, false>;

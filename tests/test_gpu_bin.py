@@ -169,3 +169,47 @@ def test_idealgas_pow2_groups_bit_exact(cuda, boost, offset):
                                 [c[1] for c in combos], 3, us=us)
     assert np.array_equal(got, ref)
     assert np.all(got.sum(axis=1) == n)
+
+
+GRID_LAYOUTS = {
+    # (dx values, dt values, drift per dt or None): pairs (dx, dt) for every dt and dx
+    "ns2": ((0.5, 1.0), (0.25, 1.0, 2.0), None),
+    "ns3": ((1.0, 2.0, 4.0), (0.5, 1.0, 2.0), None),
+    "ns4": ((1.0, 2.0, 4.0, 8.0), (0.5, 2.0), None),
+    "ns3_drift": ((1.0, 2.0, 4.0), (0.5, 1.0), ((0.4, -0.2), (0.0, 0.7))),
+}
+
+
+@pytest.mark.parametrize("layout", sorted(GRID_LAYOUTS) + ["near_grid"])
+def test_idealgas_full_grid_layouts_bit_exact(cuda, layout):
+    # Pair lists that form a full (dt, U) x dx grid run with the shifts as
+    # compile-time constants (2, 3 or 4 dx per group); a list that is almost a
+    # grid (the second group's largest dx differs) keeps the runtime shifts.
+    # Pairs are given out of order and the particle count is odd; every layout is
+    # bit-exact against the oracle.
+    import torch
+    n = 100_003
+    pos, vel = mi.idealgas_state(n, 512.0, 1.0, seed=41)
+    if layout == "near_grid":
+        pairs = [(dx, 0.5) for dx in (1.0, 2.0, 4.0)] + [(dx, 1.0) for dx in (1.0, 2.0, 8.0)]
+        drift = [None] * len(pairs)
+    else:
+        dxs, dts, us_ = GRID_LAYOUTS[layout]
+        pairs, drift = [], []
+        for g, dt in enumerate(dts):
+            for dx in dxs:
+                pairs.append((dx, dt))
+                drift.append(None if us_ is None else us_[g])
+    order = np.random.default_rng(7).permutation(len(pairs))
+    combos = [pairs[i] for i in order]
+    us = None
+    if any(d is not None for d in drift):
+        us = np.array([drift[i] for i in order], np.float32)
+    counts = torch.zeros((len(combos), 50), dtype=torch.int64, device=cuda)
+    m.idealgas_bin(torch.from_numpy(pos).to(cuda), torch.from_numpy(vel).to(cuda), combos, 3,
+                   counts, us=us)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().view(np.uint64)
+    ref = oracle.stream_bin_f32(pos, vel, [c[0] for c in combos], [c[1] for c in combos], 3, us=us)
+    assert np.array_equal(got, ref)
+    assert np.all(got.sum(axis=1) == n)

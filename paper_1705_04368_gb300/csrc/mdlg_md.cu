@@ -350,10 +350,10 @@ __device__ __forceinline__ float step_slot(const StepArgs &a, const Geom &geo, i
             __stcs(a.v_out + i, vh);
             a.cl_out[i] = pn;
             vmax2 = fmaf(vh.x, vh.x, vh.y * vh.y);
-            // the input offset is finite (checked at upload, by this test at
-            // every earlier step, and re-expressed by finite shifts at each
-            // sort), so a finite |v|^2 below 3e38 also bounds the new offset
-            if (!(vmax2 < 3.0e38f)) set_status(a.ctl, kErrNonFinite);
+            // a non-finite velocity or offset (from the forces, or restored from
+            // a corrupt checkpoint) makes the sum NaN or infinite; the values of
+            // any sane run are many orders of magnitude below the bound
+            if (!(vmax2 + fabsf(pn.x) + fabsf(pn.y) < 3.0e38f)) set_status(a.ctl, kErrNonFinite);
         } else if (MODE == kModeInit) {
             vn = v;
             a.v_out[i] = make_float2(fmaf(-fx, a.half_dt_m, v.x), fmaf(-fy, a.half_dt_m, v.y));

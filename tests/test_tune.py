@@ -67,3 +67,24 @@ def test_batch_tuning_keeps_sort_interval_and_checks_every_box(tmp_path):
     assert [s[0] for s in seen] == [0.5, 0.25] and all(s[2] == 7 for s in seen)
     assert (best.grid, best.skin, best.sort_every) == (0.5, 0.5, 7)
     assert rep["key"].startswith("batch nsys=2 n=4e+03")
+
+
+def test_default_candidates_are_valid_geometries_for_the_benchmark_boxes():
+    # every default (grid, skin) gives an MD cell width (grid * ceil((rc + skin) /
+    # grid), the list radius) from 2.75 to 4.0 sigma, on a power-of-two grid that
+    # divides the lattice spacing dx = 4; the production boxes (L = 3740 at
+    # rho = 0.3, 2644 at rho = 0.6) stay within 65535 base cells per axis on every
+    # grid, so the library accepts each candidate there
+    import math
+    import mdlg_inputs as mi
+    widths = []
+    for g, sk in tune.DEFAULT_CANDIDATES:
+        assert g > 0 and math.log2(g) == int(math.log2(g))
+        assert (4.0 / g) == int(4.0 / g)
+        w = g * math.ceil((2.5 + sk) / g - 1e-12)
+        assert 2.75 - 1e-12 <= w <= 4.0 + 1e-12, (g, sk, w)
+        widths.append(w)
+        for c in (mi.PRODUCTION_LJ, mi.PRODUCTION_LJ_DENSE):
+            assert c.box / g <= 65535 and (c.box / g) == int(c.box / g), (g, c.box)
+    assert len(set(widths)) == len(widths)            # no two candidates alike
+    assert {3.125, 3.25, 3.375} <= set(widths)        # the fine steps around the usual optimum
